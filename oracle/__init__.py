@@ -1,0 +1,169 @@
+"""NumPy front end of the plain CPU oracle -- TEST INFRASTRUCTURE ONLY.
+
+Only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline leg may import
+this package.  It shares no code with the CUDA library; see ms_oracle.c for what
+each function computes and which passage of the paper it follows.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+SCALE_MUL = 2.7      # Sec. 3, Eq. 2: scale_mul
+NO_TRIAG = 8         # Sec. 3: no_triag = 8 in all experiments
+OPAC_MUL = 0.2       # Sec. 3: opac_mul = 0.2 in all experiments
+
+_lib = None
+
+
+class OrcCamera(C.Structure):
+    _fields_ = [("width", C.c_int32), ("height", C.c_int32),
+                ("fx", C.c_float), ("fy", C.c_float), ("cx", C.c_float), ("cy", C.c_float),
+                ("R_cw", C.c_float * 9), ("C", C.c_float * 3), ("znear", C.c_float)]
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = C.CDLL(path)
+        P = C.c_void_p
+        L.orc_mesh_build.argtypes = [C.c_int64, P, P, P, P, P, C.c_int, C.c_int, C.c_int, C.c_double,
+                                     C.c_double, C.c_int, P, P, P, P, P]
+        L.orc_render.argtypes = [C.c_int64, P, P, P, C.c_int64, P, P, P, C.c_int, C.c_int, C.c_int,
+                                 C.c_int, C.c_int, C.c_int, P, P, P]
+        L.orc_render_backward.argtypes = [C.c_int64, P, P, P, C.c_int64, P, P, P, C.c_int, C.c_int,
+                                          C.c_int, C.c_int, C.c_int, P, P, P, P]
+        L.orc_sh_basis.argtypes = [C.c_int, P, P]
+        L.orc_quat_to_rot.argtypes = [P, P]
+        L.orc_fan_tris.argtypes = [C.c_int64, C.c_int32, P]
+        L.orc_project.argtypes = [P, P, P, P]
+        _lib = L
+    return _lib
+
+
+def _p(a):
+    return a.ctypes.data_as(C.c_void_p) if a is not None else None
+
+
+def _c(a, dt):
+    return np.ascontiguousarray(a, dtype=dt)
+
+
+def camera_struct(cam) -> OrcCamera:
+    c = OrcCamera()
+    c.width, c.height = int(cam.width), int(cam.height)
+    c.fx, c.fy, c.cx, c.cy = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)
+    R = np.asarray(cam.R_cw, np.float32).reshape(9)
+    for i in range(9):
+        c.R_cw[i] = float(R[i])
+    Cc = np.asarray(cam.C, np.float32).reshape(3)
+    for i in range(3):
+        c.C[i] = float(Cc[i])
+    c.znear = float(cam.znear)
+    return c
+
+
+def threads_used() -> int:
+    return int(lib().orc_last_threads())
+
+
+def quat_to_rot(q) -> np.ndarray:
+    q = _c(q, np.float64)
+    R = np.zeros(9)
+    lib().orc_quat_to_rot(_p(q), _p(R))
+    return R.reshape(3, 3)
+
+
+def sh_basis(degree: int, d) -> np.ndarray:
+    d = _c(d, np.float64)
+    Y = np.zeros(16)
+    if lib().orc_sh_basis(int(degree), _p(d), _p(Y)) != 0:
+        raise ValueError("degree")
+    return Y[: (degree + 1) ** 2]
+
+
+def project(cam, p):
+    """Returns (decided float32 (xs, ys, Z, valid), FP64 (xs, ys, Z)) for one world point."""
+    cs = camera_struct(cam)
+    p = _c(p, np.float64)
+    dec = np.zeros(4, np.float32)
+    val = np.zeros(3)
+    lib().orc_project(C.byref(cs), _p(p), _p(dec), _p(val))
+    return dec, val
+
+
+def fan_tris(n: int, K: int) -> np.ndarray:
+    t = np.zeros((n * K, 3), np.int32)
+    lib().orc_fan_tris(int(n), int(K), _p(t))
+    return t
+
+
+def mesh_build(scene, K=NO_TRIAG, scale_mul=SCALE_MUL, opac_mul=OPAC_MUL, axis_rule=1,
+               cam_center=None, corr=None):
+    """Gaussians -> fan soup (xyz, rgb, alpha), FP64."""
+    n = scene.n
+    V = n * (K + 1)
+    xyz, rgb, alpha = np.zeros((V, 3)), np.zeros((V, 3)), np.zeros(V)
+    sh = _c(scene.sh, np.uint16 if scene.sh_bf16 else np.float32)
+    cc = _c(cam_center, np.float32) if cam_center is not None else None
+    cr = _c(corr, np.float64) if corr is not None else None
+    rc = lib().orc_mesh_build(n, _p(_c(scene.means, np.float32)), _p(_c(scene.log_scales, np.float32)),
+                              _p(_c(scene.quats, np.float32)), _p(_c(scene.opacity, np.float32)), _p(sh),
+                              1 if scene.sh_bf16 else 0, int(scene.sh_degree), int(K), float(scale_mul),
+                              float(opac_mul), int(axis_rule), _p(cc), _p(cr), _p(xyz), _p(rgb), _p(alpha))
+    if rc:
+        raise ValueError(f"orc_mesh_build failed ({rc})")
+    return xyz, rgb, alpha
+
+
+def _window(cam, window):
+    if window is None:
+        return 0, 0, int(cam.width), int(cam.height)
+    return tuple(int(v) for v in window)
+
+
+def render(xyz, rgb, alpha, tris, cam, bg=(0.0, 0.0, 0.0), window=None, brute=False, nthreads=0):
+    """Returns (rgba (h, w, 4) float64, fragments per pixel (h, w) int32, culled triangle count)."""
+    x0, y0, x1, y1 = _window(cam, window)
+    out = np.zeros((max(y1 - y0, 0), max(x1 - x0, 0), 4))
+    nfrag = np.zeros(out.shape[:2], np.int32)
+    nc = np.zeros(1, np.int64)
+    xyz, rgb, alpha = _c(xyz, np.float64), _c(rgb, np.float64), _c(alpha, np.float64)
+    tris = _c(tris, np.int32)
+    cs = camera_struct(cam)
+    bgv = _c(bg, np.float64)
+    rc = lib().orc_render(xyz.shape[0], _p(xyz), _p(rgb), _p(alpha), tris.shape[0], _p(tris), C.byref(cs),
+                          _p(bgv), x0, y0, x1, y1, int(bool(brute)), int(nthreads), _p(out), _p(nfrag), _p(nc))
+    if rc:
+        raise RuntimeError(f"orc_render failed ({rc})")
+    return out, nfrag, int(nc[0])
+
+
+def render_backward(xyz, rgb, alpha, tris, cam, dL, bg=(0.0, 0.0, 0.0), window=None, nthreads=0):
+    """Exact reverse pass; returns (d_xyz, d_rgb, d_alpha) in FP64."""
+    x0, y0, x1, y1 = _window(cam, window)
+    xyz, rgb, alpha = _c(xyz, np.float64), _c(rgb, np.float64), _c(alpha, np.float64)
+    tris = _c(tris, np.int32)
+    dL = _c(dL, np.float64)
+    assert dL.shape == (y1 - y0, x1 - x0, 4)
+    V = xyz.shape[0]
+    gx, gc, ga = np.zeros((V, 3)), np.zeros((V, 3)), np.zeros(V)
+    cs = camera_struct(cam)
+    bgv = _c(bg, np.float64)
+    rc = lib().orc_render_backward(V, _p(xyz), _p(rgb), _p(alpha), tris.shape[0], _p(tris), C.byref(cs),
+                                   _p(bgv), x0, y0, x1, y1, int(nthreads), _p(dL), _p(gx), _p(gc), _p(ga))
+    if rc:
+        raise RuntimeError(f"orc_render_backward failed ({rc})")
+    return gx, gc, ga
+
+
+def l1_loss_grad(rgb_img, target_rgb):
+    """L1 = mean |C - C*| over the RGB channels (Eq. 3 with lambda = 1); returns (loss, dL/dC)."""
+    d = rgb_img - target_rgb
+    n = d.size
+    return float(np.abs(d).sum() / n), np.sign(d) / n
