@@ -1,0 +1,398 @@
+#!/usr/bin/env python
+"""Benchmark of the MeshSplats hot path on GB300.
+
+One step = one pass of the hot path over the 1,000,000-Gaussian clustered scene at
+1920x1080 (SH degree 3 in bfloat16, K = 8): fan conversion with SH colour, render
+(projection, tile binning, radix sort, exact-order composite), L1 loss against a
+jittered-scene target, adjoint, and the two-learning-rate Adam update of the fans.
+
+Prints one JSON line (rank 0).  `value` is rendered megapixels per second of the
+forward+backward step summed over ranks (every rank runs its own replica); `e2e`
+is the same step through the public API with the Gaussians copied from pinned host
+memory and the loss read back inside the timed region.  `--impl reference` times
+the plain CPU oracle on a bounded window of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes as C
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "rendered Mpix/s fwd and fwd+bwd (1080p, 1M fans) vs plain, at 1e-4 image err"
+STAGES = ["mesh_build", "bin", "sort", "composite", "composite_bwd", "loss", "adam"]
+# ncu DRAM traffic per launch (bytes) of the kernels, with the source file digest it
+# was captured on; reported only while the digest still matches.
+TRAFFIC = {}
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", type=int, default=3)
+    p.add_argument("--gaussians", type=int, default=0, help="override the Gaussian count (profiling cases)")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def dist_setup():
+    import torch
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.gpu)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def mpix(W, H, ms):
+    return W * H / (ms * 1e-3) / 1e6
+
+
+# --------------------------------------------------------------------------- oracle arm
+
+def oracle_step_sample(w, K, win, with_backward=True):
+    """One oracle pass over a window of the workload: conversion of every Gaussian,
+    render of the window, L1 against the target window, reverse pass."""
+    import oracle
+    cam = w.cameras[0]
+    xyz, rgb, a = oracle.mesh_build(w.scene, K=K, cam_center=cam.C)
+    tris = oracle.fan_tris(w.scene.n, K)
+    img, _, _ = oracle.render(xyz.astype(np.float32).astype(np.float64), rgb, a, tris, cam, window=win)
+    if with_backward:
+        tgt = np.zeros_like(img)
+        _, g = oracle.l1_loss_grad(img[..., :3], tgt[..., :3])
+        dL = np.zeros_like(img)
+        dL[..., :3] = g
+        oracle.render_backward(xyz.astype(np.float32).astype(np.float64), rgb, a, tris, cam, dL, window=win)
+    return img
+
+
+def cpu_baseline(w, K, target_s=15.0):
+    import oracle
+    cam = w.cameras[0]
+    cx, cy = cam.width // 2, cam.height // 2
+    win = (cx - 64, cy - 64, cx + 64, cy + 64)
+    t0 = time.perf_counter()
+    oracle_step_sample(w, K, win)
+    dt = time.perf_counter() - t0
+    reps = max(1, min(20, int(target_s / max(dt, 1e-3))))
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        oracle_step_sample(w, K, win)
+    dt = (time.perf_counter() - t0) / reps
+    npx = (win[2] - win[0]) * (win[3] - win[1])
+    return {"value": npx / dt / 1e6, "unit": "Mpix/s", "cores": oracle.threads_used(), "kind": "oracle",
+            "sample": f"{reps} passes over the {win[2]-win[0]}x{win[3]-win[1]} centre window (conversion of all "
+                      f"{w.scene.n} Gaussians, window render, L1, reverse pass), {dt:.2f} s each"}
+
+
+def run_reference(args, ws, rank):
+    import synthetic
+    if rank != 0:
+        return
+    w = synthetic.workload(args.workload, n=args.gaussians or None)
+    K = w.K
+    cam = w.cameras[0]
+    cx, cy = cam.width // 2, cam.height // 2
+    win = (cx - 32, cy - 32, cx + 32, cy + 32)
+    for _ in range(args.warmup):
+        oracle_step_sample(w, K, win)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle_step_sample(w, K, win)
+    dt = (time.perf_counter() - t0) / args.steps
+    import oracle
+    npx = (win[2] - win[0]) * (win[3] - win[1])
+    val = npx / dt / 1e6
+    sample = (f"each step: conversion of all {w.scene.n} Gaussians, render + L1 + reverse pass of the "
+              f"{win[2]-win[0]}x{win[3]-win[1]} centre window")
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "Mpix/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "gaussians": w.scene.n, "K": K,
+                       "resolution": f"{cam.width}x{cam.height}", "parallelism": "replicas"},
+            "cpu_baseline": {"value": val, "unit": "Mpix/s", "cores": oracle.threads_used(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": val, "unit": "Mpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------- GPU arm
+
+def run_ours(args, ws, rank, local):
+    import torch
+
+    import synthetic
+    import paper_2502_07754_gb300 as ms
+    from paper_2502_07754_gb300 import _lib
+
+    torch.cuda.set_device(local)
+    if rank == 0:
+        _lib.lib()
+    barrier(ws)
+    L = _lib.lib(build_if_missing=False)
+    w = synthetic.workload(args.workload, n=args.gaussians or None)
+    sc, K, cam = w.scene, w.K, w.cameras[0]
+    W, H = cam.width, cam.height
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    sh_host = sc.sh.view(np.int16) if sc.sh_bf16 else sc.sh
+    G = [dev(sc.means), dev(sc.log_scales), dev(sc.quats), dev(sc.opacity), dev(sh_host)]
+
+    def convert(gs):
+        return ms.mesh_build(*gs, sc.sh_degree, K=K, cam_center=cam.C)
+
+    # target image: the jittered scene, rendered once (an input of the loss, untimed)
+    tg = w.target_scene
+    tG = [dev(tg.means), dev(tg.log_scales), dev(tg.quats), dev(tg.opacity), dev(sh_host)]
+    rend = ms.Renderer(sc.n, K, cam)
+    txyz, trgb, ta = ms.mesh_build(*tG, tg.sh_degree, K=K, cam_center=cam.C)
+    target = rend.forward(txyz, trgb, ta).clone()
+    del txyz, trgb, ta, tG
+
+    xyz, rgb, a = convert(G)
+    rend.forward(xyz, rgb, a)           # sizes the pair capacity (host check, untimed)
+    V = xyz.shape[0]
+    d_xyz, d_rgb, d_a = torch.zeros_like(xyz), torch.zeros_like(rgb), torch.zeros_like(a)
+    adam = ms.FanAdam(xyz, rgb, a)
+    out = torch.empty(H, W, 4, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step(gs):
+        x, c, al = convert(gs)
+        rend.forward(x, c, al, out=out, check_status=False)
+        loss, dL = ms.l1_loss(out, target)
+        d_xyz.zero_(); d_rgb.zero_(); d_a.zero_()
+        rend.backward(x, c, al, out, dL, d_xyz, d_rgb, d_a)
+        adam.step(x, c, al, d_xyz, d_rgb, d_a)
+        return loss
+
+    for _ in range(args.warmup):
+        step(G)
+    torch.cuda.synchronize()
+    st, info = rend.info()
+    _lib.check(st)
+
+    # ---- timed region: K full steps, L2 flushed before each, per-step CUDA events
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    L.ms_profile_read(None, None, 0)
+    launches0 = L.ms_kernel_launches()
+    L.ms_profile_enable(1)
+    barrier(ws)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for i in range(args.steps):
+            flush.zero_()
+            ev0[i].record(stream)
+            step(G)
+            ev1[i].record(stream)
+        torch.cuda.synchronize()
+    barrier(ws)
+    L.ms_profile_enable(0)
+    launches = (L.ms_kernel_launches() - launches0) // args.steps
+    stage_ms = (C.c_double * 7)()
+    stage_n = (C.c_int64 * 7)()
+    _lib.check(L.ms_profile_read(stage_ms, stage_n, 7))
+    step_ms = sum(a_.elapsed_time(b_) for a_, b_ in zip(ev0, ev1)) / args.steps
+    step_ms = max_over_ranks(step_ms, ws)
+    st, info = rend.info()
+    _lib.check(st)
+
+    # ---- forward-only throughput (render call alone)
+    f0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    f1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    x, c, al = convert(G)
+    for i in range(args.steps):
+        flush.zero_()
+        f0[i].record(stream)
+        rend.forward(x, c, al, out=out, check_status=False)
+        f1[i].record(stream)
+    torch.cuda.synchronize()
+    fwd_ms = max_over_ranks(sum(a_.elapsed_time(b_) for a_, b_ in zip(f0, f1)) / args.steps, ws)
+
+    # ---- end to end through the public API from pinned host memory
+    e2e = None
+    if not args.no_e2e:
+        hostG = [torch.from_numpy(np.ascontiguousarray(a_)).pin_memory() for a_ in
+                 (sc.means, sc.log_scales, sc.quats, sc.opacity, sh_host)]
+        devG = [torch.empty_like(h, device="cuda") for h in hostG]
+        loss_host = torch.empty(1, dtype=torch.float32).pin_memory()
+        h2d = sum(h.numel() * h.element_size() for h in hostG)
+        for _ in range(2):
+            for d_, h_ in zip(devG, hostG):
+                d_.copy_(h_, non_blocking=True)
+            step(devG)
+        torch.cuda.synchronize()
+        e0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        e1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        for i in range(args.steps):
+            flush.zero_()
+            e0[i].record(stream)
+            for d_, h_ in zip(devG, hostG):
+                d_.copy_(h_, non_blocking=True)
+            loss = step(devG)
+            loss_host.copy_(loss, non_blocking=True)
+            e1[i].record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = max_over_ranks(sum(a_.elapsed_time(b_) for a_, b_ in zip(e0, e1)) / args.steps, ws)
+        e2e = {"value": ws * mpix(W, H, e2e_ms), "unit": "Mpix/s", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": 4, "ms_per_step": e2e_ms}
+
+    if rank != 0:
+        return
+    # ---- roofline of the dominant kernel
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    per_launch = {STAGES[i]: stage_ms[i] / max(stage_n[i], 1) for i in range(7)}
+    clocks = clk.summary()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    props = torch.cuda.get_device_properties(local)
+    n_sm = props.multi_processor_count
+    alu_peak = n_sm * 128 * sm_max * 1e6 / 1e12           # FP32 lane-ops per second, TOP/s
+    # algorithmic work per launch (unit figures stated in the design notes)
+    cov_ops = info.rect_tests * 10 * K + info.fragments * 40
+    comp_ops = {"composite": cov_ops, "composite_bwd": cov_ops + info.commits * 120}
+    nb = (sc.sh_degree + 1) ** 2 * 3 * (2 if sc.sh_bf16 else 4)
+    hbm_bytes = {"mesh_build": sc.n * (44 + nb) + V * 28,
+                 "bin": V * 12 + info.pairs * 12,
+                 "sort": info.pairs * (8 + 24 * ((info.sort_bits + 7) // 8)),
+                 "loss": W * H * 48,
+                 "adam": V * 7 * 28}
+    stages = {}
+    for s_ in STAGES:
+        t = per_launch[s_]
+        if s_ in hbm_bytes:
+            ach = hbm_bytes[s_] / (t * 1e-3) / 1e9
+            stages[s_] = {"ms": t, "bound": "hbm", "achieved": ach, "unit": "GB/s", "frac": ach / hbm}
+        else:
+            ach = comp_ops[s_] / (t * 1e-3) / 1e12
+            stages[s_] = {"ms": t, "bound": "alu", "achieved": ach, "unit": "TOP/s", "frac": ach / alu_peak}
+    dom = max(STAGES, key=lambda s_: per_launch[s_])
+    d = stages[dom]
+    roof = {"kernel": dom, "bound": d["bound"], "achieved": d["achieved"],
+            "peak": hbm if d["bound"] == "hbm" else alu_peak, "unit": d["unit"], "frac": d["frac"],
+            "peak_source": ("measured hbm_gbs (MEASURED_PEAKS.json)" if d["bound"] == "hbm" else
+                            f"{n_sm} SMs x 128 FP32 lanes x {sm_max:.0f} MHz (max SM clock)"),
+            "traffic": TRAFFIC.get(dom)}
+    line = {"metric": METRIC, "value": ws * mpix(W, H, step_ms), "unit": "Mpix/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w.name, "gaussians": sc.n, "K": K, "resolution": f"{W}x{H}",
+                       "sh": f"degree {sc.sh_degree} {'bf16' if sc.sh_bf16 else 'f32'}",
+                       "step": "mesh_build+render+l1+render_backward+adam",
+                       "l2": "flushed before every timed step (256 MB write)", "parallelism": "replicas"},
+            "fwd_mpix_s": ws * mpix(W, H, fwd_ms), "fwd_ms": fwd_ms,
+            "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks, "roofline": roof, "stages": stages,
+            "work": {"pairs": info.pairs, "rect_tests": info.rect_tests, "fragments": info.fragments,
+                     "commits": info.commits, "extra_passes": info.extra_passes, "sort_bits": info.sort_bits}}
+    if not args.no_cpu_baseline and ws == 1:
+        line["cpu_baseline"] = cpu_baseline(w, K)
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    ws, rank, local = (1, 0, 0)
+    if args.impl == "reference":
+        ws = int(os.environ.get("WORLD_SIZE", "1"))
+        rank = int(os.environ.get("RANK", "0"))
+        run_reference(args, ws, rank)
+        return
+    ws, rank, local = dist_setup()
+    run_ours(args, ws, rank, local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

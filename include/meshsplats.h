@@ -1,0 +1,218 @@
+/*
+ * meshsplats.h -- C ABI of the GB300 (sm_103a) MeshSplats hot path.
+ *
+ * MeshSplats (arXiv 2502.07754) turns every Gaussian of a Gaussian-Splatting scene
+ * into a disjoint triangle fan and renders and fine-tunes those fans with
+ * order-correct alpha compositing.  This library implements, as CUDA kernels:
+ *   ms_mesh_build       Gaussian -> fan conversion with SH colour (Sec. 3, Eq. 2 and the
+ *                       vertex / colour / opacity rules that follow it)
+ *   ms_render           MVP projection, tile binning, radix sort of (tile, depth) keys,
+ *                       exact per-pixel depth order, perspective-correct barycentric
+ *                       interpolation, front-to-back compositing (Sec. 3 "Rendering
+ *                       MeshSplats in Nvdiffrast")
+ *   ms_render_backward  adjoint of ms_render for vertex positions, colours and opacities
+ *                       (Sec. 3 "Fine-tuning", "Optimization and Pruning")
+ *   ms_l1_loss, ms_adam_step   the L1 term of Eq. 3 and the two-learning-rate update
+ *
+ * Conventions (all entry points):
+ *   - Every pointer named d_* or documented as "device" is caller-owned device memory;
+ *     the library never allocates device memory.  Per-call scratch lives in a
+ *     caller-provided workspace sized by the matching *_workspace_size function.
+ *   - Calls are asynchronous on the given stream (cudaStream_t passed as void*; NULL
+ *     is the legacy default stream).  Errors found on the host return immediately;
+ *     errors found on the device (capacity overflow, bounded wait expired) are
+ *     recorded in the workspace and reported by ms_render_get_info().
+ *   - Arrays are row-major, little-endian.  Images are H x W x 4 float32 (R,G,B,A),
+ *     row 0 at the top.  Fan soups are structure-of-arrays: xyz V x 3, rgb V x 3,
+ *     alpha V, with V = N (K+1); vertex g(K+1) is the centre of fan g and vertex
+ *     g(K+1)+1+i its i-th boundary vertex; triangle g K + j is
+ *     (g(K+1), g(K+1)+1+j, g(K+1)+1+((j+1) mod K)).
+ *   - Gradient outputs accumulate (+=); the caller zeroes them.
+ *   - Camera: pinhole, OpenCV axes (x right, y down, z forward), X_cam = R_cw (p - C),
+ *     pixel (fx X/Z + cx, fy Y/Z + cy); pixel (i, j) has its centre at (i+0.5, j+0.5).
+ *
+ * Decisions.  Coverage (top-left fill rule) and the per-pixel depth order are decided
+ * in IEEE binary32 by these formulas, evaluated left to right with round-to-nearest
+ * and no fused multiply-add:
+ *   d = p - C;  X = (R0 d.x + R1 d.y) + R2 d.z (rows of R_cw likewise for Y, Z);
+ *   xs = fx (X / Z) + cx;  ys = fy (Y / Z) + cy;  iz = 1 / Z;
+ *   vertex valid iff Z > znear and |xs|, |ys| <= 2^17 (triangles with an invalid
+ *   vertex are culled);
+ *   area2(A,B,C) = (xB - xA)(yC - yA) - (yB - yA)(xC - xA); 0 never covers, < 0 swaps B,C;
+ *   edge value of the vertex pair {a < b} (by vertex index) at pixel centre p:
+ *   F = (xb - xa)(py - ya) - (yb - ya)(px - xa), negated when the oriented edge runs b->a;
+ *   an edge passes if E > 0, or E == 0 and its direction (ex, ey) has ey < 0, or ey == 0
+ *   and ex > 0; depth Zf = clamp(area2 / ((E0 iz0 + E1 iz1) + E2 iz2), min Z, max Z);
+ *   order: ascending Zf, ties by ascending triangle index.
+ * Interpolation and compositing are FP32: mu_k = (E_k / Z_k) / sum_j (E_j / Z_j),
+ * c = sum mu_k c_k, a = sum mu_k a_k; C += T a c, T *= 1 - a, stop once T < T_eps;
+ * out = (C + T bg, 1 - T).
+ */
+#ifndef MESHSPLATS_H
+#define MESHSPLATS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MS_API __attribute__((visibility("default")))
+
+typedef enum {
+    MS_OK = 0,
+    MS_ERR_INVALID = 1,     /* bad argument (null pointer, size, K out of range, ...) */
+    MS_ERR_CAPACITY = 2,    /* workspace pair capacity exceeded; see ms_render_info */
+    MS_ERR_CUDA = 3,        /* a CUDA runtime call or launch failed */
+    MS_ERR_TIMEOUT = 4,     /* a bounded device-side wait expired (result invalid) */
+    MS_ERR_UNSUPPORTED = 5  /* valid request this build does not implement */
+} ms_status;
+
+/* Fan conversion hyperparameters (Sec. 3: scale_mul, no_triag, opac_mul). */
+typedef struct {
+    int32_t K;          /* no_triag, 3..16 (paper: 8) */
+    float scale_mul;    /* paper: 2.7 */
+    float opac_mul;     /* paper: 0.2 */
+    int32_t axis_rule;  /* 0: drop axis 0 (GaMeS epsilon axis); 1: drop the axis of smallest scale */
+} ms_fan_params;
+
+typedef struct {
+    int32_t width, height;
+    float fx, fy, cx, cy;
+    float R_cw[9];      /* row-major world -> camera rotation */
+    float C[3];         /* camera centre, world */
+    float znear;        /* triangles with a vertex at Z <= znear are culled */
+} ms_camera;
+
+typedef struct {
+    int32_t tile;           /* screen tile edge in pixels: 8, 16 or 32 */
+    int32_t kbuf;           /* per-pixel pending-fragment buffer: 8 or 16 */
+    float T_eps;            /* early-termination transmittance (default 1e-5) */
+    float bg[3];            /* background colour */
+    int64_t pair_capacity;  /* (tile, fan) pair capacity of the workspace; 0 = default */
+    int32_t depth_bits;     /* depth bits in the sort key, 8..31 (0 = default 27) */
+} ms_render_params;
+
+/* Device-side outcome of the last ms_render / ms_render_backward on a workspace. */
+typedef struct {
+    int64_t pairs;          /* (tile, fan) pairs the binning produced */
+    int64_t pair_capacity;  /* capacity of the workspace */
+    int64_t culled_tris;    /* triangles culled at the near plane / guard band */
+    int64_t extra_passes;   /* pixel-passes re-run because the pending buffer overflowed */
+    int32_t overflow;       /* 1 if pairs > pair_capacity (image invalid) */
+    int32_t timeouts;       /* bounded waits that expired (image invalid) */
+    int32_t sort_bits;      /* key bits sorted */
+    int32_t n_tiles;
+    int64_t rect_tests;     /* (pixel, fan) pairs evaluated by the forward composite */
+    int64_t fragments;      /* covered (pixel, triangle) fragments found by the forward composite */
+    int64_t commits;        /* fragments composited by the forward composite */
+} ms_render_info;
+
+/* Stages timed by the optional profiler (ms_profile_enable). */
+typedef enum {
+    MS_STAGE_MESH_BUILD = 0,
+    MS_STAGE_BIN = 1,
+    MS_STAGE_SORT = 2,
+    MS_STAGE_COMPOSITE = 3,
+    MS_STAGE_COMPOSITE_BWD = 4,
+    MS_STAGE_LOSS = 5,
+    MS_STAGE_ADAM = 6,
+    MS_STAGE_COUNT = 7
+} ms_stage;
+
+MS_API const char *ms_version(void);
+/* Message of the last host-side error of this thread (static storage). */
+MS_API const char *ms_last_error(void);
+/* Fills the defaults (tile 16, kbuf 16, T_eps 1e-5, black background, capacity 0). */
+MS_API void ms_render_params_default(ms_render_params *p);
+
+/*
+ * Gaussians -> fan soup (Sec. 3, "MeshSplats Transformation for Flat Gaussians": Eq. 2
+ * a = scale_mul exp(s_a) r_a, b = scale_mul exp(s_b) r_b; v_0 = m,
+ * v_{1+i} = m + cos(theta_i) a + sin(theta_i) b with theta_i = -pi + 2 pi i / K; every
+ * vertex gets the Gaussian's colour; centre opacity sigma, boundary opacity
+ * opac_mul sigma).
+ *   means, log_scales: N x 3 f32; quats: N x 4 f32 (w,x,y,z), normalised here;
+ *   opacity: N f32 (activated); sh: N x (deg+1)^2 x 3, f32 (sh_dtype 0) or bf16 (1);
+ *   colour = max(0, 0.5 + sum_lm Y_lm(dir) f_lm), dir = normalize(m - cam_center), real SH
+ *   basis of degree <= 3; cam_center (host, 3 floats) NULL -> degree 0 only.
+ *   corr: NULL or device N x 2(K+1) f32: radial (first K+1, centre entry unused) and
+ *   log-opacity corrections: v_{1+i} = m + (1 + corr_r) (...), alpha = clamp(alpha exp(corr_o), 0, 1).
+ *   Outputs (device): xyz, rgb (V x 3), alpha (V), V = N (K+1).
+ * All inputs and outputs are device memory.
+ */
+MS_API ms_status ms_mesh_build(const float *means, const float *log_scales, const float *quats,
+                               const float *opacity, const void *sh, int32_t sh_dtype, int32_t sh_degree,
+                               int64_t N, const ms_fan_params *fan, const float *cam_center,
+                               const float *corr, float *xyz, float *rgb, float *alpha, void *stream);
+
+/* Bytes of workspace ms_render / ms_render_backward need for n_fans fans of K triangles. */
+MS_API size_t ms_render_workspace_size(int64_t n_fans, int32_t K, const ms_camera *cam,
+                                       const ms_render_params *params);
+
+/*
+ * Forward render of an implicit-topology fan soup (see Conventions) with exact
+ * per-pixel depth order (Sec. 3 "Rendering MeshSplats in Nvdiffrast": the
+ * depth-peeled layers composited front to back, here with an unbounded layer count).
+ *   xyz, rgb, alpha: device fan soup; n_fans fans of K (3..16) triangles.
+ *   out_rgba: device H x W x 4.
+ *   workspace: device, >= ms_render_workspace_size bytes, 256-byte aligned; it keeps
+ *   the sorted tile lists and per-pixel transmittance that ms_render_backward reuses.
+ * Returns once the work is queued; call ms_render_get_info for device-side errors.
+ */
+MS_API ms_status ms_render(const float *xyz, const float *rgb, const float *alpha, int64_t n_fans, int32_t K,
+                           const ms_camera *cam, const ms_render_params *params, float *out_rgba,
+                           void *workspace, size_t ws_bytes, void *stream);
+
+/*
+ * Adjoint of the last ms_render on this workspace (same scene, camera and params; the
+ * scene must not have changed).  Replays the front-to-back traversal, recomputing
+ * transmittance, and accumulates dL/dxyz, dL/drgb, dL/dalpha (device, +=) from dL/drgba
+ * (device H x W x 4) and the forward output out_rgba.  Visibility (coverage and order)
+ * is held fixed.
+ */
+MS_API ms_status ms_render_backward(const float *xyz, const float *rgb, const float *alpha, int64_t n_fans,
+                                    int32_t K, const ms_camera *cam, const ms_render_params *params,
+                                    const float *out_rgba, const float *dL_drgba, float *d_xyz, float *d_rgb,
+                                    float *d_alpha, void *workspace, size_t ws_bytes, void *stream);
+
+/* Synchronises the stream and reads the device-side outcome recorded in the workspace.
+ * Returns MS_ERR_CAPACITY or MS_ERR_TIMEOUT when the last render on it was invalid. */
+MS_API ms_status ms_render_get_info(const void *workspace, ms_render_info *info, void *stream);
+
+/*
+ * L1 term of Eq. 3: loss = mean over H x W x 3 of |C - C*|.  img_rgba: device H x W x 4;
+ * target_rgba: device H x W x 4 (alpha ignored).  Writes dL_drgba (device H x W x 4,
+ * alpha gradient 0) and loss (device, 1 float; overwritten).
+ */
+MS_API ms_status ms_l1_loss(const float *img_rgba, const float *target_rgba, int64_t n_pixels,
+                            float *dL_drgba, float *loss, void *stream);
+
+/*
+ * Adam step on the fan soup (Sec. 3 "Optimization and Pruning": colours and opacities at
+ * lr_color, positions at lr_xyz = exp(-3) lr_color).  Parameters and gradients are
+ * device SoA arrays of V vertices; m, v: device moments, 7 V floats each (xyz, rgb,
+ * alpha), zeroed before step 1.  step counts from 1.  Opacity is clamped to [0, 1].
+ */
+MS_API ms_status ms_adam_step(float *xyz, float *rgb, float *alpha, const float *d_xyz, const float *d_rgb,
+                              const float *d_alpha, float *m, float *v, int64_t V, int32_t step,
+                              float lr_color, float lr_xyz, float beta1, float beta2, float eps, void *stream);
+
+/*
+ * Optional stage profiler (host-side instrumentation, not part of the method).  While
+ * enabled, every entry point records a CUDA event pair around each of its stages on
+ * the caller's stream.  ms_profile_read waits for those events, writes the summed
+ * milliseconds and the number of timed launches per stage (arrays of n entries,
+ * n <= MS_STAGE_COUNT) and clears the record.  Not thread-safe.
+ */
+MS_API void ms_profile_enable(int32_t on);
+MS_API ms_status ms_profile_read(double *ms_per_stage, int64_t *launches_per_stage, int32_t n);
+
+/* Number of CUDA kernels this library has launched in this process. */
+MS_API int64_t ms_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -167,3 +167,17 @@ def l1_loss_grad(rgb_img, target_rgb):
     d = rgb_img - target_rgb
     n = d.size
     return float(np.abs(d).sum() / n), np.sign(d) / n
+
+
+def adam_step(params, grads, m, v, step, lrs, betas=(0.9, 0.999), eps=1e-15):
+    """Adam (Sec. 3 'Optimization and Pruning': colours and opacities at lr_color,
+    positions at exp(-3) lr_color), FP64, in place on lists of arrays; the opacity
+    (last entry) is clamped to [0, 1] after the step."""
+    b1, b2 = betas
+    for i, (p, g) in enumerate(zip(params, grads)):
+        m[i][...] = b1 * m[i] + (1 - b1) * g
+        v[i][...] = b2 * v[i] + (1 - b2) * g * g
+        mh = m[i] / (1 - b1 ** step)
+        vh = v[i] / (1 - b2 ** step)
+        p -= lrs[i] * mh / (np.sqrt(vh) + eps)
+    np.clip(params[-1], 0.0, 1.0, out=params[-1])

@@ -1,0 +1,6 @@
+"""GB300-native (sm_103a) MeshSplats hot path: fan conversion, tile-binned exact-order
+rendering, its adjoint and the fine-tune update, behind the C ABI of
+include/meshsplats.h (libmeshsplats.so) with a thin torch front end."""
+from . import _lib  # noqa: F401
+from .api import (FanAdam, Renderer, RenderFn, camera_struct, l1_loss, mesh_build, render,  # noqa: F401
+                  render_params)

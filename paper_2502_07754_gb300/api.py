@@ -1,0 +1,180 @@
+"""Thin torch front end of the C ABI: tensors supply device pointers and the current
+stream; every step of the hot path runs in libmeshsplats.so.  There is no CPU or
+eager fallback -- a missing library or a non-CUDA tensor is an error."""
+from __future__ import annotations
+
+import ctypes as C
+import math
+
+import torch
+
+from . import _lib
+from ._lib import check, lib
+
+SCALE_MUL = 2.7
+OPAC_MUL = 0.2
+LR_XYZ_RATIO = math.exp(-3.0)   # Sec. 3: lr_verts = exp(-3) lr_color
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("tensor must live on a CUDA device")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def camera_struct(cam) -> _lib.Camera:
+    c = _lib.Camera()
+    c.width, c.height = int(cam.width), int(cam.height)
+    c.fx, c.fy, c.cx, c.cy = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)
+    R = [float(x) for x in torch.as_tensor(cam.R_cw, dtype=torch.float32).reshape(9).tolist()]
+    for i in range(9):
+        c.R_cw[i] = R[i]
+    Cc = [float(x) for x in torch.as_tensor(cam.C, dtype=torch.float32).reshape(3).tolist()]
+    for i in range(3):
+        c.C[i] = Cc[i]
+    c.znear = float(cam.znear)
+    return c
+
+
+def render_params(tile=16, kbuf=16, T_eps=1e-5, bg=(0.0, 0.0, 0.0), pair_capacity=0, depth_bits=27):
+    p = _lib.RenderParams()
+    lib().ms_render_params_default(C.byref(p))
+    p.tile, p.kbuf, p.T_eps = int(tile), int(kbuf), float(T_eps)
+    for i in range(3):
+        p.bg[i] = float(bg[i])
+    p.pair_capacity = int(pair_capacity)
+    p.depth_bits = int(depth_bits)
+    return p
+
+
+def mesh_build(means, log_scales, quats, opacity, sh, sh_degree, K=8, scale_mul=SCALE_MUL, opac_mul=OPAC_MUL,
+               axis_rule=1, cam_center=None, corr=None, stream=None):
+    """Gaussians -> fan soup (xyz, rgb, alpha) on the device.  sh is float32 or a uint16 /
+    int16 / bfloat16 tensor of bfloat16 bits, shape (N, (deg+1)^2, 3)."""
+    N = means.shape[0]
+    dev = means.device
+    V = N * (K + 1)
+    xyz = torch.empty(V, 3, device=dev, dtype=torch.float32)
+    rgb = torch.empty(V, 3, device=dev, dtype=torch.float32)
+    alpha = torch.empty(V, device=dev, dtype=torch.float32)
+    fp = _lib.FanParams(int(K), float(scale_mul), float(opac_mul), int(axis_rule))
+    sh_dtype = 0 if sh.dtype == torch.float32 else 1
+    cc = (C.c_float * 3)(*[float(x) for x in cam_center]) if cam_center is not None else None
+    check(lib().ms_mesh_build(_ptr(means), _ptr(log_scales), _ptr(quats), _ptr(opacity), _ptr(sh), sh_dtype,
+                              int(sh_degree), N, C.byref(fp), cc, _ptr(corr), _ptr(xyz), _ptr(rgb), _ptr(alpha),
+                              _stream(stream)))
+    return xyz, rgb, alpha
+
+
+class Renderer:
+    """Owns a render workspace for one (fan count, K, camera, params) and grows its pair
+    capacity when a render reports MS_ERR_CAPACITY."""
+
+    def __init__(self, n_fans: int, K: int, cam, params=None, device="cuda"):
+        self.n_fans, self.K = int(n_fans), int(K)
+        self.cam = cam if isinstance(cam, _lib.Camera) else camera_struct(cam)
+        self.params = params if params is not None else render_params()
+        self.device = torch.device(device)
+        self._alloc()
+
+    def _alloc(self):
+        n = lib().ms_render_workspace_size(self.n_fans, self.K, C.byref(self.cam), C.byref(self.params))
+        if n == 0:
+            raise ValueError("invalid render configuration")
+        self.ws = torch.empty(int(n), dtype=torch.uint8, device=self.device)
+
+    @property
+    def shape(self):
+        return (self.cam.height, self.cam.width)
+
+    def info(self, stream=None):
+        inf = _lib.RenderInfo()
+        st = lib().ms_render_get_info(_ptr(self.ws), C.byref(inf), _stream(stream))
+        return st, inf
+
+    def forward(self, xyz, rgb, alpha, out=None, check_status=True, stream=None):
+        if out is None:
+            out = torch.empty(self.cam.height, self.cam.width, 4, device=xyz.device, dtype=torch.float32)
+        for _ in range(4):
+            check(lib().ms_render(_ptr(xyz), _ptr(rgb), _ptr(alpha), self.n_fans, self.K, C.byref(self.cam),
+                                  C.byref(self.params), _ptr(out), _ptr(self.ws), self.ws.numel(), _stream(stream)))
+            if not check_status:
+                return out
+            st, inf = self.info(stream)
+            if st == _lib.MS_ERR_CAPACITY:
+                self.params.pair_capacity = int(inf.pairs * 1.25) + 4096
+                self._alloc()
+                continue
+            check(st)
+            self.last_info = inf
+            return out
+        raise _lib.MSError(_lib.MS_ERR_CAPACITY, "pair capacity did not converge")
+
+    def backward(self, xyz, rgb, alpha, out_rgba, dL, d_xyz=None, d_rgb=None, d_alpha=None, stream=None):
+        if d_xyz is None:
+            d_xyz = torch.zeros_like(xyz)
+            d_rgb = torch.zeros_like(rgb)
+            d_alpha = torch.zeros_like(alpha)
+        check(lib().ms_render_backward(_ptr(xyz), _ptr(rgb), _ptr(alpha), self.n_fans, self.K, C.byref(self.cam),
+                                       C.byref(self.params), _ptr(out_rgba), _ptr(dL.contiguous()), _ptr(d_xyz),
+                                       _ptr(d_rgb), _ptr(d_alpha), _ptr(self.ws), self.ws.numel(), _stream(stream)))
+        return d_xyz, d_rgb, d_alpha
+
+
+class RenderFn(torch.autograd.Function):
+    """Differentiable render of a fan soup; gradients for vertex positions, colours and
+    opacities come from ms_render_backward (visibility held fixed)."""
+
+    @staticmethod
+    def forward(ctx, xyz, rgb, alpha, renderer: Renderer):
+        out = renderer.forward(xyz.detach(), rgb.detach(), alpha.detach())
+        ctx.renderer = renderer
+        ctx.save_for_backward(xyz, rgb, alpha, out)
+        return out
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        xyz, rgb, alpha, out = ctx.saved_tensors
+        d = ctx.renderer.backward(xyz.detach(), rgb.detach(), alpha.detach(), out, grad_out.contiguous())
+        return d[0], d[1], d[2], None
+
+
+def render(xyz, rgb, alpha, renderer: Renderer):
+    return RenderFn.apply(xyz, rgb, alpha, renderer)
+
+
+def l1_loss(img_rgba, target_rgba, stream=None):
+    """Returns (loss as a 1-element device tensor, dL/d img_rgba)."""
+    dL = torch.empty_like(img_rgba)
+    loss = torch.empty(1, device=img_rgba.device, dtype=torch.float32)
+    check(lib().ms_l1_loss(_ptr(img_rgba), _ptr(target_rgba), img_rgba.numel() // 4, _ptr(dL), _ptr(loss),
+                           _stream(stream)))
+    return loss, dL
+
+
+class FanAdam:
+    """Adam over the fan soup: colours/opacities at lr_color, positions at exp(-3) lr_color."""
+
+    def __init__(self, xyz, rgb, alpha, lr_color=5e-3, betas=(0.9, 0.999), eps=1e-15):
+        self.V = xyz.shape[0]
+        self.lr_color = lr_color
+        self.betas, self.eps = betas, eps
+        self.m = torch.zeros(7 * self.V, device=xyz.device)
+        self.v = torch.zeros(7 * self.V, device=xyz.device)
+        self.t = 0
+
+    def step(self, xyz, rgb, alpha, d_xyz, d_rgb, d_alpha, stream=None):
+        self.t += 1
+        check(lib().ms_adam_step(_ptr(xyz), _ptr(rgb), _ptr(alpha), _ptr(d_xyz), _ptr(d_rgb), _ptr(d_alpha),
+                                 _ptr(self.m), _ptr(self.v), self.V, self.t, float(self.lr_color),
+                                 float(self.lr_color * LR_XYZ_RATIO), float(self.betas[0]), float(self.betas[1]),
+                                 float(self.eps), _stream(stream)))

@@ -1,0 +1,374 @@
+// C ABI entry points (include/meshsplats.h): argument checks, workspace layout and
+// the launch sequence of each call.  Nothing here allocates device memory.
+#include <math.h>
+#include <stdarg.h>
+
+#include <atomic>
+#include <vector>
+#include <stdio.h>
+#include <string.h>
+
+#include "ms_common.cuh"
+#include "ms_internal.h"
+
+namespace ms {
+
+static thread_local char g_err[512] = "";
+
+static ms_status fail(ms_status s, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return s;
+}
+
+static ms_status cuda_fail(cudaError_t e, const char *what) {
+    return fail(MS_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// ------------------------------------------------------------------ launch accounting
+static std::atomic<long long> g_launches{0};
+void count_launches(int n) { g_launches += n; }
+
+// ------------------------------------------------------------------ stage profiler
+struct EvPair {
+    int stage;
+    cudaEvent_t a, b;
+};
+static bool g_prof = false;
+static std::vector<EvPair> g_ev;
+static size_t g_ev_used = 0;
+
+StageScope::StageScope(int s, cudaStream_t st_) : stage(s), st(st_), slot(-1) {
+    if (!g_prof) return;
+    if (g_ev_used == g_ev.size()) {
+        EvPair p;
+        p.stage = s;
+        if (cudaEventCreate(&p.a) != cudaSuccess || cudaEventCreate(&p.b) != cudaSuccess) return;
+        g_ev.push_back(p);
+    }
+    slot = (int)g_ev_used++;
+    g_ev[slot].stage = s;
+    cudaEventRecord(g_ev[slot].a, st);
+}
+StageScope::~StageScope() {
+    if (slot >= 0) cudaEventRecord(g_ev[slot].b, st);
+}
+
+static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+static int bits_for(int64_t n) {   // bits to hold values 0..n-1 (at least 1)
+    int b = 1;
+    while (b < 62 && (1ll << b) < n) ++b;
+    return b;
+}
+
+static void params_or_default(const ms_render_params *p, ms_render_params &out) {
+    if (p) {
+        out = *p;
+    } else {
+        ms_render_params_default(&out);
+    }
+    if (out.depth_bits == 0) out.depth_bits = 27;
+    if (out.T_eps <= 0.0f) out.T_eps = 1e-5f;
+}
+
+RenderLayout render_layout(int64_t n_fans, int K, const ms_camera &cam, const ms_render_params &p) {
+    RenderLayout L;
+    memset(&L, 0, sizeof(L));
+    L.tile = p.tile;
+    L.kbuf = p.kbuf;
+    L.tiles_x = (cam.width + p.tile - 1) / p.tile;
+    L.tiles_y = (cam.height + p.tile - 1) / p.tile;
+    L.n_tiles = L.tiles_x * L.tiles_y;
+    L.tile_bits = bits_for(L.n_tiles);
+    L.depth_bits = p.depth_bits;
+    L.key_bits = L.tile_bits + L.depth_bits;
+    L.passes = (L.key_bits + 7) / 8;
+    L.n_fans = n_fans;
+    L.V = n_fans * (K + 1);
+    int64_t cap = p.pair_capacity;
+    if (cap <= 0) {
+        cap = 8 * n_fans;
+        if (cap < 65536) cap = 65536;
+        const int64_t most = n_fans * (int64_t)L.n_tiles;
+        if (cap > most) cap = most > 0 ? most : 1;
+    }
+    L.cap = cap;
+    L.bin_blocks = (n_fans + 255) / 256;
+    L.sort_blocks = (cap + 4095) / 4096;
+    size_t o = 0;
+    L.off_status = o;            o = align_up(o + 256, 256);
+    L.off_bin_state = o;         o = align_up(o + 8 * (size_t)L.bin_blocks, 256);
+    L.off_hist = o;              o = align_up(o + 8 * 256 * 4, 256);
+    L.off_lookback = o;          o = align_up(o + (size_t)L.passes * L.sort_blocks * 256 * 4, 256);
+    L.off_ranges = o;            o = align_up(o + 8 * (size_t)L.n_tiles, 256);
+    L.off_keys0 = o;             o = align_up(o + 8 * (size_t)cap, 256);   // (zeroed prefix ends here)
+    L.off_keys1 = o;             o = align_up(o + 8 * (size_t)cap, 256);
+    L.off_vals0 = o;             o = align_up(o + 4 * (size_t)cap, 256);
+    L.off_vals1 = o;             o = align_up(o + 4 * (size_t)cap, 256);
+    const size_t npx = (size_t)cam.width * cam.height;
+    L.off_tfinal = o;            o = align_up(o + 4 * npx, 256);
+    L.off_ncommit = o;           o = align_up(o + 4 * npx, 256);
+    L.off_grad = o;              o = align_up(o + 32 * (size_t)L.V, 256);
+    L.total = o;
+    return L;
+}
+
+static ms_status check_render_args(const float *xyz, const float *rgb, const float *alpha, int64_t n_fans, int K,
+                                   const ms_camera *cam, const ms_render_params &p, const void *ws, size_t ws_bytes,
+                                   RenderLayout &L) {
+    if (!cam) return fail(MS_ERR_INVALID, "camera is NULL");
+    if (K < 3 || K > kMaxK) return fail(MS_ERR_INVALID, "K=%d outside 3..%d", K, kMaxK);
+    if (n_fans < 0) return fail(MS_ERR_INVALID, "n_fans < 0");
+    if (n_fans > 0 && (!xyz || !rgb || !alpha)) return fail(MS_ERR_INVALID, "scene pointer is NULL");
+    if (n_fans * (int64_t)(K + 1) >= (1ll << 32)) return fail(MS_ERR_INVALID, "too many vertices");
+    if (cam->width <= 0 || cam->height <= 0 || cam->width > 32768 || cam->height > 32768)
+        return fail(MS_ERR_INVALID, "image size %dx%d", cam->width, cam->height);
+    if (!(cam->znear > 0.0f)) return fail(MS_ERR_INVALID, "znear must be > 0");
+    if (!(cam->fx != 0.0f && cam->fy != 0.0f)) return fail(MS_ERR_INVALID, "zero focal length");
+    if (p.tile != 8 && p.tile != 16 && p.tile != 32) return fail(MS_ERR_INVALID, "tile %d not in {8,16,32}", p.tile);
+    if (p.kbuf != 8 && p.kbuf != 16) return fail(MS_ERR_INVALID, "kbuf %d not in {8,16}", p.kbuf);
+    if (p.tile == 32 && p.kbuf != 8) return fail(MS_ERR_UNSUPPORTED, "tile 32 supports kbuf 8 only");
+    if (p.depth_bits < 8 || p.depth_bits > 31) return fail(MS_ERR_INVALID, "depth_bits %d", p.depth_bits);
+    L = render_layout(n_fans, K, *cam, p);
+    if (L.key_bits > 64) return fail(MS_ERR_INVALID, "sort key needs %d bits", L.key_bits);
+    if (L.cap >= (1ll << 30)) return fail(MS_ERR_INVALID, "pair capacity %lld >= 2^30", (long long)L.cap);
+    if (!ws) return fail(MS_ERR_INVALID, "workspace is NULL");
+    if (reinterpret_cast<uintptr_t>(ws) & 255) return fail(MS_ERR_INVALID, "workspace not 256-byte aligned");
+    if (ws_bytes < L.total) return fail(MS_ERR_INVALID, "workspace %zu bytes < %zu needed", ws_bytes, L.total);
+    return MS_OK;
+}
+
+}  // namespace ms
+
+using namespace ms;
+
+extern "C" {
+
+MS_API const char *ms_version(void) { return "meshsplats-gb300 0.1 (sm_103a)"; }
+
+MS_API const char *ms_last_error(void) { return g_err; }
+
+MS_API void ms_render_params_default(ms_render_params *p) {
+    if (!p) return;
+    memset(p, 0, sizeof(*p));
+    p->tile = 16;
+    p->kbuf = 16;
+    p->T_eps = 1e-5f;
+    p->depth_bits = 27;
+}
+
+MS_API ms_status ms_mesh_build(const float *means, const float *log_scales, const float *quats, const float *opacity,
+                               const void *sh, int32_t sh_dtype, int32_t sh_degree, int64_t N, const ms_fan_params *fan,
+                               const float *cam_center, const float *corr, float *xyz, float *rgb, float *alpha,
+                               void *stream) {
+    if (!fan) return fail(MS_ERR_INVALID, "fan params NULL");
+    if (N < 0) return fail(MS_ERR_INVALID, "N < 0");
+    if (fan->K < 3 || fan->K > kMaxK) return fail(MS_ERR_INVALID, "K=%d outside 3..%d", fan->K, kMaxK);
+    if (sh_degree < 0 || sh_degree > 3) return fail(MS_ERR_INVALID, "sh_degree %d", sh_degree);
+    if (sh_dtype != 0 && sh_dtype != 1) return fail(MS_ERR_INVALID, "sh_dtype %d", sh_dtype);
+    if (fan->axis_rule != 0 && fan->axis_rule != 1) return fail(MS_ERR_INVALID, "axis_rule %d", fan->axis_rule);
+    if (N == 0) return MS_OK;
+    if (!means || !log_scales || !quats || !opacity || !sh || !xyz || !rgb || !alpha)
+        return fail(MS_ERR_INVALID, "NULL pointer");
+    if (reinterpret_cast<uintptr_t>(quats) & 15) return fail(MS_ERR_INVALID, "quats must be 16-byte aligned");
+    if (N * (int64_t)(fan->K + 1) >= (1ll << 32)) return fail(MS_ERR_INVALID, "too many vertices");
+    MeshBuildConst kc;
+    memset(&kc, 0, sizeof(kc));
+    kc.K = fan->K;
+    kc.scale_mul = fan->scale_mul;
+    kc.opac_mul = fan->opac_mul;
+    kc.axis_rule = fan->axis_rule;
+    const double PI = 3.14159265358979323846;
+    for (int i = 0; i < fan->K; ++i) {
+        const double th = -PI + 2.0 * PI * i / fan->K;
+        kc.cs[i] = (float)cos(th);
+        kc.sn[i] = (float)sin(th);
+    }
+    kc.shc[0] = (float)(0.5 * sqrt(1.0 / PI));
+    kc.shc[1] = (float)sqrt(3.0 / (4.0 * PI));
+    kc.shc[2] = (float)(0.5 * sqrt(15.0 / PI));
+    kc.shc[3] = (float)(0.25 * sqrt(5.0 / PI));
+    kc.shc[4] = (float)(0.25 * sqrt(15.0 / PI));
+    kc.shc[5] = (float)(0.125 * sqrt(70.0 / PI));
+    kc.shc[6] = (float)(0.25 * sqrt(105.0 / PI));
+    kc.shc[7] = (float)(0.125 * sqrt(42.0 / PI));
+    kc.shc[8] = (float)(0.25 * sqrt(7.0 / PI));
+    if (cam_center) {
+        kc.has_cam = 1;
+        kc.cc[0] = cam_center[0];
+        kc.cc[1] = cam_center[1];
+        kc.cc[2] = cam_center[2];
+    }
+    kc.sh_vec_ok = (reinterpret_cast<uintptr_t>(sh) & 15) == 0;
+    cudaError_t e;
+    {
+        StageScope sc(MS_STAGE_MESH_BUILD, (cudaStream_t)stream);
+        e = launch_mesh_build(means, log_scales, quats, opacity, sh, sh_dtype, sh_degree, N, kc, corr, xyz, rgb, alpha,
+                              (cudaStream_t)stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "mesh_build launch");
+    count_launches(1);
+    return MS_OK;
+}
+
+MS_API size_t ms_render_workspace_size(int64_t n_fans, int32_t K, const ms_camera *cam, const ms_render_params *params) {
+    if (!cam || K < 3 || K > kMaxK || n_fans < 0) return 0;
+    ms_render_params p;
+    params_or_default(params, p);
+    return render_layout(n_fans, K, *cam, p).total;
+}
+
+MS_API ms_status ms_render(const float *xyz, const float *rgb, const float *alpha, int64_t n_fans, int32_t K,
+                           const ms_camera *cam, const ms_render_params *params, float *out_rgba, void *workspace,
+                           size_t ws_bytes, void *stream) {
+    ms_render_params p;
+    params_or_default(params, p);
+    RenderLayout L;
+    ms_status s = check_render_args(xyz, rgb, alpha, n_fans, K, cam, p, workspace, ws_bytes, L);
+    if (s != MS_OK) return s;
+    if (!out_rgba) return fail(MS_ERR_INVALID, "out_rgba is NULL");
+    if (reinterpret_cast<uintptr_t>(out_rgba) & 15) return fail(MS_ERR_INVALID, "out_rgba must be 16-byte aligned");
+    cudaStream_t st = (cudaStream_t)stream;
+    char *ws = static_cast<char *>(workspace);
+    cudaError_t e = cudaMemsetAsync(ws, 0, L.off_keys0, st);
+    if (e != cudaSuccess) return cuda_fail(e, "workspace clear");
+    RenderArgs a;
+    memset(&a, 0, sizeof(a));
+    a.xyz = xyz; a.rgb = rgb; a.alpha = alpha; a.n_fans = n_fans; a.K = K; a.cam = cam; a.prm = p; a.L = L;
+    a.ws = ws; a.out_rgba = out_rgba;
+    {
+        StageScope sc(MS_STAGE_BIN, st);
+        if ((e = launch_bin(a, st)) != cudaSuccess) return cuda_fail(e, "bin launch");
+    }
+    {
+        StageScope sc(MS_STAGE_SORT, st);
+        if ((e = launch_sort(a, st)) != cudaSuccess) return cuda_fail(e, "sort launch");
+    }
+    {
+        StageScope sc(MS_STAGE_COMPOSITE, st);
+        if ((e = launch_composite(a, false, st)) != cudaSuccess) return cuda_fail(e, "composite launch");
+    }
+    if (n_fans > 0) count_launches(1 + 3 + L.passes);
+    if (L.n_tiles > 0) count_launches(1);
+    return MS_OK;
+}
+
+MS_API ms_status ms_render_backward(const float *xyz, const float *rgb, const float *alpha, int64_t n_fans, int32_t K,
+                                    const ms_camera *cam, const ms_render_params *params, const float *out_rgba,
+                                    const float *dL_drgba, float *d_xyz, float *d_rgb, float *d_alpha, void *workspace,
+                                    size_t ws_bytes, void *stream) {
+    ms_render_params p;
+    params_or_default(params, p);
+    RenderLayout L;
+    ms_status s = check_render_args(xyz, rgb, alpha, n_fans, K, cam, p, workspace, ws_bytes, L);
+    if (s != MS_OK) return s;
+    if (!out_rgba || !dL_drgba) return fail(MS_ERR_INVALID, "out_rgba / dL_drgba is NULL");
+    if ((reinterpret_cast<uintptr_t>(out_rgba) | reinterpret_cast<uintptr_t>(dL_drgba)) & 15)
+        return fail(MS_ERR_INVALID, "out_rgba / dL_drgba must be 16-byte aligned");
+    if (n_fans > 0 && (!d_xyz || !d_rgb || !d_alpha)) return fail(MS_ERR_INVALID, "gradient pointer is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    char *ws = static_cast<char *>(workspace);
+    StageScope sc(MS_STAGE_COMPOSITE_BWD, st);
+    cudaError_t e = cudaMemsetAsync(ws + L.off_grad, 0, 32 * (size_t)L.V, st);
+    if (e != cudaSuccess) return cuda_fail(e, "gradient clear");
+    RenderArgs a;
+    memset(&a, 0, sizeof(a));
+    a.xyz = xyz; a.rgb = rgb; a.alpha = alpha; a.n_fans = n_fans; a.K = K; a.cam = cam; a.prm = p; a.L = L;
+    a.ws = ws; a.out_fwd = out_rgba; a.dL = dL_drgba; a.d_xyz = d_xyz; a.d_rgb = d_rgb; a.d_alpha = d_alpha;
+    if ((e = launch_composite(a, true, st)) != cudaSuccess) return cuda_fail(e, "composite backward launch");
+    if ((e = launch_grad_scatter(a, st)) != cudaSuccess) return cuda_fail(e, "gradient scatter launch");
+    count_launches((L.n_tiles > 0 ? 1 : 0) + (L.V > 0 ? 1 : 0));
+    return MS_OK;
+}
+
+MS_API ms_status ms_render_get_info(const void *workspace, ms_render_info *info, void *stream) {
+    if (!workspace || !info) return fail(MS_ERR_INVALID, "NULL argument");
+    Status st;
+    cudaError_t e = cudaMemcpyAsync(&st, workspace, sizeof(Status), cudaMemcpyDeviceToHost, (cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "status read");
+    memset(info, 0, sizeof(*info));
+    info->pairs = (int64_t)st.pairs;
+    info->culled_tris = (int64_t)st.culled;
+    info->extra_passes = (int64_t)st.extra_passes;
+    info->timeouts = (int32_t)st.timeouts;
+    info->pair_capacity = (int64_t)st.cap;
+    info->n_tiles = (int32_t)st.n_tiles;
+    info->sort_bits = (int32_t)st.sort_bits;
+    info->overflow = st.pairs > st.cap ? 1 : 0;
+    info->rect_tests = (int64_t)st.rect_tests;
+    info->fragments = (int64_t)st.fragments;
+    info->commits = (int64_t)st.commits;
+    if (info->overflow)
+        return fail(MS_ERR_CAPACITY, "%llu (tile, fan) pairs exceed the workspace capacity %llu", st.pairs, st.cap);
+    if (st.timeouts) return fail(MS_ERR_TIMEOUT, "%u bounded device waits expired", st.timeouts);
+    return MS_OK;
+}
+
+MS_API ms_status ms_l1_loss(const float *img_rgba, const float *target_rgba, int64_t n_pixels, float *dL_drgba,
+                            float *loss, void *stream) {
+    if (n_pixels < 0 || !loss) return fail(MS_ERR_INVALID, "bad arguments");
+    if (n_pixels > 0 && (!img_rgba || !target_rgba || !dL_drgba)) return fail(MS_ERR_INVALID, "NULL pointer");
+    if ((reinterpret_cast<uintptr_t>(img_rgba) | reinterpret_cast<uintptr_t>(target_rgba) |
+         reinterpret_cast<uintptr_t>(dL_drgba)) & 15)
+        return fail(MS_ERR_INVALID, "images must be 16-byte aligned");
+    cudaError_t e;
+    {
+        StageScope sc(MS_STAGE_LOSS, (cudaStream_t)stream);
+        e = launch_l1(img_rgba, target_rgba, n_pixels, dL_drgba, loss, (cudaStream_t)stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "l1 launch");
+    if (n_pixels > 0) count_launches(1);
+    return MS_OK;
+}
+
+MS_API ms_status ms_adam_step(float *xyz, float *rgb, float *alpha, const float *d_xyz, const float *d_rgb,
+                              const float *d_alpha, float *m, float *v, int64_t V, int32_t step, float lr_color,
+                              float lr_xyz, float beta1, float beta2, float eps, void *stream) {
+    if (V < 0 || step < 1) return fail(MS_ERR_INVALID, "bad V or step");
+    if (V > 0 && (!xyz || !rgb || !alpha || !d_xyz || !d_rgb || !d_alpha || !m || !v))
+        return fail(MS_ERR_INVALID, "NULL pointer");
+    cudaError_t e;
+    {
+        StageScope sc(MS_STAGE_ADAM, (cudaStream_t)stream);
+        e = launch_adam(xyz, rgb, alpha, d_xyz, d_rgb, d_alpha, m, v, V, step, lr_color, lr_xyz, beta1, beta2, eps,
+                        (cudaStream_t)stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "adam launch");
+    if (V > 0) count_launches(1);
+    return MS_OK;
+}
+
+MS_API void ms_profile_enable(int32_t on) { g_prof = on != 0; }
+
+MS_API ms_status ms_profile_read(double *ms_per_stage, int64_t *launches_per_stage, int32_t n) {
+    if (n < 0 || n > MS_STAGE_COUNT) return fail(MS_ERR_INVALID, "n=%d", n);
+    for (int i = 0; i < n; ++i) {
+        if (ms_per_stage) ms_per_stage[i] = 0.0;
+        if (launches_per_stage) launches_per_stage[i] = 0;
+    }
+    ms_status s = MS_OK;
+    for (size_t i = 0; i < g_ev_used; ++i) {
+        float t = 0.0f;
+        cudaError_t e = cudaEventSynchronize(g_ev[i].b);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, g_ev[i].a, g_ev[i].b);
+        if (e != cudaSuccess) {
+            s = cuda_fail(e, "profile event");
+            continue;
+        }
+        const int st = g_ev[i].stage;
+        if (st < n) {
+            if (ms_per_stage) ms_per_stage[st] += t;
+            if (launches_per_stage) launches_per_stage[st] += 1;
+        }
+    }
+    g_ev_used = 0;
+    return s;
+}
+
+MS_API int64_t ms_kernel_launches(void) { return (int64_t)g_launches.load(); }
+
+}  // extern "C"

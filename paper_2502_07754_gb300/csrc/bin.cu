@@ -1,0 +1,176 @@
+// Tile binning of fans: project, count overlapped tiles, scan and emit
+// (tile << depth_bits | quantised min depth, fan id) pairs -- one pass.
+//
+// The binning unit is the fan (K triangles sharing the centre), not the single
+// triangle: a fan is a few pixels wide, so one record per (tile, fan) instead of per
+// (tile, triangle) cuts the pairs the sort moves by about K.  Counting, the
+// exclusive scan across blocks (decoupled look-back with bounded waits) and the
+// emission happen in a single kernel, so fan vertices are read from HBM once.
+#include "fan_geom.cuh"
+#include "ms_internal.h"
+
+namespace ms {
+
+namespace {
+
+constexpr int kBinThreads = 256;
+constexpr unsigned long long kFlagAgg = 1ull << 62, kFlagPre = 2ull << 62, kValMask = (1ull << 62) - 1;
+
+__global__ void __launch_bounds__(kBinThreads) bin_kernel(const float *__restrict__ xyz, int64_t n_fans, int K,
+                                                          CamDev cam, int tile_shift, int tiles_x,
+                                                          int depth_bits, int64_t cap, int64_t nblocks,
+                                                          unsigned n_tiles, unsigned sort_bits,
+                                                          Status *st, unsigned long long *state,
+                                                          unsigned long long *__restrict__ keys,
+                                                          uint32_t *__restrict__ vals) {
+    extern __shared__ float s_xyz[];   // kBinThreads * (K+1) * 3
+    __shared__ uint32_t s_off[kBinThreads + 1];
+    __shared__ uint32_t s_rect[kBinThreads][2];   // (tx0 | ty0 << 16), (w | h << 16)
+    __shared__ uint32_t s_q[kBinThreads];
+    __shared__ uint32_t s_warp[kBinThreads / 32];
+    __shared__ unsigned long long s_excl;
+    __shared__ int s_vid;
+    __shared__ unsigned s_culled;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int KV = K + 1;
+    if (tid == 0) {
+        s_vid = (int)atomicAdd(&st->bin_ticket, 1u);
+        s_culled = 0;
+    }
+    __syncthreads();
+    const int64_t vid = s_vid;
+    const int64_t f0 = vid * kBinThreads;
+    const int nloc = (int)min64(kBinThreads, n_fans - f0);
+
+    // Coalesced staging of the block's vertices.
+    {
+        const float *src = xyz + f0 * KV * 3;
+        const int n = nloc * KV * 3;
+        if ((reinterpret_cast<uintptr_t>(src) & 15) == 0 && (n & 3) == 0) {
+            const float4 *s4 = reinterpret_cast<const float4 *>(src);
+            float4 *d4 = reinterpret_cast<float4 *>(s_xyz);
+            for (int i = tid; i < n / 4; i += kBinThreads) d4[i] = __ldg(s4 + i);
+        } else {
+            for (int i = tid; i < n; i += kBinThreads) s_xyz[i] = __ldg(src + i);
+        }
+    }
+    __syncthreads();
+
+    uint32_t count = 0;
+    if (tid < nloc) {
+        DVert v[kMaxK + 1];
+        const float *p = s_xyz + tid * KV * 3;
+        for (int k = 0; k < KV; ++k) v[k] = decide_vertex(cam, p[3 * k], p[3 * k + 1], p[3 * k + 2]);
+        FanRect r = fan_rect(v, K, cam.width, cam.height);
+        const unsigned ntri_bad = K - __popc(r.valid);
+        if (ntri_bad) atomicAdd(&s_culled, ntri_bad);
+        if (!r.empty) {
+            const int tx0 = r.i0 >> tile_shift, tx1 = r.i1 >> tile_shift;
+            const int ty0 = r.j0 >> tile_shift, ty1 = r.j1 >> tile_shift;
+            const int w = tx1 - tx0 + 1, h = ty1 - ty0 + 1;
+            count = (uint32_t)(w * h);
+            s_rect[tid][0] = (uint32_t)tx0 | ((uint32_t)ty0 << 16);
+            s_rect[tid][1] = (uint32_t)w | ((uint32_t)h << 16);
+            s_q[tid] = depth_q(r.zmin, depth_bits);
+        }
+    }
+    // Block-wide exclusive scan of the counts (fan order).
+    uint32_t x = count;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t t = lane < kBinThreads / 32 ? s_warp[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        if (lane < kBinThreads / 32) s_warp[lane] = t;
+    }
+    __syncthreads();
+    const uint32_t incl = x + (warp > 0 ? s_warp[warp - 1] : 0);
+    s_off[tid + 1] = incl;
+    if (tid == 0) s_off[0] = 0;
+    const uint32_t total = s_warp[kBinThreads / 32 - 1];
+
+    // Decoupled look-back over the preceding (already started) blocks.
+    if (tid == 0) {
+        unsigned long long excl = 0;
+        if (vid == 0) {
+            st_release_u64(&state[0], kFlagPre | (unsigned long long)total);
+        } else {
+            st_release_u64(&state[vid], kFlagAgg | (unsigned long long)total);
+            int64_t j = vid - 1;
+            uint32_t spins = 0;
+            while (j >= 0) {
+                unsigned long long s = ld_acquire_u64(&state[j]);
+                const unsigned long long flag = s & ~kValMask;
+                if (flag == 0) {
+                    if (++spins > kSpinLimit) {
+                        atomicAdd(&st->timeouts, 1u);
+                        break;
+                    }
+                    continue;
+                }
+                excl += s & kValMask;
+                if (flag == kFlagPre) break;
+                --j;
+            }
+            st_release_u64(&state[vid], kFlagPre | (excl + total));
+        }
+        s_excl = excl;
+        if (vid == nblocks - 1) st->pairs = excl + total;
+        if (vid == 0) {
+            st->cap = (unsigned long long)cap;
+            st->n_tiles = n_tiles;
+            st->sort_bits = sort_bits;
+        }
+        if (s_culled) atomicAdd(&st->culled, (unsigned long long)s_culled);
+    }
+    __syncthreads();
+
+    // Output-major emission: consecutive threads write consecutive pairs.
+    const unsigned long long base = s_excl;
+    const unsigned long long tmask = ~0ull;
+    for (uint32_t o = tid; o < total; o += kBinThreads) {
+        const unsigned long long idx = base + o;
+        if (idx >= (unsigned long long)cap) break;
+        int lo = 0, hi = nloc;   // largest f with s_off[f] <= o
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (s_off[mid] <= o) lo = mid; else hi = mid;
+        }
+        const uint32_t k = o - s_off[lo];
+        const uint32_t r0 = s_rect[lo][0], r1 = s_rect[lo][1];
+        const uint32_t w = r1 & 0xFFFFu;
+        const uint32_t tx = (r0 & 0xFFFFu) + k % w, ty = (r0 >> 16) + k / w;
+        const unsigned long long tile = (unsigned long long)ty * tiles_x + tx;
+        keys[idx] = ((tile << depth_bits) | s_q[lo]) & tmask;
+        vals[idx] = (uint32_t)(f0 + lo);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_bin(const RenderArgs &a, cudaStream_t st) {
+    const RenderLayout &L = a.L;
+    if (a.n_fans == 0) return cudaSuccess;
+    const size_t smem = sizeof(float) * kBinThreads * (a.K + 1) * 3;
+    cudaFuncSetAttribute(bin_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int shift = 0;
+    while ((1 << shift) < L.tile) ++shift;
+    bin_kernel<<<(unsigned)L.bin_blocks, kBinThreads, smem, st>>>(
+        a.xyz, a.n_fans, a.K, make_cam(*a.cam), shift, L.tiles_x, L.depth_bits, L.cap, L.bin_blocks,
+        (unsigned)L.n_tiles, (unsigned)(8 * L.passes),
+        reinterpret_cast<Status *>(a.ws + L.off_status), reinterpret_cast<unsigned long long *>(a.ws + L.off_bin_state),
+        reinterpret_cast<unsigned long long *>(a.ws + L.off_keys0), reinterpret_cast<uint32_t *>(a.ws + L.off_vals0));
+    return cudaGetLastError();
+}
+
+}  // namespace ms

@@ -1,0 +1,73 @@
+// Internal launch interfaces between the C ABI (api.cu) and the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/meshsplats.h"
+
+namespace ms {
+
+struct CamDev;
+
+struct MeshBuildConst {
+    int K;
+    float scale_mul, opac_mul;
+    int axis_rule;
+    float cs[16], sn[16];   // cos / sin of theta_i = -pi + 2 pi i / K
+    float shc[9];           // SH normalisation constants (see sh_basis)
+    int has_cam;
+    float cc[3];
+    int sh_vec_ok;          // SH base pointer 16-byte aligned
+};
+
+cudaError_t launch_mesh_build(const float *means, const float *log_scales, const float *quats, const float *opacity,
+                              const void *sh, int sh_dtype, int sh_degree, int64_t N, const MeshBuildConst &kc,
+                              const float *corr, float *xyz, float *rgb, float *alpha, cudaStream_t st);
+
+// Render workspace layout (byte offsets from the workspace base, 256-byte aligned).
+struct RenderLayout {
+    int tile, tiles_x, tiles_y, n_tiles, tile_bits, depth_bits, key_bits, passes, kbuf;
+    int64_t n_fans, V, cap;
+    int64_t bin_blocks, sort_blocks;
+    size_t off_status, off_bin_state, off_keys0, off_keys1, off_vals0, off_vals1, off_hist, off_lookback,
+        off_ranges, off_tfinal, off_ncommit, off_grad, total;
+};
+
+RenderLayout render_layout(int64_t n_fans, int K, const ms_camera &cam, const ms_render_params &p);
+
+struct RenderArgs {
+    const float *xyz, *rgb, *alpha;
+    int64_t n_fans;
+    int K;
+    const ms_camera *cam;
+    ms_render_params prm;
+    RenderLayout L;
+    char *ws;
+    float *out_rgba;
+    // backward
+    const float *out_fwd, *dL;
+    float *d_xyz, *d_rgb, *d_alpha;
+};
+
+cudaError_t launch_bin(const RenderArgs &a, cudaStream_t st);
+cudaError_t launch_sort(const RenderArgs &a, cudaStream_t st);
+cudaError_t launch_composite(const RenderArgs &a, bool backward, cudaStream_t st);
+cudaError_t launch_grad_scatter(const RenderArgs &a, cudaStream_t st);
+
+// Launch accounting and optional stage events (api.cu).
+void count_launches(int n);
+struct StageScope {
+    int stage;
+    cudaStream_t st;
+    int slot;
+    StageScope(int stage, cudaStream_t st);
+    ~StageScope();
+};
+
+cudaError_t launch_l1(const float *img, const float *tgt, int64_t n_pixels, float *dL, float *loss, cudaStream_t st);
+cudaError_t launch_adam(float *xyz, float *rgb, float *alpha, const float *dx, const float *dc, const float *da,
+                        float *m, float *v, int64_t V, int step, float lr_c, float lr_x, float b1, float b2, float eps,
+                        cudaStream_t st);
+
+}  // namespace ms

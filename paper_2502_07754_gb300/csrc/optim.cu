@@ -1,0 +1,92 @@
+// L1 image loss (the L1 term of Eq. 3) and the two-learning-rate Adam update of the
+// fan soup (Sec. 3 "Optimization and Pruning": colours and opacities at lr_color,
+// positions at exp(-3) lr_color).  Both are elementwise and HBM-bound.
+#include "ms_common.cuh"
+#include "ms_internal.h"
+
+namespace ms {
+
+namespace {
+
+__global__ void l1_kernel(const float4 *__restrict__ img, const float4 *__restrict__ tgt, int64_t n,
+                          float4 *__restrict__ dL, float *loss) {
+    const float sc = 1.0f / (3.0f * (float)n);
+    float acc = 0.0f;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float4 a = img[i], b = tgt[i];
+        const float d0 = a.x - b.x, d1 = a.y - b.y, d2 = a.z - b.z;
+        acc += fabsf(d0) + fabsf(d1) + fabsf(d2);
+        dL[i] = make_float4(d0 > 0 ? sc : (d0 < 0 ? -sc : 0.0f), d1 > 0 ? sc : (d1 < 0 ? -sc : 0.0f),
+                            d2 > 0 ? sc : (d2 < 0 ? -sc : 0.0f), 0.0f);
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    __shared__ float s[32];
+    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        float v = threadIdx.x < (blockDim.x >> 5) ? s[threadIdx.x] : 0.0f;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (threadIdx.x == 0) atomicAdd(loss, v * sc);
+    }
+}
+
+__device__ __forceinline__ float adam1(float &p, float g, float &m, float &v, float lr, float b1, float b2, float eps,
+                                       float bc1, float bc2) {
+    m = b1 * m + (1.0f - b1) * g;
+    v = b2 * v + (1.0f - b2) * g * g;
+    p -= lr * (m / bc1) / (sqrtf(v / bc2) + eps);
+    return p;
+}
+
+// Moments are stored as 7 planes of V floats: x, y, z, r, g, b, alpha.
+__global__ void adam_kernel(float *__restrict__ xyz, float *__restrict__ rgb, float *__restrict__ alpha,
+                            const float *__restrict__ dx, const float *__restrict__ dc, const float *__restrict__ da,
+                            float *__restrict__ m, float *__restrict__ v, int64_t V, float lr_c, float lr_x, float b1,
+                            float b2, float eps, float bc1, float bc2) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < V; i += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            float p = xyz[3 * i + r], mm = m[r * V + i], vv = v[r * V + i];
+            adam1(p, dx[3 * i + r], mm, vv, lr_x, b1, b2, eps, bc1, bc2);
+            xyz[3 * i + r] = p;
+            m[r * V + i] = mm;
+            v[r * V + i] = vv;
+        }
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            float p = rgb[3 * i + r], mm = m[(3 + r) * V + i], vv = v[(3 + r) * V + i];
+            adam1(p, dc[3 * i + r], mm, vv, lr_c, b1, b2, eps, bc1, bc2);
+            rgb[3 * i + r] = p;
+            m[(3 + r) * V + i] = mm;
+            v[(3 + r) * V + i] = vv;
+        }
+        float p = alpha[i], mm = m[6 * V + i], vv = v[6 * V + i];
+        adam1(p, da[i], mm, vv, lr_c, b1, b2, eps, bc1, bc2);
+        alpha[i] = fminf(fmaxf(p, 0.0f), 1.0f);
+        m[6 * V + i] = mm;
+        v[6 * V + i] = vv;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_l1(const float *img, const float *tgt, int64_t n, float *dL, float *loss, cudaStream_t st) {
+    cudaMemsetAsync(loss, 0, sizeof(float), st);
+    if (n == 0) return cudaGetLastError();
+    const int grid = (int)min64((n + 255) / 256, 8 * 152);
+    l1_kernel<<<grid, 256, 0, st>>>(reinterpret_cast<const float4 *>(img), reinterpret_cast<const float4 *>(tgt), n,
+                                    reinterpret_cast<float4 *>(dL), loss);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adam(float *xyz, float *rgb, float *alpha, const float *dx, const float *dc, const float *da,
+                        float *m, float *v, int64_t V, int step, float lr_c, float lr_x, float b1, float b2, float eps,
+                        cudaStream_t st) {
+    if (V == 0) return cudaSuccess;
+    const float bc1 = 1.0f - powf(b1, (float)step), bc2 = 1.0f - powf(b2, (float)step);
+    const int grid = (int)min64((V + 255) / 256, 16 * 152);
+    adam_kernel<<<grid, 256, 0, st>>>(xyz, rgb, alpha, dx, dc, da, m, v, V, lr_c, lr_x, b1, b2, eps, bc1, bc2);
+    return cudaGetLastError();
+}
+
+}  // namespace ms

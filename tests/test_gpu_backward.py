@@ -1,0 +1,195 @@
+"""GPU adjoint (ms_render_backward) against the oracle's exact reverse pass and FP64
+central finite differences; L1 loss and Adam against the oracle."""
+import json
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle  # noqa: E402
+import synthetic  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+from gpu_util import dev, gpu_render, oracle_mesh_f32  # noqa: E402
+
+
+def _gpu_grads(r, X, Cc, A, out, dL):
+    dLt = dev(dL.astype(np.float32))
+    gx, gc, ga = r.backward(X, Cc, A, torch.from_numpy(out.astype(np.float32)).cuda(), dLt)
+    torch.cuda.synchronize()
+    return gx.cpu().numpy().astype(np.float64), gc.cpu().numpy().astype(np.float64), ga.cpu().numpy().astype(np.float64)
+
+
+def _close(g, o, rel=1e-2, frac=1e-4):
+    atol = frac * max(np.abs(o).max(), 1e-30)
+    bad = np.abs(g - o) > rel * np.abs(o) + atol
+    return int(bad.sum()), float(np.abs(g - o).max() / max(np.abs(o).max(), 1e-30))
+
+
+def test_backward_matches_oracle_reverse_pass():
+    w = synthetic.workload(1)
+    cam = w.cameras[0]
+    sc = w.scene
+    sc.opacity[:] = np.minimum(sc.opacity, 0.99)
+    xyz, rgb, a = oracle_mesh_f32(sc, 8, cam.C)
+    img, r, (X, Cc, A) = gpu_render(xyz, rgb, a, 8, cam)
+    dL = np.random.default_rng(0).normal(size=img.shape)
+    gx, gc, ga = _gpu_grads(r, X, Cc, A, img, dL)
+    ox, oc, oa = oracle.render_backward(xyz.astype(np.float64), rgb, a, oracle.fan_tris(sc.n, 8), cam, dL)
+    for name, g, o in (("xyz", gx, ox), ("rgb", gc, oc), ("alpha", ga, oa)):
+        nbad, rel = _close(g, o)
+        print(json.dumps({"grad": name, "n_bad": nbad, "max_rel_to_max": rel}))
+        assert nbad == 0, (name, nbad, rel)
+
+
+def test_autograd_function_matches_direct_backward():
+    import paper_2502_07754_gb300 as ms
+    w = synthetic.workload(1, n=300)
+    cam = w.cameras[0]
+    xyz, rgb, a = oracle_mesh_f32(w.scene, 8, cam.C)
+    r = ms.Renderer(300, 8, cam)
+    X = dev(xyz).requires_grad_()
+    Cc = dev(rgb).requires_grad_()
+    A = dev(a).requires_grad_()
+    out = ms.render(X, Cc, A, r)
+    wts = torch.randn_like(out)
+    (out * wts).sum().backward()
+    gx, gc, ga = r.backward(X.detach(), Cc.detach(), A.detach(), out.detach(), wts)
+    # float atomics accumulate in a run-dependent order: equal up to rounding
+    for u, v in ((X.grad, gx), (Cc.grad, gc), (A.grad, ga)):
+        assert torch.allclose(u, v, rtol=1e-4, atol=1e-5 * v.abs().max().item())
+
+
+def _project_np(cam, P):
+    R = np.asarray(cam.R_cw, np.float64)
+    Xc = (P - np.asarray(cam.C, np.float64)) @ R.T
+    return cam.fx * Xc[:, 0] / Xc[:, 2] + cam.cx, cam.fy * Xc[:, 1] / Xc[:, 2] + cam.cy, Xc[:, 2]
+
+
+def test_finetune_gradients_vs_fp64_finite_differences():
+    """Workload 3 (1M clustered Gaussians, 1080p, L1 against the jittered scene): GPU
+    gradients of 64 fans checked against central differences of the FP64 oracle."""
+    w = synthetic.workload(3)
+    cam = w.cameras[0]
+    K = 8
+    xyz, rgb, a = oracle_mesh_f32(w.scene, K, cam.C)
+    txyz, trgb, ta = oracle_mesh_f32(w.target_scene, K, cam.C)
+    img, r, (X, Cc, A) = gpu_render(xyz, rgb, a, K, cam)
+    H, W = cam.height, cam.width
+    n = w.scene.n
+    xs, ys, zs = _project_np(cam, xyz.astype(np.float64))
+    xs, ys = xs.reshape(n, K + 1), ys.reshape(n, K + 1)
+    bx0, bx1 = np.floor(xs.min(1)).astype(int) - 2, np.ceil(xs.max(1)).astype(int) + 3
+    by0, by1 = np.floor(ys.min(1)).astype(int) - 2, np.ceil(ys.max(1)).astype(int) + 3
+    area = (np.clip(bx1, 0, W) - np.clip(bx0, 0, W)) * (np.clip(by1, 0, H) - np.clip(by0, 0, H))
+    rng = np.random.default_rng(11)
+    cand = rng.permutation(np.nonzero((area >= 80) & (bx0 > 0) & (by0 > 0) & (bx1 < W) & (by1 < H))[0])
+    tgtP = txyz.astype(np.float64)
+    dL = np.zeros((H, W, 4))
+    picked = []
+    for g in cand:
+        if len(picked) == 64:
+            break
+        win = (bx0[g], by0[g], bx1[g], by1[g])
+        # fans that can touch the window (3 px margin around their FP64 projections)
+        sel = np.nonzero((bx1 + 3 >= win[0]) & (bx0 - 3 <= win[2]) & (by1 + 3 >= win[1]) & (by0 - 3 <= win[3]))[0]
+        if g not in sel:
+            continue
+        vsel = (sel[:, None] * (K + 1) + np.arange(K + 1)).reshape(-1)
+        tris = oracle.fan_tris(sel.size, K)
+        P = xyz[vsel].astype(np.float64)
+        own = np.nonzero(sel == g)[0][0]
+        # covered pixels of this fan alone
+        _, nf1, _ = oracle.render(P[own * 9:own * 9 + 9], rgb[vsel][own * 9:own * 9 + 9].astype(np.float64),
+                                  a[vsel][own * 9:own * 9 + 9].astype(np.float64), oracle.fan_tris(1, K), cam,
+                                  window=win)
+        if nf1.sum() < 50:
+            continue
+        # the jittered target moves fans by ~0.3 px: the same selection covers the window
+        tgt, _, _ = oracle.render(tgtP[vsel], trgb[vsel].astype(np.float64), ta[vsel].astype(np.float64),
+                                  tris, cam, window=win)
+        picked.append((g, win, sel, vsel, tris, own, tgt))
+    assert len(picked) == 64
+    # dL of the full-image L1 loss, from the oracle's images, inside every picked window
+    scale = 1.0 / (3 * H * W)
+    for g, win, sel, vsel, tris, own, tgt in picked:
+        C_o, _, _ = oracle.render(xyz[vsel].astype(np.float64), rgb[vsel].astype(np.float64),
+                                  a[vsel].astype(np.float64), tris, cam, window=win)
+        dL[win[1]:win[3], win[0]:win[2], :3] = np.sign(C_o[..., :3] - tgt[..., :3]) * scale
+    gx, gc, ga = _gpu_grads(r, X, Cc, A, img, dL)
+    worst = 0.0
+    for g, win, sel, vsel, tris, own, tgt in picked:
+        P0 = xyz[vsel].astype(np.float64)
+        C0 = rgb[vsel].astype(np.float64)
+        A0 = a[vsel].astype(np.float64)
+        # other picked fans' windows may overlap this one; the loss is restricted to this window
+        dLw = dL[win[1]:win[3], win[0]:win[2]]
+
+        def loss(P, Cv, Av):
+            o, _, _ = oracle.render(P, Cv, Av, tris, cam, window=win, nthreads=1)
+            return float((np.abs(o[..., :3] - tgt[..., :3]) * (dLw[..., :3] != 0)).sum() * scale)
+
+        fd, gg = [], []
+        for k in range(K + 1):
+            li, vi = own * (K + 1) + k, g * (K + 1) + k
+            for c in range(3):
+                h = float(np.spacing(np.float32(P0[li, c]))) / 8
+                Pp, Pm = P0.copy(), P0.copy()
+                Pp[li, c] += h
+                Pm[li, c] -= h
+                fd.append((loss(Pp, C0, A0) - loss(Pm, C0, A0)) / (2 * h))
+                gg.append(gx[vi, c])
+            for c in range(3):
+                h = 1e-6
+                Cp, Cm = C0.copy(), C0.copy()
+                Cp[li, c] += h
+                Cm[li, c] -= h
+                fd.append((loss(P0, Cp, A0) - loss(P0, Cm, A0)) / (2 * h))
+                gg.append(gc[vi, c])
+            h = 1e-6
+            Ap, Am = A0.copy(), A0.copy()
+            Ap[li] += h
+            Am[li] -= h
+            fd.append((loss(P0, C0, Ap) - loss(P0, C0, Am)) / (2 * h))
+            gg.append(ga[vi])
+        fd, gg = np.array(fd), np.array(gg)
+        rel = np.linalg.norm(gg - fd) / max(np.linalg.norm(fd), 1e-30)
+        worst = max(worst, rel)
+        assert rel <= 1e-2, (g, rel)
+    print(json.dumps({"fd_fans": 64, "worst_rel_err": worst}))
+
+
+def test_l1_loss_and_adam_match_oracle():
+    import paper_2502_07754_gb300 as ms
+    rng = np.random.default_rng(2)
+    a_img = rng.uniform(0, 1, (37, 53, 4)).astype(np.float32)
+    b_img = rng.uniform(0, 1, (37, 53, 4)).astype(np.float32)
+    loss, dL = ms.l1_loss(dev(a_img), dev(b_img))
+    lo, go = oracle.l1_loss_grad(a_img[..., :3].astype(np.float64), b_img[..., :3].astype(np.float64))
+    assert abs(loss.item() - lo) < 1e-6
+    assert np.abs(dL.cpu().numpy()[..., :3] - go).max() < 1e-9 and (dL.cpu().numpy()[..., 3] == 0).all()
+    V = 1000
+    P = [rng.normal(size=(V, 3)), rng.uniform(0, 1, (V, 3)), rng.uniform(0, 1, V)]
+    Pg = [dev(p.astype(np.float32)) for p in P]
+    P = [p.astype(np.float32).astype(np.float64) for p in P]
+    opt = ms.FanAdam(*Pg, lr_color=5e-3)
+    mo = [np.zeros_like(p) for p in P]
+    vo = [np.zeros_like(p) for p in P]
+    for step in range(1, 4):
+        G = [rng.normal(size=p.shape) * 1e-2 for p in P]
+        Gg = [dev(gr.astype(np.float32)) for gr in G]
+        opt.step(*Pg, *Gg)
+        oracle.adam_step(P, [gr.astype(np.float32).astype(np.float64) for gr in G], mo, vo, step,
+                         [5e-3 * math.exp(-3), 5e-3, 5e-3])
+    for pg, po in zip(Pg, P):
+        assert np.abs(pg.cpu().numpy() - po).max() < 1e-5
