@@ -30,7 +30,7 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 METRIC = "rendered Mpix/s fwd and fwd+bwd (1080p, 1M fans) vs plain, at 1e-4 image err"
-STAGES = ["mesh_build", "bin", "sort", "composite", "composite_bwd", "loss", "adam"]
+STAGES = ["mesh_build", "bin", "sort", "raster", "raster_bwd", "loss", "adam"]
 # ncu DRAM traffic per launch (bytes) of the kernels, with the source file digest it
 # was captured on; reported only while the digest still matches.
 TRAFFIC = {}
@@ -340,7 +340,7 @@ def run_ours(args, ws, rank, local):
     alu_peak = n_sm * 128 * sm_max * 1e6 / 1e12           # FP32 lane-ops per second, TOP/s
     # algorithmic work per launch (unit figures stated in the design notes)
     cov_ops = info.rect_tests * 10 * K + info.fragments * 40
-    comp_ops = {"composite": cov_ops, "composite_bwd": cov_ops + info.commits * 120}
+    comp_ops = {"raster": 2 * cov_ops, "raster_bwd": cov_ops + info.commits * 120}
     nb = (sc.sh_degree + 1) ** 2 * 3 * (2 if sc.sh_bf16 else 4)
     hbm_bytes = {"mesh_build": sc.n * (44 + nb) + V * 28,
                  "bin": V * 12 + info.pairs * 12,

@@ -86,12 +86,13 @@ typedef struct {
 } ms_camera;
 
 typedef struct {
-    int32_t tile;           /* screen tile edge in pixels: 8, 16 or 32 */
+    int32_t tile;           /* screen tile edge in pixels: 8 or 16 (32: MS_ERR_UNSUPPORTED) */
     int32_t kbuf;           /* per-pixel pending-fragment buffer: 8 or 16 */
     float T_eps;            /* early-termination transmittance (default 1e-5) */
     float bg[3];            /* background colour */
     int64_t pair_capacity;  /* (tile, fan) pair capacity of the workspace; 0 = default */
     int32_t depth_bits;     /* depth bits in the sort key, 8..31 (0 = default 27) */
+    int64_t frag_capacity;  /* per-pixel fragment records of the workspace; 0 = 16 W H + 65536 */
 } ms_render_params;
 
 /* Device-side outcome of the last ms_render / ms_render_backward on a workspace. */
@@ -100,13 +101,15 @@ typedef struct {
     int64_t pair_capacity;  /* capacity of the workspace */
     int64_t culled_tris;    /* triangles culled at the near plane / guard band */
     int64_t extra_passes;   /* pixel-passes re-run because the pending buffer overflowed */
-    int32_t overflow;       /* 1 if pairs > pair_capacity (image invalid) */
+    int32_t overflow;       /* 1 if pairs or fragments exceed their capacity (image invalid) */
     int32_t timeouts;       /* bounded waits that expired (image invalid) */
     int32_t sort_bits;      /* key bits sorted */
     int32_t n_tiles;
-    int64_t rect_tests;     /* (pixel, fan) pairs evaluated by the forward composite */
-    int64_t fragments;      /* covered (pixel, triangle) fragments found by the forward composite */
-    int64_t commits;        /* fragments composited by the forward composite */
+    int64_t rect_tests;     /* (pixel, fan) pairs the forward rasterisation evaluated */
+    int64_t fragments;      /* covered (pixel, triangle) fragments it found */
+    int64_t commits;        /* fragments composited by the forward resolve */
+    int64_t frags;          /* fragment records the rasterisation produced */
+    int64_t frag_capacity;  /* fragment record capacity of the workspace */
 } ms_render_info;
 
 /* Stages timed by the optional profiler (ms_profile_enable). */
@@ -114,8 +117,8 @@ typedef enum {
     MS_STAGE_MESH_BUILD = 0,
     MS_STAGE_BIN = 1,
     MS_STAGE_SORT = 2,
-    MS_STAGE_COMPOSITE = 3,
-    MS_STAGE_COMPOSITE_BWD = 4,
+    MS_STAGE_RASTER = 3,          /* count, pixel scan, fill and resolve of the forward */
+    MS_STAGE_RASTER_BWD = 4,      /* fill, adjoint resolve and gradient scatter */
     MS_STAGE_LOSS = 5,
     MS_STAGE_ADAM = 6,
     MS_STAGE_COUNT = 7
@@ -124,7 +127,7 @@ typedef enum {
 MS_API const char *ms_version(void);
 /* Message of the last host-side error of this thread (static storage). */
 MS_API const char *ms_last_error(void);
-/* Fills the defaults (tile 16, kbuf 16, T_eps 1e-5, black background, capacity 0). */
+/* Fills the defaults (tile 16, kbuf 8, T_eps 1e-5, black background, capacity 0, depth bits 27). */
 MS_API void ms_render_params_default(ms_render_params *p);
 
 /*

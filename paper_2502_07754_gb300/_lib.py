@@ -31,14 +31,15 @@ class Camera(C.Structure):
 
 class RenderParams(C.Structure):
     _fields_ = [("tile", C.c_int32), ("kbuf", C.c_int32), ("T_eps", C.c_float), ("bg", C.c_float * 3),
-                ("pair_capacity", C.c_int64), ("depth_bits", C.c_int32)]
+                ("pair_capacity", C.c_int64), ("depth_bits", C.c_int32), ("frag_capacity", C.c_int64)]
 
 
 class RenderInfo(C.Structure):
     _fields_ = [("pairs", C.c_int64), ("pair_capacity", C.c_int64), ("culled_tris", C.c_int64),
                 ("extra_passes", C.c_int64), ("overflow", C.c_int32), ("timeouts", C.c_int32),
                 ("sort_bits", C.c_int32), ("n_tiles", C.c_int32), ("rect_tests", C.c_int64),
-                ("fragments", C.c_int64), ("commits", C.c_int64)]
+                ("fragments", C.c_int64), ("commits", C.c_int64), ("frags", C.c_int64),
+                ("frag_capacity", C.c_int64)]
 
 
 # name -> (restype, argtypes); P = pointer-sized value

@@ -45,7 +45,7 @@ def camera_struct(cam) -> _lib.Camera:
     return c
 
 
-def render_params(tile=16, kbuf=16, T_eps=1e-5, bg=(0.0, 0.0, 0.0), pair_capacity=0, depth_bits=27):
+def render_params(tile=16, kbuf=8, T_eps=1e-5, bg=(0.0, 0.0, 0.0), pair_capacity=0, depth_bits=27):
     p = _lib.RenderParams()
     lib().ms_render_params_default(C.byref(p))
     p.tile, p.kbuf, p.T_eps = int(tile), int(kbuf), float(T_eps)
@@ -111,7 +111,10 @@ class Renderer:
                 return out
             st, inf = self.info(stream)
             if st == _lib.MS_ERR_CAPACITY:
-                self.params.pair_capacity = int(inf.pairs * 1.25) + 4096
+                if inf.pairs > inf.pair_capacity:
+                    self.params.pair_capacity = int(inf.pairs * 1.25) + 4096
+                if inf.frags > inf.frag_capacity:
+                    self.params.frag_capacity = int(inf.frags * 1.25) + 65536
                 self._alloc()
                 continue
             check(st)

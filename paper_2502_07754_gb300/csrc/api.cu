@@ -96,19 +96,34 @@ RenderLayout render_layout(int64_t n_fans, int K, const ms_camera &cam, const ms
         if (cap > most) cap = most > 0 ? most : 1;
     }
     L.cap = cap;
+    const size_t npx = (size_t)cam.width * cam.height;
+    int64_t fcap = p.frag_capacity;
+    if (fcap <= 0) fcap = 16 * (int64_t)npx + 65536;
+    L.frag_cap = fcap;
     L.bin_blocks = (n_fans + 255) / 256;
     L.sort_blocks = (cap + 4095) / 4096;
+    L.scan_blocks = ((int64_t)npx + 2047) / 2048;
+    L.max_items = L.n_tiles + (cap + kItemFans - 1) / kItemFans;
+    L.tscan_blocks = ((int64_t)L.n_tiles + 2047) / 2048;
     size_t o = 0;
     L.off_status = o;            o = align_up(o + 256, 256);
     L.off_bin_state = o;         o = align_up(o + 8 * (size_t)L.bin_blocks, 256);
     L.off_hist = o;              o = align_up(o + 8 * 256 * 4, 256);
     L.off_lookback = o;          o = align_up(o + (size_t)L.passes * L.sort_blocks * 256 * 4, 256);
     L.off_ranges = o;            o = align_up(o + 8 * (size_t)L.n_tiles, 256);
+    L.off_scan_state = o;        o = align_up(o + 8 * (size_t)L.scan_blocks, 256);
+    L.off_tscan_state = o;       o = align_up(o + 8 * (size_t)L.tscan_blocks, 256);
     L.off_keys0 = o;             o = align_up(o + 8 * (size_t)cap, 256);   // (zeroed prefix ends here)
     L.off_keys1 = o;             o = align_up(o + 8 * (size_t)cap, 256);
     L.off_vals0 = o;             o = align_up(o + 4 * (size_t)cap, 256);
     L.off_vals1 = o;             o = align_up(o + 4 * (size_t)cap, 256);
-    const size_t npx = (size_t)cam.width * cam.height;
+    L.off_tile_nitems = o;       o = align_up(o + 4 * (size_t)L.n_tiles, 256);
+    L.off_tile_ibase = o;        o = align_up(o + 4 * (size_t)L.n_tiles, 256);
+    L.off_items = o;             o = align_up(o + 16 * (size_t)L.max_items, 256);
+    L.off_icnt = o;              o = align_up(o + 4 * (size_t)L.max_items * p.tile * p.tile, 256);
+    L.off_counts = o;            o = align_up(o + 4 * npx, 256);
+    L.off_offsets = o;           o = align_up(o + 4 * npx, 256);
+    L.off_frags = o;             o = align_up(o + 32 * (size_t)fcap, 256);
     L.off_tfinal = o;            o = align_up(o + 4 * npx, 256);
     L.off_ncommit = o;           o = align_up(o + 4 * npx, 256);
     L.off_grad = o;              o = align_up(o + 32 * (size_t)L.V, 256);
@@ -128,9 +143,9 @@ static ms_status check_render_args(const float *xyz, const float *rgb, const flo
         return fail(MS_ERR_INVALID, "image size %dx%d", cam->width, cam->height);
     if (!(cam->znear > 0.0f)) return fail(MS_ERR_INVALID, "znear must be > 0");
     if (!(cam->fx != 0.0f && cam->fy != 0.0f)) return fail(MS_ERR_INVALID, "zero focal length");
-    if (p.tile != 8 && p.tile != 16 && p.tile != 32) return fail(MS_ERR_INVALID, "tile %d not in {8,16,32}", p.tile);
+    if (p.tile == 32) return fail(MS_ERR_UNSUPPORTED, "tile 32 is not built (one pixel per thread needs 1024 threads)");
+    if (p.tile != 8 && p.tile != 16) return fail(MS_ERR_INVALID, "tile %d not in {8,16}", p.tile);
     if (p.kbuf != 8 && p.kbuf != 16) return fail(MS_ERR_INVALID, "kbuf %d not in {8,16}", p.kbuf);
-    if (p.tile == 32 && p.kbuf != 8) return fail(MS_ERR_UNSUPPORTED, "tile 32 supports kbuf 8 only");
     if (p.depth_bits < 8 || p.depth_bits > 31) return fail(MS_ERR_INVALID, "depth_bits %d", p.depth_bits);
     L = render_layout(n_fans, K, *cam, p);
     if (L.key_bits > 64) return fail(MS_ERR_INVALID, "sort key needs %d bits", L.key_bits);
@@ -155,7 +170,7 @@ MS_API void ms_render_params_default(ms_render_params *p) {
     if (!p) return;
     memset(p, 0, sizeof(*p));
     p->tile = 16;
-    p->kbuf = 16;
+    p->kbuf = 8;
     p->T_eps = 1e-5f;
     p->depth_bits = 27;
 }
@@ -248,11 +263,13 @@ MS_API ms_status ms_render(const float *xyz, const float *rgb, const float *alph
         if ((e = launch_sort(a, st)) != cudaSuccess) return cuda_fail(e, "sort launch");
     }
     {
-        StageScope sc(MS_STAGE_COMPOSITE, st);
-        if ((e = launch_composite(a, false, st)) != cudaSuccess) return cuda_fail(e, "composite launch");
+        StageScope sc(MS_STAGE_RASTER, st);
+        if ((e = launch_raster_count(a, st)) != cudaSuccess) return cuda_fail(e, "raster count launch");
+        if ((e = launch_raster(a, true, st)) != cudaSuccess) return cuda_fail(e, "raster fill launch");
+        if ((e = launch_resolve(a, false, st)) != cudaSuccess) return cuda_fail(e, "resolve launch");
     }
     if (n_fans > 0) count_launches(1 + 3 + L.passes);
-    if (L.n_tiles > 0) count_launches(1);
+    count_launches(1);   // resolve (raster kernels count themselves)
     return MS_OK;
 }
 
@@ -271,16 +288,19 @@ MS_API ms_status ms_render_backward(const float *xyz, const float *rgb, const fl
     if (n_fans > 0 && (!d_xyz || !d_rgb || !d_alpha)) return fail(MS_ERR_INVALID, "gradient pointer is NULL");
     cudaStream_t st = (cudaStream_t)stream;
     char *ws = static_cast<char *>(workspace);
-    StageScope sc(MS_STAGE_COMPOSITE_BWD, st);
+    StageScope sc(MS_STAGE_RASTER_BWD, st);
     cudaError_t e = cudaMemsetAsync(ws + L.off_grad, 0, 32 * (size_t)L.V, st);
     if (e != cudaSuccess) return cuda_fail(e, "gradient clear");
     RenderArgs a;
     memset(&a, 0, sizeof(a));
     a.xyz = xyz; a.rgb = rgb; a.alpha = alpha; a.n_fans = n_fans; a.K = K; a.cam = cam; a.prm = p; a.L = L;
     a.ws = ws; a.out_fwd = out_rgba; a.dL = dL_drgba; a.d_xyz = d_xyz; a.d_rgb = d_rgb; a.d_alpha = d_alpha;
-    if ((e = launch_composite(a, true, st)) != cudaSuccess) return cuda_fail(e, "composite backward launch");
+    // the fragment records are regenerated from the sorted tile lists (not kept from the
+    // forward); transmittance is recomputed during the resolve
+    if ((e = launch_raster(a, true, st)) != cudaSuccess) return cuda_fail(e, "raster fill launch");
+    if ((e = launch_resolve(a, true, st)) != cudaSuccess) return cuda_fail(e, "resolve backward launch");
     if ((e = launch_grad_scatter(a, st)) != cudaSuccess) return cuda_fail(e, "gradient scatter launch");
-    count_launches((L.n_tiles > 0 ? 1 : 0) + (L.V > 0 ? 1 : 0));
+    count_launches(1 + (L.V > 0 ? 1 : 0));   // resolve, scatter (the fill counts itself)
     return MS_OK;
 }
 
@@ -302,6 +322,13 @@ MS_API ms_status ms_render_get_info(const void *workspace, ms_render_info *info,
     info->rect_tests = (int64_t)st.rect_tests;
     info->fragments = (int64_t)st.fragments;
     info->commits = (int64_t)st.commits;
+    info->frags = (int64_t)st.frags;
+    info->frag_capacity = (int64_t)st.frag_cap;
+    if (st.frags > st.frag_cap) {
+        info->overflow = 1;
+        return fail(MS_ERR_CAPACITY, "%llu fragments exceed the workspace fragment capacity %llu", st.frags,
+                    st.frag_cap);
+    }
     if (info->overflow)
         return fail(MS_ERR_CAPACITY, "%llu (tile, fan) pairs exceed the workspace capacity %llu", st.pairs, st.cap);
     if (st.timeouts) return fail(MS_ERR_TIMEOUT, "%u bounded device waits expired", st.timeouts);

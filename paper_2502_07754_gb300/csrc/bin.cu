@@ -59,20 +59,41 @@ __global__ void __launch_bounds__(kBinThreads) bin_kernel(const float *__restric
 
     uint32_t count = 0;
     if (tid < nloc) {
-        DVert v[kMaxK + 1];
         const float *p = s_xyz + tid * KV * 3;
-        for (int k = 0; k < KV; ++k) v[k] = decide_vertex(cam, p[3 * k], p[3 * k + 1], p[3 * k + 2]);
-        FanRect r = fan_rect(v, K, cam.width, cam.height);
-        const unsigned ntri_bad = K - __popc(r.valid);
+        const uint32_t all = (2u << K) - 1u;   // K+1 vertex bits
+        uint32_t vmask = 0;
+        float mnx = 3.0e38f, mxx = -3.0e38f, mny = 3.0e38f, mxy = -3.0e38f, zmin = 3.0e38f;
+        for (int k = 0; k < KV; ++k) {
+            const DVert d = decide_vertex(cam, p[3 * k], p[3 * k + 1], p[3 * k + 2]);
+            if (d.valid) vmask |= 1u << k;
+            mnx = fminf(mnx, d.xs); mxx = fmaxf(mxx, d.xs);
+            mny = fminf(mny, d.ys); mxy = fmaxf(mxy, d.ys);
+            zmin = fminf(zmin, d.Z);
+        }
+        const uint32_t tmask = tri_valid_mask(vmask, K);
+        if (vmask != all && tmask) {   // bounds over the vertices of valid triangles only
+            mnx = 3.0e38f; mxx = -3.0e38f; mny = 3.0e38f; mxy = -3.0e38f; zmin = 3.0e38f;
+            for (int k = 0; k < KV; ++k) {
+                if (!vertex_used(tmask, k, K)) continue;
+                const DVert d = decide_vertex(cam, p[3 * k], p[3 * k + 1], p[3 * k + 2]);
+                mnx = fminf(mnx, d.xs); mxx = fmaxf(mxx, d.xs);
+                mny = fminf(mny, d.ys); mxy = fmaxf(mxy, d.ys);
+                zmin = fminf(zmin, d.Z);
+            }
+        }
+        const unsigned ntri_bad = K - __popc(tmask);
         if (ntri_bad) atomicAdd(&s_culled, ntri_bad);
-        if (!r.empty) {
-            const int tx0 = r.i0 >> tile_shift, tx1 = r.i1 >> tile_shift;
-            const int ty0 = r.j0 >> tile_shift, ty1 = r.j1 >> tile_shift;
-            const int w = tx1 - tx0 + 1, h = ty1 - ty0 + 1;
-            count = (uint32_t)(w * h);
-            s_rect[tid][0] = (uint32_t)tx0 | ((uint32_t)ty0 << 16);
-            s_rect[tid][1] = (uint32_t)w | ((uint32_t)h << 16);
-            s_q[tid] = depth_q(r.zmin, depth_bits);
+        if (tmask) {
+            const FanRect r = rect_from_bounds(mnx, mxx, mny, mxy, cam.width, cam.height);
+            if (!r.empty) {
+                const int tx0 = r.i0 >> tile_shift, tx1 = r.i1 >> tile_shift;
+                const int ty0 = r.j0 >> tile_shift, ty1 = r.j1 >> tile_shift;
+                const int w = tx1 - tx0 + 1, h = ty1 - ty0 + 1;
+                count = (uint32_t)(w * h);
+                s_rect[tid][0] = (uint32_t)tx0 | ((uint32_t)ty0 << 16);
+                s_rect[tid][1] = (uint32_t)w | ((uint32_t)h << 16);
+                s_q[tid] = depth_q(zmin, depth_bits);
+            }
         }
     }
     // Block-wide exclusive scan of the counts (fan order).

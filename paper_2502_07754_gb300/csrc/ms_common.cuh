@@ -30,9 +30,15 @@ struct Status {
     unsigned int sort_ticket[8];     // virtual block ids of each sort pass
     unsigned int n_tiles;
     unsigned int sort_bits;
-    unsigned long long rect_tests;   // forward composite work counters
+    unsigned long long rect_tests;   // forward rasterisation / resolve work counters
     unsigned long long fragments;
     unsigned long long commits;
+    unsigned long long frags;        // fragment records the pixel scan counted
+    unsigned long long frag_cap;     // fragment record capacity of the workspace
+    unsigned int scan_ticket;        // virtual block ids of the pixel scan
+    unsigned int tscan_ticket;       // virtual block ids of the tile work-item scan
+    unsigned int n_items;            // raster work items (<= 64 fans of one tile each)
+    unsigned long long items_total;  // work items the tile scan counted
 };
 static_assert(sizeof(Status) <= 256, "status block");
 

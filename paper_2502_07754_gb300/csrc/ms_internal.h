@@ -28,10 +28,11 @@ cudaError_t launch_mesh_build(const float *means, const float *log_scales, const
 // Render workspace layout (byte offsets from the workspace base, 256-byte aligned).
 struct RenderLayout {
     int tile, tiles_x, tiles_y, n_tiles, tile_bits, depth_bits, key_bits, passes, kbuf;
-    int64_t n_fans, V, cap;
-    int64_t bin_blocks, sort_blocks;
+    int64_t n_fans, V, cap, frag_cap;
+    int64_t bin_blocks, sort_blocks, scan_blocks, tscan_blocks, max_items;
     size_t off_status, off_bin_state, off_keys0, off_keys1, off_vals0, off_vals1, off_hist, off_lookback,
-        off_ranges, off_tfinal, off_ncommit, off_grad, total;
+        off_ranges, off_scan_state, off_tscan_state, off_tile_nitems, off_tile_ibase, off_items, off_icnt,
+        off_counts, off_offsets, off_frags, off_tfinal, off_ncommit, off_grad, total;
 };
 
 RenderLayout render_layout(int64_t n_fans, int K, const ms_camera &cam, const ms_render_params &p);
@@ -52,7 +53,11 @@ struct RenderArgs {
 
 cudaError_t launch_bin(const RenderArgs &a, cudaStream_t st);
 cudaError_t launch_sort(const RenderArgs &a, cudaStream_t st);
-cudaError_t launch_composite(const RenderArgs &a, bool backward, cudaStream_t st);
+constexpr int kItemFans = 64;   // fans per raster work item
+
+cudaError_t launch_raster(const RenderArgs &a, bool fill, cudaStream_t st);
+cudaError_t launch_raster_count(const RenderArgs &a, cudaStream_t st);   // items, count, prefix, pixel scan
+cudaError_t launch_resolve(const RenderArgs &a, bool backward, cudaStream_t st);
 cudaError_t launch_grad_scatter(const RenderArgs &a, cudaStream_t st);
 
 // Launch accounting and optional stage events (api.cu).

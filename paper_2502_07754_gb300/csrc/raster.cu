@@ -1,0 +1,379 @@
+// Tile rasterisation into a per-pixel fragment buffer (A-buffer) in HBM.
+//
+// Every tile's fan list (sorted by the fans' depth bounds) is cut into work items of
+// at most kItemFans fans; one warp rasterises one item, so a hot tile with thousands
+// of fans spreads over many warps instead of serialising on one.  A warp projects
+// the item's fans in parallel (one fan per lane) into its own shared-memory stage,
+// then walks them in list order: for each fan its lanes enumerate exactly the pixels
+// of the fan's pixel rectangle inside the tile and test the fan's K triangles at each
+// with the binary32 decision formulas.  No block barriers are used.
+//
+// Count pass: per (item, pixel) fragment counts.  A per-tile prefix over the tile's
+// items turns them into each item's starting slot within the pixel and gives the
+// pixel totals; an exclusive scan over pixels gives record offsets.  Fill pass: the
+// same walk writes one 32-byte record per fragment at offset + item slot + running
+// index -- depth, triangle id, the fan's depth bound, opacity, colour -- so a pixel's
+// records come out in tile-list order, which the resolve relies on.
+#include "raster_common.cuh"
+
+namespace ms {
+
+namespace {
+
+struct RastArgs {
+    SceneDev sc;
+    int tiles_x, depth_bits;
+    const unsigned long long *keys;
+    const uint32_t *vals;
+    const uint4 *items;        // (tile, start, end, index within tile)
+    uint32_t *icnt;            // [item][tile pixels]: counts, then in-pixel starting slots
+    const uint32_t *offsets;
+    const uint32_t *counts;
+    float4 *frags;
+    int64_t frag_cap;
+    Status *st;
+};
+
+constexpr int kRastWarps = 4;   // warps (work items) per block
+
+template <int TILE, int STG, bool FILL>
+__host__ __device__ __forceinline__ size_t warp_smem_bytes(int K) {
+    return (size_t)TILE * TILE * 4 * (FILL ? 2 : 1) + stage_bytes(STG, K, FILL);
+}
+
+template <int TILE, int STG, int KT, bool FILL>
+__global__ void __launch_bounds__(kRastWarps * 32) raster_kernel(RastArgs a) {
+    extern __shared__ __align__(16) char smem[];
+    const int K = KT > 0 ? KT : a.sc.K;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t item = blockIdx.x * kRastWarps + warp;
+    if (item >= a.st->n_items) return;   // whole warp; nothing below synchronises the block
+    const uint4 it = a.items[item];
+    const int tile = (int)it.x;
+    char *mine = smem + (size_t)warp * warp_smem_bytes<TILE, STG, FILL>(K);
+    uint32_t *s_cnt = reinterpret_cast<uint32_t *>(mine);   // [TILE*TILE] fragments so far
+    uint32_t *s_base = s_cnt + TILE * TILE;                   // [TILE*TILE] record offsets (fill)
+    const Stage S = stage_ptrs(mine + (size_t)TILE * TILE * 4 * (FILL ? 2 : 1), STG, K, FILL);
+    const int tx0 = (tile % a.tiles_x) * TILE, ty0 = (tile / a.tiles_x) * TILE;
+    const int tx1 = min(tx0 + TILE, a.sc.W) - 1, ty1 = min(ty0 + TILE, a.sc.H) - 1;
+    uint32_t *icnt = a.icnt + (size_t)item * TILE * TILE;
+    for (int i = lane; i < TILE * TILE; i += 32) {
+        s_cnt[i] = 0;
+        if (FILL) {
+            const int x = tx0 + (i % TILE), y = ty0 + (i / TILE);
+            uint32_t b = 0xffffffffu;
+            if (x <= tx1 && y <= ty1) {
+                const size_t pix = (size_t)y * a.sc.W + x;
+                const int64_t o = a.offsets[pix];
+                // a pixel whose records would not fit gets none (the overflow is reported)
+                if (o + a.counts[pix] <= a.frag_cap) b = (uint32_t)o + icnt[i];
+            }
+            s_base[i] = b;
+        }
+    }
+    uint32_t c_rect = 0, c_frag = 0;
+    __syncwarp();
+    for (uint32_t cb = it.y; cb < it.z; cb += STG) {
+        const int cnt = (int)min((uint32_t)STG, it.z - cb);
+        if (lane < cnt) {
+            const uint32_t li = cb + lane;
+            const uint32_t q = (uint32_t)(__ldg(a.keys + li) & ((1ull << a.depth_bits) - 1ull));
+            stage_fan(a.sc, S, STG, K, lane, __ldg(a.vals + li), q, FILL);
+        }
+        __syncwarp();
+        for (int f = 0; f < cnt; ++f) {
+            const uint32_t flags = S.flags[f];
+            const int4 r = S.rect[f];
+            const int rx0 = max(r.x, tx0), rx1 = min(r.y, tx1), ry0 = max(r.z, ty0), ry1 = min(r.w, ty1);
+            if (flags == 0 || rx0 > rx1 || ry0 > ry1) continue;   // warp-uniform
+            const int w = rx1 - rx0 + 1, npx = w * (ry1 - ry0 + 1);
+            const float inv_w = 1.0f / (float)w;
+            for (int base = 0; base < npx; base += 32) {
+                const int idx = base + lane;
+                if (idx < npx) {
+                    ++c_rect;
+                    // (idx + 0.5) / w is at least 1/(2w) away from an integer: exact row
+                    const int yy = (int)(((float)idx + 0.5f) * inv_w);
+                    const int px = rx0 + (idx - yy * w), py = ry0 + yy;
+                    const int lp = (py - ty0) * TILE + (px - tx0);
+                    const float pxc = (float)px + 0.5f, pyc = (float)py + 0.5f;
+                    cover_fan<KT>(S, STG, K, f, flags, pxc, pyc,
+                                  [&](int j, int jn, bool neg, float E0, float E1, float E2) {
+                        const uint32_t slot = s_cnt[lp]++;
+                        ++c_frag;
+                        if (FILL) {
+                            const uint32_t b = s_base[lp];
+                            if (b == 0xffffffffu) return;
+                            const float izc = S.viz[f];
+                            const float izj = S.viz[(1 + j) * STG + f], izn = S.viz[(1 + jn) * STG + f];
+                            const float zf = dec_depth(S.area[j * STG + f], E0, izc, E1, neg ? izn : izj, E2,
+                                                       neg ? izj : izn, S.vz[f], S.vz[(1 + j) * STG + f],
+                                                       S.vz[(1 + jn) * STG + f]);
+                            // perspective-correct barycentrics from the accurate centre offsets
+                            const float ox = __fsub_rn(S.cxh[f], pxc) + S.cxl[f];
+                            const float oy = __fsub_rn(S.cyh[f], pyc) + S.cyl[f];
+                            const float ujx = ox + S.du[j * STG + f], ujy = oy + S.dv[j * STG + f];
+                            const float unx = ox + S.du[jn * STG + f], uny = oy + S.dv[jn * STG + f];
+                            const float w0 = (ujx * uny - ujy * unx) * izc;
+                            const float w1 = (unx * oy - uny * ox) * izj;
+                            const float w2 = (ox * ujy - oy * ujx) * izn;
+                            const float iW = 1.0f / (w0 + w1 + w2);
+                            const float m0 = w0 * iW, m1 = w1 * iW, m2 = w2 * iW;
+                            const int vj = (1 + j) * STG + f, vn = (1 + jn) * STG + f;
+                            const float al = m0 * S.ca[f] + m1 * S.ca[vj] + m2 * S.ca[vn];
+                            const float c0 = m0 * S.cr[f] + m1 * S.cr[vj] + m2 * S.cr[vn];
+                            const float c1 = m0 * S.cg[f] + m1 * S.cg[vj] + m2 * S.cg[vn];
+                            const float c2 = m0 * S.cb[f] + m1 * S.cb[vj] + m2 * S.cb[vn];
+                            const uint32_t tri = S.fan[f] * (uint32_t)K + (uint32_t)j;
+                            float4 *rec = a.frags + 2 * ((size_t)b + slot);
+                            rec[0] = make_float4(zf, __uint_as_float(tri), __uint_as_float(S.q[f]), al);
+                            rec[1] = make_float4(c0, c1, c2, 0.0f);
+                        }
+                    });
+                }
+                __syncwarp();   // a later fan may append to the same pixel from another lane
+            }
+        }
+        __syncwarp();
+    }
+    if (!FILL) {
+        for (int i = lane; i < TILE * TILE; i += 32) icnt[i] = s_cnt[i];
+        const unsigned r0 = __reduce_add_sync(0xffffffffu, c_rect);
+        const unsigned r1 = __reduce_add_sync(0xffffffffu, c_frag);
+        if (lane == 0) {
+            atomicAdd(&a.st->rect_tests, (unsigned long long)r0);
+            atomicAdd(&a.st->fragments, (unsigned long long)r1);
+        }
+    }
+}
+
+// Exclusive scan of u32 counts into u32 offsets (decoupled look-back over virtual block
+// ids, bounded waits); the grand total goes to *total_out.
+constexpr int kScanThreads = 256, kScanItems = 8, kScanTile = kScanThreads * kScanItems;
+constexpr unsigned long long kFlagAgg = 1ull << 62, kFlagPre = 2ull << 62, kValMask = (1ull << 62) - 1;
+
+__global__ void __launch_bounds__(kScanThreads) scan_u32_kernel(const uint32_t *__restrict__ counts,
+                                                                uint32_t *__restrict__ offsets, int64_t n,
+                                                                int64_t nblocks, unsigned long long *state,
+                                                                unsigned *ticket, unsigned long long *total_out,
+                                                                Status *st) {
+    __shared__ int s_vid;
+    __shared__ uint32_t s_warp[kScanThreads / 32];
+    __shared__ unsigned long long s_excl;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) s_vid = (int)atomicAdd(ticket, 1u);
+    __syncthreads();
+    const int64_t vid = s_vid;
+    const int64_t base = vid * kScanTile + (int64_t)tid * kScanItems;
+    uint32_t v[kScanItems];
+    uint32_t sum = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        v[i] = base + i < n ? counts[base + i] : 0u;
+        sum += v[i];
+    }
+    uint32_t x = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t t = lane < kScanThreads / 32 ? s_warp[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        if (lane < kScanThreads / 32) s_warp[lane] = t;
+    }
+    __syncthreads();
+    const uint32_t total = s_warp[kScanThreads / 32 - 1];
+    const uint32_t mine = x - sum + (warp > 0 ? s_warp[warp - 1] : 0);
+    if (tid == 0) {
+        unsigned long long excl = 0;
+        if (vid == 0) {
+            st_release_u64(&state[0], kFlagPre | (unsigned long long)total);
+        } else {
+            st_release_u64(&state[vid], kFlagAgg | (unsigned long long)total);
+            int64_t j = vid - 1;
+            uint32_t spins = 0;
+            while (j >= 0) {
+                const unsigned long long s = ld_acquire_u64(&state[j]);
+                const unsigned long long flag = s & ~kValMask;
+                if (flag == 0) {
+                    if (++spins > kSpinLimit) {
+                        atomicAdd(&st->timeouts, 1u);
+                        break;
+                    }
+                    continue;
+                }
+                excl += s & kValMask;
+                if (flag == kFlagPre) break;
+                --j;
+            }
+            st_release_u64(&state[vid], kFlagPre | (excl + total));
+        }
+        s_excl = excl;
+        if (vid == nblocks - 1) *total_out = excl + total;
+    }
+    __syncthreads();
+    unsigned long long run = s_excl + mine;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        // offsets beyond 2^32 are clamped; such a buffer overflows its capacity anyway
+        if (base + i < n) offsets[base + i] = (uint32_t)(run < 0xffffffffull ? run : 0xffffffffull);
+        run += v[i];
+    }
+}
+
+__global__ void tile_item_count_kernel(const uint2 *__restrict__ ranges, int n_tiles, uint32_t *__restrict__ nitems) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n_tiles) {
+        const uint32_t len = ranges[t].y - ranges[t].x;
+        nitems[t] = (len + kItemFans - 1) / kItemFans;
+    }
+}
+
+__global__ void tile_item_emit_kernel(const uint2 *__restrict__ ranges, int n_tiles, const uint32_t *__restrict__ nitems,
+                                      const uint32_t *__restrict__ ibase, uint4 *__restrict__ items, int64_t max_items,
+                                      Status *st, unsigned long long frag_cap) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t == 0) {
+        const unsigned long long ni = st->items_total;
+        st->n_items = (unsigned)(ni < (unsigned long long)max_items ? ni : (unsigned long long)max_items);
+        st->frag_cap = frag_cap;
+    }
+    if (t >= n_tiles) return;
+    const uint2 r = ranges[t];
+    const uint32_t n = nitems[t], b = ibase[t];
+    for (uint32_t k = 0; k < n; ++k)
+        if (b + k < (uint64_t)max_items)
+            items[b + k] = make_uint4((uint32_t)t, r.x + k * kItemFans, min(r.y, r.x + (k + 1) * kItemFans), k);
+}
+
+// Per tile: exclusive prefix of the (item, pixel) counts over the tile's items, and the
+// pixel totals.  One block per tile, one thread per pixel; loads are issued four items
+// at a time so a tile with many items is not latency-bound.
+template <int TILE>
+__global__ void __launch_bounds__(TILE *TILE) item_prefix_kernel(const uint32_t *__restrict__ nitems,
+                                                                 const uint32_t *__restrict__ ibase, int tiles_x,
+                                                                 int W, int H, uint32_t *__restrict__ icnt,
+                                                                 uint32_t *__restrict__ counts) {
+    const int t = blockIdx.x, i = threadIdx.x;
+    const uint32_t n = nitems[t], b = ibase[t];
+    uint32_t *c = icnt + (size_t)b * TILE * TILE + i;
+    uint32_t run = 0;
+    uint32_t k = 0;
+    for (; k + 4 <= n; k += 4) {
+        const uint32_t v0 = c[(size_t)k * TILE * TILE], v1 = c[(size_t)(k + 1) * TILE * TILE];
+        const uint32_t v2 = c[(size_t)(k + 2) * TILE * TILE], v3 = c[(size_t)(k + 3) * TILE * TILE];
+        c[(size_t)k * TILE * TILE] = run;
+        c[(size_t)(k + 1) * TILE * TILE] = run + v0;
+        c[(size_t)(k + 2) * TILE * TILE] = run + v0 + v1;
+        c[(size_t)(k + 3) * TILE * TILE] = run + v0 + v1 + v2;
+        run += v0 + v1 + v2 + v3;
+    }
+    for (; k < n; ++k) {
+        const uint32_t v = c[(size_t)k * TILE * TILE];
+        c[(size_t)k * TILE * TILE] = run;
+        run += v;
+    }
+    const int x = (t % tiles_x) * TILE + (i % TILE), y = (t / tiles_x) * TILE + (i / TILE);
+    if (x < W && y < H) counts[(size_t)y * W + x] = run;
+}
+
+template <int TILE, int KT, bool FILL>
+cudaError_t launch_t(const RastArgs &ra, int64_t max_items, int K, cudaStream_t st) {
+    constexpr int STG = FILL ? 16 : 32;
+    const size_t smem = kRastWarps * warp_smem_bytes<TILE, STG, FILL>(K);
+    auto fn = raster_kernel<TILE, STG, KT, FILL>;
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    fn<<<(unsigned)((max_items + kRastWarps - 1) / kRastWarps), kRastWarps * 32, smem, st>>>(ra);
+    return cudaGetLastError();
+}
+
+template <bool FILL>
+cudaError_t launch_dispatch(const RastArgs &ra, const RenderLayout &L, int K, cudaStream_t st) {
+    if (L.tile == 8) {
+        if (K == 8) return launch_t<8, 8, FILL>(ra, L.max_items, K, st);
+        if (K == 6) return launch_t<8, 6, FILL>(ra, L.max_items, K, st);
+        return launch_t<8, 0, FILL>(ra, L.max_items, K, st);
+    }
+    if (K == 8) return launch_t<16, 8, FILL>(ra, L.max_items, K, st);
+    if (K == 6) return launch_t<16, 6, FILL>(ra, L.max_items, K, st);
+    return launch_t<16, 0, FILL>(ra, L.max_items, K, st);
+}
+
+RastArgs make_args(const RenderArgs &ra) {
+    const RenderLayout &L = ra.L;
+    RastArgs a;
+    a.sc.xyz = ra.xyz;
+    a.sc.rgb = ra.rgb;
+    a.sc.alpha = ra.alpha;
+    a.sc.K = ra.K;
+    a.sc.cam = make_cam(*ra.cam);
+    a.sc.W = ra.cam->width;
+    a.sc.H = ra.cam->height;
+    a.tiles_x = L.tiles_x;
+    a.depth_bits = L.depth_bits;
+    a.keys = reinterpret_cast<const unsigned long long *>(ra.ws + (L.passes & 1 ? L.off_keys1 : L.off_keys0));
+    a.vals = reinterpret_cast<const uint32_t *>(ra.ws + (L.passes & 1 ? L.off_vals1 : L.off_vals0));
+    a.items = reinterpret_cast<const uint4 *>(ra.ws + L.off_items);
+    a.icnt = reinterpret_cast<uint32_t *>(ra.ws + L.off_icnt);
+    a.offsets = reinterpret_cast<const uint32_t *>(ra.ws + L.off_offsets);
+    a.counts = reinterpret_cast<const uint32_t *>(ra.ws + L.off_counts);
+    a.frags = reinterpret_cast<float4 *>(ra.ws + L.off_frags);
+    a.frag_cap = L.frag_cap;
+    a.st = reinterpret_cast<Status *>(ra.ws + L.off_status);
+    return a;
+}
+
+}  // namespace
+
+cudaError_t launch_raster_count(const RenderArgs &ra, cudaStream_t st) {
+    const RenderLayout &L = ra.L;
+    char *ws = ra.ws;
+    Status *status = reinterpret_cast<Status *>(ws + L.off_status);
+    const RastArgs a = make_args(ra);
+    const uint2 *ranges = reinterpret_cast<const uint2 *>(ws + L.off_ranges);
+    uint32_t *nitems = reinterpret_cast<uint32_t *>(ws + L.off_tile_nitems);
+    uint32_t *ibase = reinterpret_cast<uint32_t *>(ws + L.off_tile_ibase);
+    const int tg = (L.n_tiles + 255) / 256;
+    tile_item_count_kernel<<<tg, 256, 0, st>>>(ranges, L.n_tiles, nitems);
+    scan_u32_kernel<<<(unsigned)L.tscan_blocks, kScanThreads, 0, st>>>(
+        nitems, ibase, L.n_tiles, L.tscan_blocks, reinterpret_cast<unsigned long long *>(ws + L.off_tscan_state),
+        &status->tscan_ticket, &status->items_total, status);
+    tile_item_emit_kernel<<<tg, 256, 0, st>>>(ranges, L.n_tiles, nitems, ibase,
+                                              reinterpret_cast<uint4 *>(ws + L.off_items), L.max_items, status,
+                                              (unsigned long long)L.frag_cap);
+    cudaError_t e = launch_dispatch<false>(a, L, ra.K, st);
+    if (e != cudaSuccess) return e;
+    if (L.tile == 8)
+        item_prefix_kernel<8><<<L.n_tiles, 64, 0, st>>>(nitems, ibase, L.tiles_x, ra.cam->width, ra.cam->height, a.icnt,
+                                                        reinterpret_cast<uint32_t *>(ws + L.off_counts));
+    else
+        item_prefix_kernel<16><<<L.n_tiles, 256, 0, st>>>(nitems, ibase, L.tiles_x, ra.cam->width, ra.cam->height,
+                                                          a.icnt, reinterpret_cast<uint32_t *>(ws + L.off_counts));
+    const int64_t n = (int64_t)ra.cam->width * ra.cam->height;
+    scan_u32_kernel<<<(unsigned)L.scan_blocks, kScanThreads, 0, st>>>(
+        reinterpret_cast<const uint32_t *>(ws + L.off_counts), reinterpret_cast<uint32_t *>(ws + L.off_offsets), n,
+        L.scan_blocks, reinterpret_cast<unsigned long long *>(ws + L.off_scan_state), &status->scan_ticket,
+        &status->frags, status);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) count_launches(6);
+    return e;
+}
+
+cudaError_t launch_raster(const RenderArgs &ra, bool fill, cudaStream_t st) {
+    const RenderLayout &L = ra.L;
+    if (L.n_tiles == 0) return cudaSuccess;
+    const RastArgs a = make_args(ra);
+    cudaError_t e = fill ? launch_dispatch<true>(a, L, ra.K, st) : launch_dispatch<false>(a, L, ra.K, st);
+    if (e == cudaSuccess) count_launches(1);
+    return e;
+}
+
+}  // namespace ms

@@ -1,0 +1,276 @@
+// Shared pieces of the rasterisation kernels: double-float projection of a fan
+// centre (value path), the shared-memory stage of a chunk of fans, and the per-pixel
+// coverage walk over a staged fan's K triangles with the binary32 decision formulas.
+#pragma once
+
+#include "fan_geom.cuh"
+#include "ms_internal.h"
+
+namespace ms {
+
+struct SceneDev {
+    const float *xyz, *rgb, *alpha;
+    int K;
+    CamDev cam;
+    int W, H;
+};
+
+// ------------------------------------------------------------------------------------
+// Double-float helpers (Knuth two-sum, FMA two-product)
+// ------------------------------------------------------------------------------------
+
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void two_prod(float a, float b, float &p, float &e) {
+    p = __fmul_rn(a, b);
+    e = fmaf(a, b, -p);
+}
+// Row of R_cw applied to (d_hi + d_lo), as hi + lo.
+__device__ __forceinline__ void df_dot(const float *R, const float dh[3], const float dl[3], float &h, float &l) {
+    float p0, q0, p1, q1, p2, q2, s, e1, e2;
+    two_prod(R[0], dh[0], p0, q0);
+    two_prod(R[1], dh[1], p1, q1);
+    two_prod(R[2], dh[2], p2, q2);
+    two_sum(p0, p1, s, e1);
+    two_sum(s, p2, h, e2);
+    l = ((e1 + e2) + (q0 + q1 + q2)) + (R[0] * dl[0] + R[1] * dl[1] + R[2] * dl[2]);
+}
+// f * (X / Z) + c as hi + lo, with X, Z given as hi + lo.
+__device__ __forceinline__ void df_screen(float Xh, float Xl, float Zh, float Zl, float f, float c, float &h,
+                                          float &l) {
+    const float q1 = Xh / Zh;
+    const float r = fmaf(-q1, Zh, Xh) + (Xl - q1 * Zl);
+    const float q2 = r / Zh;
+    float a1, a2, e;
+    two_prod(f, q1, a1, a2);
+    a2 = fmaf(f, q2, a2);
+    two_sum(a1, c, h, e);
+    l = e + a2;
+}
+
+// View-space centre of a fan (hi parts) and its double-float screen position.  The
+// other vertices are placed by their exact world offsets from the centre, so screen
+// positions relative to a pixel carry ~1e-6 px error instead of the ~1e-4 px of a
+// plain binary32 projection at 1080p.
+struct CentreProj {
+    float Xh, Yh, Zh;
+    float xh, xl, yh, yl;
+};
+__device__ __forceinline__ CentreProj project_centre(const CamDev &c, const float m[3]) {
+    float dh[3], dl[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) two_sum(m[r], -c.C[r], dh[r], dl[r]);
+    float Xl, Yl, Zl;
+    CentreProj o;
+    df_dot(c.R, dh, dl, o.Xh, Xl);
+    df_dot(c.R + 3, dh, dl, o.Yh, Yl);
+    df_dot(c.R + 6, dh, dl, o.Zh, Zl);
+    df_screen(o.Xh, Xl, o.Zh, Zl, c.fx, c.cx, o.xh, o.xl);
+    df_screen(o.Yh, Yl, o.Zh, Zl, c.fy, c.cy, o.yh, o.yl);
+    return o;
+}
+__device__ __forceinline__ void vertex_offset(const CamDev &c, const CentreProj &cp, const float d[3], float &du,
+                                              float &dv, float &X, float &Y, float &Z) {
+    const float dX = c.R[0] * d[0] + c.R[1] * d[1] + c.R[2] * d[2];
+    const float dY = c.R[3] * d[0] + c.R[4] * d[1] + c.R[5] * d[2];
+    const float dZ = c.R[6] * d[0] + c.R[7] * d[1] + c.R[8] * d[2];
+    X = cp.Xh + dX;
+    Y = cp.Yh + dY;
+    Z = cp.Zh + dZ;
+    const float den = 1.0f / (Z * cp.Zh);
+    du = c.fx * (dX * cp.Zh - cp.Xh * dZ) * den;
+    dv = c.fy * (dY * cp.Zh - cp.Yh * dZ) * den;
+}
+
+// ------------------------------------------------------------------------------------
+// Shared-memory stage (structure of arrays over CH slots)
+// ------------------------------------------------------------------------------------
+
+struct Stage {
+    int4 *rect;                   // [CH] i0, i1, j0, j1
+    uint32_t *flags;              // [CH] bits 0..15 valid triangle, 16..31 negative orientation
+    uint32_t *q;                  // [CH] quantised depth bound
+    uint32_t *fan;                // [CH] fan id
+    uint32_t *stie, *rtie;        // [CH] top-left tie bits of the spoke / rim directions
+    float *vx, *vy, *vz, *viz;    // [KV][CH] decided vertices
+    float *sdx, *sdy;             // [K][CH] spoke directions b_i - c
+    float *rdx, *rdy;             // [K][CH] rim directions, lower index to higher
+    float *area;                  // [K][CH] |area2|
+    float *cxh, *cxl, *cyh, *cyl; // [CH] double-float screen position of the centre (values)
+    float *du, *dv;               // [K][CH] screen offsets of the boundary vertices (values)
+    float *cr, *cg, *cb, *ca;     // [KV][CH] vertex colour and opacity (values)
+};
+
+__host__ __device__ __forceinline__ size_t stage_bytes(int CH, int K, bool values) {
+    const int dec = 4 * (K + 1) + 5 * K;
+    const int val = values ? 4 + 2 * K + 4 * (K + 1) : 0;
+    return (size_t)CH * (16 + 20 + 4 * (dec + val));
+}
+
+__device__ __forceinline__ Stage stage_ptrs(char *base, int CH, int K, bool values) {
+    const int KV = K + 1;
+    Stage s;
+    s.rect = reinterpret_cast<int4 *>(base);
+    s.flags = reinterpret_cast<uint32_t *>(s.rect + CH);
+    s.q = s.flags + CH;
+    s.fan = s.q + CH;
+    s.stie = s.fan + CH;
+    s.rtie = s.stie + CH;
+    float *f = reinterpret_cast<float *>(s.rtie + CH);
+    s.vx = f; f += KV * CH;
+    s.vy = f; f += KV * CH;
+    s.vz = f; f += KV * CH;
+    s.viz = f; f += KV * CH;
+    s.sdx = f; f += K * CH;
+    s.sdy = f; f += K * CH;
+    s.rdx = f; f += K * CH;
+    s.rdy = f; f += K * CH;
+    s.area = f; f += K * CH;
+    if (values) {
+        s.cxh = f; f += CH;
+        s.cxl = f; f += CH;
+        s.cyh = f; f += CH;
+        s.cyl = f; f += CH;
+        s.du = f; f += K * CH;
+        s.dv = f; f += K * CH;
+        s.cr = f; f += KV * CH;
+        s.cg = f; f += KV * CH;
+        s.cb = f; f += KV * CH;
+        s.ca = f;
+    }
+    return s;
+}
+
+__device__ __forceinline__ void stage_fan(const SceneDev &a, const Stage &s, int CH, int K, int slot, uint32_t fan,
+                                          uint32_t q, bool values) {
+    const int KV = K + 1;
+    const float *p = a.xyz + (size_t)fan * KV * 3;
+    uint32_t vmask = 0;
+    for (int k = 0; k < KV; ++k) {
+        const DVert d = decide_vertex(a.cam, __ldg(p + 3 * k), __ldg(p + 3 * k + 1), __ldg(p + 3 * k + 2));
+        s.vx[k * CH + slot] = d.xs;
+        s.vy[k * CH + slot] = d.ys;
+        s.vz[k * CH + slot] = d.Z;
+        s.viz[k * CH + slot] = d.iz;
+        if (d.valid) vmask |= 1u << k;
+    }
+    const uint32_t tmask = tri_valid_mask(vmask, K);
+    float mnx = 3.0e38f, mxx = -3.0e38f, mny = 3.0e38f, mxy = -3.0e38f;
+    for (int k = 0; k < KV; ++k) {
+        if (!vertex_used(tmask, k, K)) continue;
+        const float x = s.vx[k * CH + slot], y = s.vy[k * CH + slot];
+        mnx = fminf(mnx, x); mxx = fmaxf(mxx, x);
+        mny = fminf(mny, y); mxy = fmaxf(mxy, y);
+    }
+    const FanRect r = rect_from_bounds(mnx, mxx, mny, mxy, a.W, a.H);
+    const float xc = s.vx[slot], yc = s.vy[slot];
+    uint32_t flags = 0, stie = 0, rtie = 0;
+    for (int j = 0; j < K; ++j) {
+        const int b = 1 + j, c = 1 + (j + 1 == K ? 0 : j + 1);
+        const float xb = s.vx[b * CH + slot], yb = s.vy[b * CH + slot];
+        const float xn = s.vx[c * CH + slot], yn = s.vy[c * CH + slot];
+        s.sdx[j * CH + slot] = __fsub_rn(xb, xc);
+        s.sdy[j * CH + slot] = __fsub_rn(yb, yc);
+        if (j + 1 == K) {   // rim (b_{K-1}, b_0): the lower index is b_0
+            s.rdx[j * CH + slot] = __fsub_rn(xb, xn);
+            s.rdy[j * CH + slot] = __fsub_rn(yb, yn);
+        } else {
+            s.rdx[j * CH + slot] = __fsub_rn(xn, xb);
+            s.rdy[j * CH + slot] = __fsub_rn(yn, yb);
+        }
+        const float ar = dec_area2(xc, yc, xb, yb, xn, yn);
+        s.area[j * CH + slot] = fabsf(ar);
+        if (((tmask >> j) & 1u) && ar != 0.0f) flags |= 1u << j;
+        if (ar < 0.0f) flags |= 1u << (16 + j);
+        // tie acceptance (E == 0) of each direction and of its reverse
+        const float sx = s.sdx[j * CH + slot], sy = s.sdy[j * CH + slot];
+        const float rx = s.rdx[j * CH + slot], ry = s.rdy[j * CH + slot];
+        if (sy < 0.0f || (sy == 0.0f && sx > 0.0f)) stie |= 1u << j;
+        if (sy > 0.0f || (sy == 0.0f && sx < 0.0f)) stie |= 1u << (16 + j);
+        if (ry < 0.0f || (ry == 0.0f && rx > 0.0f)) rtie |= 1u << j;
+        if (ry > 0.0f || (ry == 0.0f && rx < 0.0f)) rtie |= 1u << (16 + j);
+    }
+    s.stie[slot] = stie;
+    s.rtie[slot] = rtie;
+    s.flags[slot] = (tmask == 0 || r.empty) ? 0u : flags;
+    s.q[slot] = q;
+    s.fan[slot] = fan;
+    s.rect[slot] = make_int4(r.i0, r.i1, r.j0, r.j1);
+    if (!values) return;
+    const float m[3] = {__ldg(p), __ldg(p + 1), __ldg(p + 2)};
+    const CentreProj cp = project_centre(a.cam, m);
+    s.cxh[slot] = cp.xh;
+    s.cxl[slot] = cp.xl;
+    s.cyh[slot] = cp.yh;
+    s.cyl[slot] = cp.yl;
+    for (int i = 0; i < K; ++i) {
+        const float d[3] = {__ldg(p + 3 * (1 + i)) - m[0], __ldg(p + 3 * (1 + i) + 1) - m[1],
+                            __ldg(p + 3 * (1 + i) + 2) - m[2]};
+        float du, dv, X, Y, Z;
+        vertex_offset(a.cam, cp, d, du, dv, X, Y, Z);
+        s.du[i * CH + slot] = du;
+        s.dv[i * CH + slot] = dv;
+    }
+    const float *col = a.rgb + (size_t)fan * KV * 3;
+    const float *al = a.alpha + (size_t)fan * KV;
+    for (int k = 0; k < KV; ++k) {
+        s.cr[k * CH + slot] = __ldg(col + 3 * k);
+        s.cg[k * CH + slot] = __ldg(col + 3 * k + 1);
+        s.cb[k * CH + slot] = __ldg(col + 3 * k + 2);
+        s.ca[k * CH + slot] = __ldg(al + k);
+    }
+}
+
+// Coverage of pixel centre (pxc, pyc) by the K triangles of staged fan f.  For every
+// covered triangle j calls on_frag(j, jn, neg, E0, E1, E2) with the oriented edge values
+// (opposite P0 = centre, P1, P2 of the decision formulas).  Each spoke value is computed
+// once and turned into two pass bits (as the edge c -> b_i and as its reverse; the
+// top-left tie bit of each direction was staged), so a triangle's two spoke tests are a
+// bit test; only triangles passing both get the rim edge.  The result is the
+// conjunction of the three edge tests, as stated.
+template <int KT, class F>
+__device__ __forceinline__ void cover_fan(const Stage &S, int CH, int K, int f, uint32_t flags, float pxc, float pyc,
+                                          F &&on_frag) {
+    const float xc = S.vx[f], yc = S.vy[f];
+    const float qx = __fsub_rn(pxc, xc), qy = __fsub_rn(pyc, yc);
+    const uint32_t stie = S.stie[f];
+    uint32_t P = 0, N = 0;
+#pragma unroll(KT > 0 ? KT : 1)
+    for (int i = 0; i < K; ++i) {
+        const float Si = __fsub_rn(__fmul_rn(S.sdx[i * CH + f], qy), __fmul_rn(S.sdy[i * CH + f], qx));
+        const bool z = Si == 0.0f;
+        P |= (uint32_t)(Si > 0.0f || (z && ((stie >> i) & 1u))) << i;
+        N |= (uint32_t)(Si < 0.0f || (z && ((stie >> (16 + i)) & 1u))) << i;
+    }
+    const uint32_t full = (1u << K) - 1u;
+    const uint32_t Pn = ((P >> 1) | (P << (K - 1))) & full;   // bit j: spoke j+1
+    const uint32_t Nn = ((N >> 1) | (N << (K - 1))) & full;
+    const uint32_t negm = flags >> 16;
+    uint32_t cand = ((P & Nn & ~negm) | (N & Pn & negm)) & flags & full;
+    if (!cand) return;
+    const uint32_t rtie = S.rtie[f];
+    while (cand) {
+        const int j = __ffs(cand) - 1;
+        cand &= cand - 1;
+        const int jn = (j + 1 == K) ? 0 : j + 1;
+        const bool neg = (negm >> j) & 1u;
+        const bool wrap = (j + 1 == K);
+        const int lo = wrap ? 0 : j;
+        const float Rc = dec_edge(S.rdx[j * CH + f], S.rdy[j * CH + f], S.vx[(1 + lo) * CH + f],
+                                  S.vy[(1 + lo) * CH + f], pxc, pyc);
+        // oriented rim: b_j -> b_{j+1} for positive orientation, reversed otherwise
+        const bool flip = wrap != neg;
+        const float E0 = flip ? -Rc : Rc;
+        if (E0 > 0.0f || (E0 == 0.0f && ((rtie >> (flip ? 16 + j : j)) & 1u))) {
+            const float Sj = __fsub_rn(__fmul_rn(S.sdx[j * CH + f], qy), __fmul_rn(S.sdy[j * CH + f], qx));
+            const float Sn = __fsub_rn(__fmul_rn(S.sdx[jn * CH + f], qy), __fmul_rn(S.sdy[jn * CH + f], qx));
+            const float E1 = neg ? -Sj : -Sn, E2 = neg ? Sn : Sj;
+            on_frag(j, jn, neg, E0, E1, E2);
+        }
+    }
+}
+
+}  // namespace ms
