@@ -203,6 +203,26 @@ MS_API ms_status ms_adam_step(float *xyz, float *rgb, float *alpha, const float 
                               float lr_color, float lr_xyz, float beta1, float beta2, float eps, void *stream);
 
 /*
+ * Forward render without a caller workspace.  The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory -- a plugin whose host
+ * application owns the GPU memory budget, code running while a stream is being captured
+ * into a CUDA graph (cudaMalloc cannot be captured), or a latency-critical loop that
+ * cannot afford cudaMalloc's implicit device synchronisation.  It behaves like
+ * ms_render (same inputs, output, camera and params; everything in device memory owned
+ * by the caller) but its scratch is a 32 MiB file-scope device array inside the library,
+ * held by every GPU that loads the library until the process exits.  Renders whose
+ * workspace (ms_render_workspace_size) exceeds 32 MiB are rejected with MS_ERR_INVALID
+ * and a message naming both sizes.  The first call on a device looks up the array's
+ * device address with that device current; make it before any stream capture.  All
+ * calls share the array: calls whose work overlaps on the GPU race.  The call waits for
+ * the stream, then reports device-side errors like ms_render_get_info and fills *info
+ * (optional).  It allocates nothing.
+ */
+MS_API ms_status ms_render_noalloc(const float *xyz, const float *rgb, const float *alpha, int64_t n_fans, int32_t K,
+                                   const ms_camera *cam, const ms_render_params *params, float *out_rgba,
+                                   ms_render_info *info, void *stream);
+
+/*
  * Optional stage profiler (host-side instrumentation, not part of the method).  While
  * enabled, every entry point records a CUDA event pair around each of its stages on
  * the caller's stream.  ms_profile_read waits for those events, writes the summed

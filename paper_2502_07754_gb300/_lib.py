@@ -57,6 +57,7 @@ _SIGS = {
     "ms_l1_loss": (C.c_int, [_P, _P, C.c_int64, _P, _P, _P]),
     "ms_adam_step": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, C.c_int64, C.c_int32, C.c_float, C.c_float, C.c_float,
                                C.c_float, C.c_float, _P]),
+    "ms_render_noalloc": (C.c_int, [_P, _P, _P, C.c_int64, C.c_int32, _P, _P, _P, _P, _P]),
     "ms_profile_enable": (None, [C.c_int32]),
     "ms_profile_read": (C.c_int, [_P, _P, C.c_int32]),
     "ms_kernel_launches": (C.c_int64, []),

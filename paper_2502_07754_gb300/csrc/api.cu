@@ -23,6 +23,14 @@ static ms_status fail(ms_status s, const char *fmt, ...) {
     return s;
 }
 
+ms_status set_error(ms_status s, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return s;
+}
+
 static ms_status cuda_fail(cudaError_t e, const char *what) {
     return fail(MS_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }

@@ -60,6 +60,9 @@ cudaError_t launch_raster_count(const RenderArgs &a, cudaStream_t st);   // item
 cudaError_t launch_resolve(const RenderArgs &a, bool backward, cudaStream_t st);
 cudaError_t launch_grad_scatter(const RenderArgs &a, cudaStream_t st);
 
+// Records a host-side error message for ms_last_error() (api.cu).
+ms_status set_error(ms_status s, const char *fmt, ...);
+
 // Launch accounting and optional stage events (api.cu).
 void count_launches(int n);
 struct StageScope {
