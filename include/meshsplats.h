@@ -92,7 +92,7 @@ typedef struct {
     float bg[3];            /* background colour */
     int64_t pair_capacity;  /* (tile, fan) pair capacity of the workspace; 0 = default */
     int32_t depth_bits;     /* depth bits in the sort key, 8..31 (0 = default 27) */
-    int64_t frag_capacity;  /* per-pixel fragment records of the workspace; 0 = 16 W H + 65536 */
+    int64_t frag_capacity;  /* per-pixel fragment records of the workspace; 0 = 8 W H + 65536 */
 } ms_render_params;
 
 /* Device-side outcome of the last ms_render / ms_render_backward on a workspace. */
@@ -209,9 +209,9 @@ MS_API ms_status ms_adam_step(float *xyz, float *rgb, float *alpha, const float 
  * into a CUDA graph (cudaMalloc cannot be captured), or a latency-critical loop that
  * cannot afford cudaMalloc's implicit device synchronisation.  It behaves like
  * ms_render (same inputs, output, camera and params; everything in device memory owned
- * by the caller) but its scratch is a 32 MiB file-scope device array inside the library,
+ * by the caller) but its scratch is a 64 MiB file-scope device array inside the library,
  * held by every GPU that loads the library until the process exits.  Renders whose
- * workspace (ms_render_workspace_size) exceeds 32 MiB are rejected with MS_ERR_INVALID
+ * workspace (ms_render_workspace_size) exceeds 64 MiB are rejected with MS_ERR_INVALID
  * and a message naming both sizes.  The first call on a device looks up the array's
  * device address with that device current; make it before any stream capture.  All
  * calls share the array: calls whose work overlaps on the GPU race.  The call waits for

@@ -106,7 +106,7 @@ RenderLayout render_layout(int64_t n_fans, int K, const ms_camera &cam, const ms
     L.cap = cap;
     const size_t npx = (size_t)cam.width * cam.height;
     int64_t fcap = p.frag_capacity;
-    if (fcap <= 0) fcap = 16 * (int64_t)npx + 65536;
+    if (fcap <= 0) fcap = 8 * (int64_t)npx + 65536;
     L.frag_cap = fcap;
     L.bin_blocks = (n_fans + 255) / 256;
     L.sort_blocks = (cap + 4095) / 4096;
@@ -131,7 +131,7 @@ RenderLayout render_layout(int64_t n_fans, int K, const ms_camera &cam, const ms
     L.off_icnt = o;              o = align_up(o + 4 * (size_t)L.max_items * p.tile * p.tile, 256);
     L.off_counts = o;            o = align_up(o + 4 * npx, 256);
     L.off_offsets = o;           o = align_up(o + 4 * npx, 256);
-    L.off_frags = o;             o = align_up(o + 32 * (size_t)fcap, 256);
+    L.off_frags = o;             o = align_up(o + 16 * kRecBwd * (size_t)fcap, 256);
     L.off_tfinal = o;            o = align_up(o + 4 * npx, 256);
     L.off_ncommit = o;           o = align_up(o + 4 * npx, 256);
     L.off_grad = o;              o = align_up(o + 32 * (size_t)L.V, 256);
@@ -305,7 +305,7 @@ MS_API ms_status ms_render_backward(const float *xyz, const float *rgb, const fl
     a.ws = ws; a.out_fwd = out_rgba; a.dL = dL_drgba; a.d_xyz = d_xyz; a.d_rgb = d_rgb; a.d_alpha = d_alpha;
     // the fragment records are regenerated from the sorted tile lists (not kept from the
     // forward); transmittance is recomputed during the resolve
-    if ((e = launch_raster(a, true, st)) != cudaSuccess) return cuda_fail(e, "raster fill launch");
+    if ((e = launch_raster_fill_bwd(a, st)) != cudaSuccess) return cuda_fail(e, "raster fill launch");
     if ((e = launch_resolve(a, true, st)) != cudaSuccess) return cuda_fail(e, "resolve backward launch");
     if ((e = launch_grad_scatter(a, st)) != cudaSuccess) return cuda_fail(e, "gradient scatter launch");
     count_launches(1 + (L.V > 0 ? 1 : 0));   // resolve, scatter (the fill counts itself)

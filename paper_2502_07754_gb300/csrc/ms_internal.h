@@ -57,6 +57,8 @@ constexpr int kItemFans = 64;   // fans per raster work item
 
 cudaError_t launch_raster(const RenderArgs &a, bool fill, cudaStream_t st);
 cudaError_t launch_raster_count(const RenderArgs &a, cudaStream_t st);   // items, count, prefix, pixel scan
+cudaError_t launch_raster_fill_bwd(const RenderArgs &a, cudaStream_t st);   // records of the adjoint
+constexpr int kRecFwd = 2, kRecBwd = 10;   // float4s per fragment record (forward / adjoint)
 cudaError_t launch_resolve(const RenderArgs &a, bool backward, cudaStream_t st);
 cudaError_t launch_grad_scatter(const RenderArgs &a, cudaStream_t st);
 

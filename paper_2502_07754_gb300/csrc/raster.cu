@@ -36,13 +36,20 @@ struct RastArgs {
 
 constexpr int kRastWarps = 4;   // warps (work items) per block
 
-template <int TILE, int STG, bool FILL>
+// Pass kinds: count fragments; fill their 32-byte forward records; fill the 160-byte
+// records of the adjoint, which add everything the chain rule to the vertices needs
+// (barycentrics, screen offsets, view coordinates, vertex attributes), so the backward
+// resolve never gathers vertex data from global memory.
+enum RasterMode { kCount = 0, kFill = 1, kFillBwd = 2 };
+
+template <int TILE, int STG, int MODE>
 __host__ __device__ __forceinline__ size_t warp_smem_bytes(int K) {
-    return (size_t)TILE * TILE * 4 * (FILL ? 2 : 1) + stage_bytes(STG, K, FILL);
+    return (size_t)TILE * TILE * 4 * (MODE != kCount ? 2 : 1) + stage_bytes(STG, K, MODE);
 }
 
-template <int TILE, int STG, int KT, bool FILL>
+template <int TILE, int STG, int KT, int MODE>
 __global__ void __launch_bounds__(kRastWarps * 32) raster_kernel(RastArgs a) {
+    constexpr bool FILL = MODE != kCount;   // passes that address records
     extern __shared__ __align__(16) char smem[];
     const int K = KT > 0 ? KT : a.sc.K;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -50,10 +57,10 @@ __global__ void __launch_bounds__(kRastWarps * 32) raster_kernel(RastArgs a) {
     if (item >= a.st->n_items) return;   // whole warp; nothing below synchronises the block
     const uint4 it = a.items[item];
     const int tile = (int)it.x;
-    char *mine = smem + (size_t)warp * warp_smem_bytes<TILE, STG, FILL>(K);
+    char *mine = smem + (size_t)warp * warp_smem_bytes<TILE, STG, MODE>(K);
     uint32_t *s_cnt = reinterpret_cast<uint32_t *>(mine);   // [TILE*TILE] fragments so far
     uint32_t *s_base = s_cnt + TILE * TILE;                   // [TILE*TILE] record offsets (fill)
-    const Stage S = stage_ptrs(mine + (size_t)TILE * TILE * 4 * (FILL ? 2 : 1), STG, K, FILL);
+    const Stage S = stage_ptrs(mine + (size_t)TILE * TILE * 4 * (FILL ? 2 : 1), STG, K, MODE);
     const int tx0 = (tile % a.tiles_x) * TILE, ty0 = (tile / a.tiles_x) * TILE;
     const int tx1 = min(tx0 + TILE, a.sc.W) - 1, ty1 = min(ty0 + TILE, a.sc.H) - 1;
     uint32_t *icnt = a.icnt + (size_t)item * TILE * TILE;
@@ -78,7 +85,7 @@ __global__ void __launch_bounds__(kRastWarps * 32) raster_kernel(RastArgs a) {
         if (lane < cnt) {
             const uint32_t li = cb + lane;
             const uint32_t q = (uint32_t)(__ldg(a.keys + li) & ((1ull << a.depth_bits) - 1ull));
-            stage_fan(a.sc, S, STG, K, lane, __ldg(a.vals + li), q, FILL);
+            stage_fan(a.sc, S, STG, K, lane, __ldg(a.vals + li), q, MODE);
         }
         __syncwarp();
         for (int f = 0; f < cnt; ++f) {
@@ -101,7 +108,7 @@ __global__ void __launch_bounds__(kRastWarps * 32) raster_kernel(RastArgs a) {
                                   [&](int j, int jn, bool neg, float E0, float E1, float E2) {
                         const uint32_t slot = s_cnt[lp]++;
                         ++c_frag;
-                        if (FILL) {
+                        if (MODE != kCount) {
                             const uint32_t b = s_base[lp];
                             if (b == 0xffffffffu) return;
                             const float izc = S.viz[f];
@@ -117,19 +124,30 @@ __global__ void __launch_bounds__(kRastWarps * 32) raster_kernel(RastArgs a) {
                             const float w0 = (ujx * uny - ujy * unx) * izc;
                             const float w1 = (unx * oy - uny * ox) * izj;
                             const float w2 = (ox * ujy - oy * ujx) * izn;
-                            const float iW = 1.0f / (w0 + w1 + w2);
+                            const float Wsum = w0 + w1 + w2;
+                            const float iW = 1.0f / Wsum;
                             const float m0 = w0 * iW, m1 = w1 * iW, m2 = w2 * iW;
-                            const int vj = (1 + j) * STG + f, vn = (1 + jn) * STG + f;
-                            const float al = m0 * S.ca[f] + m1 * S.ca[vj] + m2 * S.ca[vn];
-                            const float c0 = m0 * S.cr[f] + m1 * S.cr[vj] + m2 * S.cr[vn];
-                            const float c1 = m0 * S.cg[f] + m1 * S.cg[vj] + m2 * S.cg[vn];
-                            const float c2 = m0 * S.cb[f] + m1 * S.cb[vj] + m2 * S.cb[vn];
+                            const int vc = f, vj = (1 + j) * STG + f, vn = (1 + jn) * STG + f;
+                            const float al = m0 * S.ca[vc] + m1 * S.ca[vj] + m2 * S.ca[vn];
+                            const float c0 = m0 * S.cr[vc] + m1 * S.cr[vj] + m2 * S.cr[vn];
+                            const float c1 = m0 * S.cg[vc] + m1 * S.cg[vj] + m2 * S.cg[vn];
+                            const float c2 = m0 * S.cb[vc] + m1 * S.cb[vj] + m2 * S.cb[vn];
                             const uint32_t tri = S.fan[f] * (uint32_t)K + (uint32_t)j;
-                            float4 *rec = a.frags + 2 * ((size_t)b + slot);
+                            float4 *rec = a.frags + (size_t)(MODE == kFill ? kRecFwd : kRecBwd) * ((size_t)b + slot);
                             rec[0] = make_float4(zf, __uint_as_float(tri), __uint_as_float(S.q[f]), al);
                             rec[1] = make_float4(c0, c1, c2, 0.0f);
-                        }
-                    });
+                            if (MODE == kFillBwd) {
+                                const float iz0 = 1.0f / S.vZ[vc], iz1 = 1.0f / S.vZ[vj], iz2 = 1.0f / S.vZ[vn];
+                                rec[2] = make_float4(m0, m1, m2, Wsum);
+                                rec[3] = make_float4(ox, oy, ujx, ujy);
+                                rec[4] = make_float4(unx, uny, iz0, iz1);
+                                rec[5] = make_float4(iz2, S.vX[vc], S.vY[vc], S.vX[vj]);
+                                rec[6] = make_float4(S.vY[vj], S.vX[vn], S.vY[vn], S.ca[vc]);
+                                rec[7] = make_float4(S.ca[vj], S.ca[vn], S.cr[vc], S.cg[vc]);
+                                rec[8] = make_float4(S.cb[vc], S.cr[vj], S.cg[vj], S.cb[vj]);
+                                rec[9] = make_float4(S.cr[vn], S.cg[vn], S.cb[vn], 0.0f);
+                            }
+                        }                    });
                 }
                 __syncwarp();   // a later fan may append to the same pixel from another lane
             }
@@ -285,26 +303,26 @@ __global__ void __launch_bounds__(TILE *TILE) item_prefix_kernel(const uint32_t 
     if (x < W && y < H) counts[(size_t)y * W + x] = run;
 }
 
-template <int TILE, int KT, bool FILL>
+template <int TILE, int KT, int MODE>
 cudaError_t launch_t(const RastArgs &ra, int64_t max_items, int K, cudaStream_t st) {
-    constexpr int STG = FILL ? 16 : 32;
-    const size_t smem = kRastWarps * warp_smem_bytes<TILE, STG, FILL>(K);
-    auto fn = raster_kernel<TILE, STG, KT, FILL>;
+    constexpr int STG = MODE == kCount ? 32 : 16;
+    const size_t smem = kRastWarps * warp_smem_bytes<TILE, STG, MODE>(K);
+    auto fn = raster_kernel<TILE, STG, KT, MODE>;
     cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     fn<<<(unsigned)((max_items + kRastWarps - 1) / kRastWarps), kRastWarps * 32, smem, st>>>(ra);
     return cudaGetLastError();
 }
 
-template <bool FILL>
+template <int MODE>
 cudaError_t launch_dispatch(const RastArgs &ra, const RenderLayout &L, int K, cudaStream_t st) {
     if (L.tile == 8) {
-        if (K == 8) return launch_t<8, 8, FILL>(ra, L.max_items, K, st);
-        if (K == 6) return launch_t<8, 6, FILL>(ra, L.max_items, K, st);
-        return launch_t<8, 0, FILL>(ra, L.max_items, K, st);
+        if (K == 8) return launch_t<8, 8, MODE>(ra, L.max_items, K, st);
+        if (K == 6) return launch_t<8, 6, MODE>(ra, L.max_items, K, st);
+        return launch_t<8, 0, MODE>(ra, L.max_items, K, st);
     }
-    if (K == 8) return launch_t<16, 8, FILL>(ra, L.max_items, K, st);
-    if (K == 6) return launch_t<16, 6, FILL>(ra, L.max_items, K, st);
-    return launch_t<16, 0, FILL>(ra, L.max_items, K, st);
+    if (K == 8) return launch_t<16, 8, MODE>(ra, L.max_items, K, st);
+    if (K == 6) return launch_t<16, 6, MODE>(ra, L.max_items, K, st);
+    return launch_t<16, 0, MODE>(ra, L.max_items, K, st);
 }
 
 RastArgs make_args(const RenderArgs &ra) {
@@ -349,7 +367,7 @@ cudaError_t launch_raster_count(const RenderArgs &ra, cudaStream_t st) {
     tile_item_emit_kernel<<<tg, 256, 0, st>>>(ranges, L.n_tiles, nitems, ibase,
                                               reinterpret_cast<uint4 *>(ws + L.off_items), L.max_items, status,
                                               (unsigned long long)L.frag_cap);
-    cudaError_t e = launch_dispatch<false>(a, L, ra.K, st);
+    cudaError_t e = launch_dispatch<kCount>(a, L, ra.K, st);
     if (e != cudaSuccess) return e;
     if (L.tile == 8)
         item_prefix_kernel<8><<<L.n_tiles, 64, 0, st>>>(nitems, ibase, L.tiles_x, ra.cam->width, ra.cam->height, a.icnt,
@@ -371,7 +389,16 @@ cudaError_t launch_raster(const RenderArgs &ra, bool fill, cudaStream_t st) {
     const RenderLayout &L = ra.L;
     if (L.n_tiles == 0) return cudaSuccess;
     const RastArgs a = make_args(ra);
-    cudaError_t e = fill ? launch_dispatch<true>(a, L, ra.K, st) : launch_dispatch<false>(a, L, ra.K, st);
+    cudaError_t e = fill ? launch_dispatch<kFill>(a, L, ra.K, st) : launch_dispatch<kCount>(a, L, ra.K, st);
+    if (e == cudaSuccess) count_launches(1);
+    return e;
+}
+
+cudaError_t launch_raster_fill_bwd(const RenderArgs &ra, cudaStream_t st) {
+    const RenderLayout &L = ra.L;
+    if (L.n_tiles == 0) return cudaSuccess;
+    const RastArgs a = make_args(ra);
+    cudaError_t e = launch_dispatch<kFillBwd>(a, L, ra.K, st);
     if (e == cudaSuccess) count_launches(1);
     return e;
 }

@@ -102,15 +102,21 @@ struct Stage {
     float *cxh, *cxl, *cyh, *cyl; // [CH] double-float screen position of the centre (values)
     float *du, *dv;               // [K][CH] screen offsets of the boundary vertices (values)
     float *cr, *cg, *cb, *ca;     // [KV][CH] vertex colour and opacity (values)
+    float *vX, *vY, *vZ;          // [KV][CH] view-space vertices (adjoint records)
 };
 
-__host__ __device__ __forceinline__ size_t stage_bytes(int CH, int K, bool values) {
+// What a stage holds: decisions only, + values (fill), + view coordinates (fill of the
+// adjoint's records).
+enum StageLevel { kStageDecide = 0, kStageValues = 1, kStageGrad = 2 };
+
+__host__ __device__ __forceinline__ size_t stage_bytes(int CH, int K, int level) {
     const int dec = 4 * (K + 1) + 5 * K;
-    const int val = values ? 4 + 2 * K + 4 * (K + 1) : 0;
-    return (size_t)CH * (16 + 20 + 4 * (dec + val));
+    const int val = level >= kStageValues ? 4 + 2 * K + 4 * (K + 1) : 0;
+    const int grd = level >= kStageGrad ? 3 * (K + 1) : 0;
+    return (size_t)CH * (16 + 20 + 4 * (dec + val + grd));
 }
 
-__device__ __forceinline__ Stage stage_ptrs(char *base, int CH, int K, bool values) {
+__device__ __forceinline__ Stage stage_ptrs(char *base, int CH, int K, int level) {
     const int KV = K + 1;
     Stage s;
     s.rect = reinterpret_cast<int4 *>(base);
@@ -129,7 +135,7 @@ __device__ __forceinline__ Stage stage_ptrs(char *base, int CH, int K, bool valu
     s.rdx = f; f += K * CH;
     s.rdy = f; f += K * CH;
     s.area = f; f += K * CH;
-    if (values) {
+    if (level >= kStageValues) {
         s.cxh = f; f += CH;
         s.cxl = f; f += CH;
         s.cyh = f; f += CH;
@@ -139,13 +145,18 @@ __device__ __forceinline__ Stage stage_ptrs(char *base, int CH, int K, bool valu
         s.cr = f; f += KV * CH;
         s.cg = f; f += KV * CH;
         s.cb = f; f += KV * CH;
-        s.ca = f;
+        s.ca = f; f += KV * CH;
+    }
+    if (level >= kStageGrad) {
+        s.vX = f; f += KV * CH;
+        s.vY = f; f += KV * CH;
+        s.vZ = f;
     }
     return s;
 }
 
 __device__ __forceinline__ void stage_fan(const SceneDev &a, const Stage &s, int CH, int K, int slot, uint32_t fan,
-                                          uint32_t q, bool values) {
+                                          uint32_t q, int level) {
     const int KV = K + 1;
     const float *p = a.xyz + (size_t)fan * KV * 3;
     uint32_t vmask = 0;
@@ -199,7 +210,7 @@ __device__ __forceinline__ void stage_fan(const SceneDev &a, const Stage &s, int
     s.q[slot] = q;
     s.fan[slot] = fan;
     s.rect[slot] = make_int4(r.i0, r.i1, r.j0, r.j1);
-    if (!values) return;
+    if (level < kStageValues) return;
     const float m[3] = {__ldg(p), __ldg(p + 1), __ldg(p + 2)};
     const CentreProj cp = project_centre(a.cam, m);
     s.cxh[slot] = cp.xh;
@@ -213,6 +224,16 @@ __device__ __forceinline__ void stage_fan(const SceneDev &a, const Stage &s, int
         vertex_offset(a.cam, cp, d, du, dv, X, Y, Z);
         s.du[i * CH + slot] = du;
         s.dv[i * CH + slot] = dv;
+        if (level >= kStageGrad) {
+            s.vX[(1 + i) * CH + slot] = X;
+            s.vY[(1 + i) * CH + slot] = Y;
+            s.vZ[(1 + i) * CH + slot] = Z;
+        }
+    }
+    if (level >= kStageGrad) {
+        s.vX[slot] = cp.Xh;
+        s.vY[slot] = cp.Yh;
+        s.vZ[slot] = cp.Zh;
     }
     const float *col = a.rgb + (size_t)fan * KV * 3;
     const float *al = a.alpha + (size_t)fan * KV;

@@ -7,7 +7,7 @@
 // workspace that ms_render needs, so this entry point uses a file-scope device array
 // instead.  Inputs and the output image are still the caller's.
 //
-// The array is kNoAllocWorkspaceBytes (32 MiB).  Every GPU that loads this library
+// The array is kNoAllocWorkspaceBytes (64 MiB).  Every GPU that loads this library
 // holds it until the process exits.  Its device address is looked up once per device
 // (cudaGetSymbolAddress, with that device current) on the first call made on that
 // device; make that first call before any stream capture begins.  All calls share the
@@ -21,7 +21,7 @@
 namespace ms {
 namespace {
 
-constexpr size_t kNoAllocWorkspaceBytes = 32u << 20;
+constexpr size_t kNoAllocWorkspaceBytes = 64u << 20;
 constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_noalloc_ws[kNoAllocWorkspaceBytes];

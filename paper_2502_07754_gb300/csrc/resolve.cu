@@ -12,12 +12,11 @@
 // Compositing stops once the transmittance falls below T_eps.
 //
 // The backward replays the same order, stops after the forward's committed count,
-// and at each committed fragment f forms dC/dc_f = T_f a_f,
-// dC/da_f = T_f c_f - (C_out - C_{<=f}) / (1 - a_f), dA/da_f = T_out / (1 - a_f) from
-// the recomputed transmittance, then chains through the perspective-correct
-// barycentrics and the projection to world space; per-vertex gradients accumulate
-// with 16-byte vector atomics into a (xyz, alpha | rgb, 0) scratch, scattered to the
-// caller's arrays at the end.
+// and at each committed fragment f forms, from the recomputed transmittance T_f,
+// dC/dc_f = T_f a_f, dC/da_f = T_f c_f - (C_out - C_{<=f}) / (1 - a_f) and
+// dA/da_f = T_out / (1 - a_f), and chains dL/dc_f, dL/da_f to the vertices from the
+// fragment's adjoint record (filled by the rasteriser with everything the chain needs,
+// so no vertex data is gathered here).
 #include "raster_common.cuh"
 
 namespace ms {
@@ -27,7 +26,7 @@ namespace {
 struct ResolveArgs {
     SceneDev sc;
     const uint32_t *counts, *offsets;
-    const float4 *frags;
+    float4 *frags;
     int64_t frag_cap;
     int depth_bits;
     float T_eps, bg0, bg1, bg2;
@@ -39,93 +38,61 @@ struct ResolveArgs {
     float4 *grad;
 };
 
-// Geometry of a fragment recomputed from global memory (backward only).
-struct Frag {
-    uint32_t vid[3];     // centre, b_j, b_{j+1}
-    float X[3], Y[3], Z[3];
-    float ux[3], uy[3];  // screen position relative to the pixel centre
-    float E[3], W, mu[3];
-};
-
-__device__ __forceinline__ void frag_geometry(const SceneDev &a, uint32_t tri, float pxc, float pyc, Frag &f) {
-    const int K = a.K, KV = K + 1;
-    const uint32_t fan = tri / (uint32_t)K, j = tri - fan * (uint32_t)K;
-    f.vid[0] = fan * KV;
-    f.vid[1] = fan * KV + 1 + j;
-    f.vid[2] = fan * KV + 1 + (j + 1 == (uint32_t)K ? 0 : j + 1);
-    const CamDev &c = a.cam;
-    const float *pc = a.xyz + 3 * (size_t)f.vid[0];
-    const float m[3] = {__ldg(pc), __ldg(pc + 1), __ldg(pc + 2)};
-    const CentreProj cp = project_centre(c, m);
-    const float ocx = __fsub_rn(cp.xh, pxc) + cp.xl, ocy = __fsub_rn(cp.yh, pyc) + cp.yl;
-    f.X[0] = cp.Xh; f.Y[0] = cp.Yh; f.Z[0] = cp.Zh;
-    f.ux[0] = ocx; f.uy[0] = ocy;
-#pragma unroll
-    for (int k = 1; k < 3; ++k) {
-        const float *p = a.xyz + 3 * (size_t)f.vid[k];
-        const float d[3] = {__ldg(p) - m[0], __ldg(p + 1) - m[1], __ldg(p + 2) - m[2]};
-        float du, dv;
-        vertex_offset(c, cp, d, du, dv, f.X[k], f.Y[k], f.Z[k]);
-        f.ux[k] = ocx + du;
-        f.uy[k] = ocy + dv;
-    }
-    f.E[0] = f.ux[1] * f.uy[2] - f.uy[1] * f.ux[2];
-    f.E[1] = f.ux[2] * f.uy[0] - f.uy[2] * f.ux[0];
-    f.E[2] = f.ux[0] * f.uy[1] - f.uy[0] * f.ux[1];
-    float w[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) w[k] = f.E[k] / f.Z[k];
-    f.W = w[0] + w[1] + w[2];
-    const float iW = 1.0f / f.W;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) f.mu[k] = w[k] * iW;
-}
-
-// Adjoint of one fragment given dL/dc (3) and dL/da; accumulates per-vertex gradients.
-__device__ __forceinline__ void frag_backward(const SceneDev &a, float4 *grad, const Frag &f, const float gc[3],
-                                              float ga) {
-    const CamDev &c = a.cam;
-    float gmu[3];
+// Chain rule from one composited fragment's dL/dc (gc0..2) and dL/da (ga) to its three
+// vertices, using the adjoint record (barycentrics mu and their normaliser W, screen
+// offsets u from the pixel, 1/Z and view X, Y of the vertices, vertex attributes).
+// mu_k = w_k / W with w_k = E_k / Z_k, E_k = cross(u_a, u_b) for the edge opposite k;
+// screen position -> view space -> world space through R_cw^T.  Gradients go to the
+// (xyz, alpha | rgb, 0) scratch with two 16-byte vector atomics per vertex.
+__device__ __forceinline__ void chain_to_vertices(const ResolveArgs &a, const float4 *r, uint32_t tri, float gc0,
+                                                  float gc1, float gc2, float ga) {
+    const float4 r2 = r[2], r3 = r[3], r4 = r[4], r5 = r[5], r6 = r[6], r7 = r[7], r8 = r[8], r9 = r[9];
+    const float mu[3] = {r2.x, r2.y, r2.z};
+    const float iW = 1.0f / r2.w;
+    const float ux[3] = {r3.x, r3.z, r4.x}, uy[3] = {r3.y, r3.w, r4.y};
+    const float iz[3] = {r4.z, r4.w, r5.x};
+    const float X[3] = {r5.y, r5.w, r6.y}, Y[3] = {r5.z, r6.x, r6.z};
+    const float al[3] = {r6.w, r7.x, r7.y};
+    const float cr[3] = {r7.z, r8.y, r9.x}, cg[3] = {r7.w, r8.z, r9.y}, cb[3] = {r8.x, r8.w, r9.z};
+    float gmu[3], s = 0.0f;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        const float *col = a.rgb + 3 * (size_t)f.vid[k];
-        gmu[k] = gc[0] * __ldg(col) + gc[1] * __ldg(col + 1) + gc[2] * __ldg(col + 2) + ga * __ldg(a.alpha + f.vid[k]);
+        gmu[k] = gc0 * cr[k] + gc1 * cg[k] + gc2 * cb[k] + ga * al[k];
+        s += mu[k] * gmu[k];
     }
-    const float s = gmu[0] * f.mu[0] + gmu[1] * f.mu[1] + gmu[2] * f.mu[2];
-    const float iW = 1.0f / f.W;
-    float gE[3], gZ[3], gux[3] = {0, 0, 0}, guy[3] = {0, 0, 0};
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        const float gw = (gmu[k] - s) * iW;
-        gE[k] = gw / f.Z[k];
-        gZ[k] = -gw * f.E[k] / (f.Z[k] * f.Z[k]);
-    }
-    // E_k = ux_a uy_b - uy_a ux_b for (a, b) = (k+1, k+2) mod 3.
+    float gux[3] = {0, 0, 0}, guy[3] = {0, 0, 0}, gZ[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         const int ia = (k + 1) % 3, ib = (k + 2) % 3;
-        gux[ia] += gE[k] * f.uy[ib];
-        guy[ia] -= gE[k] * f.ux[ib];
-        guy[ib] += gE[k] * f.ux[ia];
-        gux[ib] -= gE[k] * f.uy[ia];
+        const float E = ux[ia] * uy[ib] - uy[ia] * ux[ib];
+        const float gw = (gmu[k] - s) * iW;
+        const float gE = gw * iz[k];
+        gZ[k] = -gw * E * iz[k] * iz[k];
+        gux[ia] += gE * uy[ib];
+        guy[ia] -= gE * ux[ib];
+        guy[ib] += gE * ux[ia];
+        gux[ib] -= gE * uy[ia];
     }
+    const int K = a.sc.K, KV = K + 1;
+    const uint32_t fan = tri / (uint32_t)K, j = tri - fan * (uint32_t)K;
+    const uint32_t vid[3] = {fan * KV, fan * KV + 1 + j, fan * KV + 1 + (j + 1 == (uint32_t)K ? 0 : j + 1)};
+    const CamDev &c = a.sc.cam;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        const float iz = 1.0f / f.Z[k];
-        const float gX = gux[k] * c.fx * iz;
-        const float gY = guy[k] * c.fy * iz;
-        const float gZv = gZ[k] - (gux[k] * c.fx * f.X[k] + guy[k] * c.fy * f.Y[k]) * iz * iz;
+        const float gX = gux[k] * c.fx * iz[k];
+        const float gY = guy[k] * c.fy * iz[k];
+        const float gZv = gZ[k] - (gux[k] * c.fx * X[k] + guy[k] * c.fy * Y[k]) * iz[k] * iz[k];
         float4 g0, g1;
         g0.x = c.R[0] * gX + c.R[3] * gY + c.R[6] * gZv;
         g0.y = c.R[1] * gX + c.R[4] * gY + c.R[7] * gZv;
         g0.z = c.R[2] * gX + c.R[5] * gY + c.R[8] * gZv;
-        g0.w = f.mu[k] * ga;
-        g1.x = f.mu[k] * gc[0];
-        g1.y = f.mu[k] * gc[1];
-        g1.z = f.mu[k] * gc[2];
+        g0.w = mu[k] * ga;
+        g1.x = mu[k] * gc0;
+        g1.y = mu[k] * gc1;
+        g1.z = mu[k] * gc2;
         g1.w = 0.0f;
-        atomicAdd(grad + 2 * (size_t)f.vid[k], g0);
-        atomicAdd(grad + 2 * (size_t)f.vid[k] + 1, g1);
+        atomicAdd(a.grad + 2 * (size_t)vid[k], g0);
+        atomicAdd(a.grad + 2 * (size_t)vid[k] + 1, g1);
     }
 }
 
@@ -144,7 +111,8 @@ __global__ void __launch_bounds__(256) resolve_kernel(ResolveArgs a) {
     int n = valid ? (int)a.counts[pix] : 0;
     const int64_t off = a.offsets[pix];
     if (off + n > a.frag_cap) n = 0;   // the buffer overflowed: reported through the status block
-    const float4 *rec = a.frags + 2 * off;
+    constexpr int RS = BWD ? kRecBwd : kRecFwd;   // float4s per record
+    float4 *rec = a.frags + (size_t)RS * off;
 
     float T = 1.0f, C0 = 0.0f, C1 = 0.0f, C2 = 0.0f;
     float kz[KB], kr[KB], kg[KB], kb[KB], ka[KB];
@@ -178,10 +146,7 @@ __global__ void __launch_bounds__(256) resolve_kernel(ResolveArgs a) {
             const float inv = 1.0f / fmaxf(1.0f - al, 1e-6f);
             const float ga = gR * (T * c0 - (oR - nC0) * inv) + gG * (T * c1 - (oG - nC1) * inv) +
                              gB * (T * c2 - (oB - nC2) * inv) + gA * Tout * inv;
-            const float gc[3] = {gR * w, gG * w, gB * w};
-            Frag f;
-            frag_geometry(a.sc, kt[0], pxc, pyc, f);
-            frag_backward(a.sc, a.grad, f, gc, ga);
+            chain_to_vertices(a, rec + (size_t)RS * ki[0], kt[0], gR * w, gG * w, gB * w, ga);
             C0 = nC0; C1 = nC1; C2 = nC2;
         } else {
             C0 += w * c0;
@@ -208,7 +173,7 @@ __global__ void __launch_bounds__(256) resolve_kernel(ResolveArgs a) {
     int start = 0;
     while (!done) {
         for (int i = start; i < n && !done; ++i) {
-            const float4 r0 = rec[2 * i];
+            const float4 r0 = rec[RS * i];
             const float z = r0.x;
             const uint32_t tri = __float_as_uint(r0.y), qk = __float_as_uint(r0.z);
             while (nb > 0 && !done && depth_q(kz[0], a.depth_bits) < qk) commit_front();
@@ -235,7 +200,7 @@ __global__ void __launch_bounds__(256) resolve_kernel(ResolveArgs a) {
                     continue;
                 }
             }
-            const float4 r1 = rec[2 * i + 1];
+            const float4 r1 = rec[RS * i + 1];
             bool placed = false;
 #pragma unroll
             for (int s = KB - 1; s >= 1; --s) {
@@ -315,7 +280,7 @@ cudaError_t launch_resolve(const RenderArgs &ra, bool backward, cudaStream_t st)
     a.sc.H = ra.cam->height;
     a.counts = reinterpret_cast<const uint32_t *>(ra.ws + L.off_counts);
     a.offsets = reinterpret_cast<const uint32_t *>(ra.ws + L.off_offsets);
-    a.frags = reinterpret_cast<const float4 *>(ra.ws + L.off_frags);
+    a.frags = reinterpret_cast<float4 *>(ra.ws + L.off_frags);
     a.frag_cap = L.frag_cap;
     a.depth_bits = L.depth_bits;
     a.T_eps = ra.prm.T_eps;

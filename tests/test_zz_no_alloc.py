@@ -1,7 +1,7 @@
 """ms_render_noalloc: the forward render for callers that cannot allocate device memory
 (a plugin inside a host application that owns the GPU memory budget, code running while
 a stream is captured into a CUDA graph, a loop that cannot afford cudaMalloc's implicit
-synchronisation).  Its scratch is a fixed 32 MiB array inside the library.  This file is
+synchronisation).  Its scratch is a fixed 64 MiB array inside the library.  This file is
 collected last on purpose: if it fails, a run that stops at the first failure has already
 run every other test."""
 import ctypes as C
