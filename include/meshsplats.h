@@ -181,8 +181,78 @@ MS_API ms_status ms_render_backward(const float *xyz, const float *rgb, const fl
                                     float *d_alpha, void *workspace, size_t ws_bytes, void *stream);
 
 /* Synchronises the stream and reads the device-side outcome recorded in the workspace.
- * Returns MS_ERR_CAPACITY or MS_ERR_TIMEOUT when the last render on it was invalid. */
+ * Returns MS_ERR_CAPACITY or MS_ERR_TIMEOUT when the last render (single or batch) on it
+ * was invalid; the counters then cover all views of a batch together. */
 MS_API ms_status ms_render_get_info(const void *workspace, ms_render_info *info, void *stream);
+
+/* Largest number of views of one batch call. */
+#define MS_MAX_VIEWS 32
+
+/* Bytes of workspace ms_batch_render / ms_batch_render_backward need for n_views
+ * (1..MS_MAX_VIEWS) cameras of any resolutions; 0 for an invalid request.
+ * ms_batch_workspace_size(n, K, cam, 1, p) == ms_render_workspace_size(n, K, cam, p). */
+MS_API size_t ms_batch_workspace_size(int64_t n_fans, int32_t K, const ms_camera *cams, int32_t n_views,
+                                      const ms_render_params *params);
+
+/*
+ * Forward render of one fan soup into n_views images of (possibly) different sizes in
+ * one pass of the pipeline: the tiles of all views form one index space, so binning,
+ * the key sort, rasterisation and the per-pixel resolve each launch once for the whole
+ * batch (the multi-view renders of fine-tuning, Sec. 3 "Fine-tuning", and of the
+ * evaluation in Sec. 4).  Image v equals ms_render with cams[v] bit for bit.
+ *   cams: host array of n_views cameras (read during the call only).
+ *   out_rgba: host array of n_views device pointers, image v H_v x W_v x 4, 16-byte aligned.
+ *   workspace: device, >= ms_batch_workspace_size bytes, 256-byte aligned.
+ * The call does no host synchronisation and no allocation, so it can be captured in a
+ * CUDA graph (the host arrays are copied into the kernel parameters at capture).
+ */
+MS_API ms_status ms_batch_render(const float *xyz, const float *rgb, const float *alpha, int64_t n_fans, int32_t K,
+                                 const ms_camera *cams, int32_t n_views, const ms_render_params *params,
+                                 float *const *out_rgba, void *workspace, size_t ws_bytes, void *stream);
+
+/*
+ * Adjoint of the last ms_batch_render on this workspace (same scene, cameras and params),
+ * summed over all views into d_xyz, d_rgb, d_alpha (device, +=).  out_rgba and dL_drgba
+ * are host arrays of n_views device images.
+ */
+MS_API ms_status ms_batch_render_backward(const float *xyz, const float *rgb, const float *alpha, int64_t n_fans,
+                                          int32_t K, const ms_camera *cams, int32_t n_views,
+                                          const ms_render_params *params, const float *const *out_rgba,
+                                          const float *const *dL_drgba, float *d_xyz, float *d_rgb, float *d_alpha,
+                                          void *workspace, size_t ws_bytes, void *stream);
+
+/* Candidates the autotuner times: tile in {8, 16, 32} x kbuf in {8, 16}. */
+#define MS_TUNE_CANDIDATES 6
+
+typedef struct {
+    /* per candidate c (tile = 8 << (c / 2), kbuf = 8 << (c % 2)): median milliseconds of one
+     * forward+backward batch step, or -1 unsupported (tile 32), -2 workspace too small,
+     * -3 capacity did not settle */
+    float cand_ms[MS_TUNE_CANDIDATES];
+    size_t cand_ws_bytes[MS_TUNE_CANDIDATES];   /* workspace each candidate needs (0 if unknown) */
+    int32_t best;                               /* index of the chosen candidate, -1 if none */
+    float best_ms;
+    int64_t pairs, frags;                       /* measured list lengths of the chosen candidate */
+} ms_tune_result;
+
+/*
+ * Autotuner of the batch render (no counterpart in the paper, whose renderer has fixed
+ * settings).  For every candidate (tile edge, per-pixel buffer) it renders once to
+ * measure the (tile, fan) pair list and the fragment-record list, sets both capacities
+ * to the measured length times (1 + headroom) (headroom >= 0; the "list capacity" of the
+ * batch), then times `reps` (>= 1) forward+backward batch steps with CUDA events and
+ * keeps the median.  *best receives `base` with the fastest candidate's tile, kbuf and
+ * capacities.  Candidates whose workspace exceeds ws_bytes are skipped and report their
+ * size in res->cand_ws_bytes.  out_rgba / dL_drgba as in ms_batch_render(_backward);
+ * d_xyz, d_rgb, d_alpha are overwritten with scratch values.  This call synchronises the
+ * stream (it reads list lengths and event times on the host), so run it before any graph
+ * capture.  Returns MS_ERR_CAPACITY if no candidate fits the workspace.
+ */
+MS_API ms_status ms_batch_autotune(const float *xyz, const float *rgb, const float *alpha, int64_t n_fans, int32_t K,
+                                   const ms_camera *cams, int32_t n_views, const ms_render_params *base,
+                                   float *const *out_rgba, const float *const *dL_drgba, float *d_xyz, float *d_rgb,
+                                   float *d_alpha, void *workspace, size_t ws_bytes, int32_t reps, float headroom,
+                                   ms_render_params *best, ms_tune_result *res, void *stream);
 
 /*
  * L1 term of Eq. 3: loss = mean over H x W x 3 of |C - C*|.  img_rgba: device H x W x 4;

@@ -8,6 +8,8 @@ from . import build as _build
 
 _lib = None
 
+MAX_VIEWS = 32   # MS_MAX_VIEWS
+
 MS_OK, MS_ERR_INVALID, MS_ERR_CAPACITY, MS_ERR_CUDA, MS_ERR_TIMEOUT, MS_ERR_UNSUPPORTED = range(6)
 STATUS_NAMES = {0: "MS_OK", 1: "MS_ERR_INVALID", 2: "MS_ERR_CAPACITY", 3: "MS_ERR_CUDA", 4: "MS_ERR_TIMEOUT",
                 5: "MS_ERR_UNSUPPORTED"}
@@ -42,6 +44,14 @@ class RenderInfo(C.Structure):
                 ("frag_capacity", C.c_int64)]
 
 
+TUNE_CANDIDATES = 6   # MS_TUNE_CANDIDATES
+
+
+class TuneResult(C.Structure):
+    _fields_ = [("cand_ms", C.c_float * TUNE_CANDIDATES), ("cand_ws_bytes", C.c_size_t * TUNE_CANDIDATES),
+                ("best", C.c_int32), ("best_ms", C.c_float), ("pairs", C.c_int64), ("frags", C.c_int64)]
+
+
 # name -> (restype, argtypes); P = pointer-sized value
 _P = C.c_void_p
 _SIGS = {
@@ -57,6 +67,12 @@ _SIGS = {
     "ms_l1_loss": (C.c_int, [_P, _P, C.c_int64, _P, _P, _P]),
     "ms_adam_step": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, C.c_int64, C.c_int32, C.c_float, C.c_float, C.c_float,
                                C.c_float, C.c_float, _P]),
+    "ms_batch_workspace_size": (C.c_size_t, [C.c_int64, C.c_int32, _P, C.c_int32, _P]),
+    "ms_batch_render": (C.c_int, [_P, _P, _P, C.c_int64, C.c_int32, _P, C.c_int32, _P, _P, _P, C.c_size_t, _P]),
+    "ms_batch_render_backward": (C.c_int, [_P, _P, _P, C.c_int64, C.c_int32, _P, C.c_int32, _P, _P, _P, _P, _P, _P,
+                                           _P, C.c_size_t, _P]),
+    "ms_batch_autotune": (C.c_int, [_P, _P, _P, C.c_int64, C.c_int32, _P, C.c_int32, _P, _P, _P, _P, _P, _P, _P,
+                                    C.c_size_t, C.c_int32, C.c_float, _P, _P, _P]),
     "ms_render_noalloc": (C.c_int, [_P, _P, _P, C.c_int64, C.c_int32, _P, _P, _P, _P, _P]),
     "ms_profile_enable": (None, [C.c_int32]),
     "ms_profile_read": (C.c_int, [_P, _P, C.c_int32]),

@@ -133,6 +133,124 @@ class Renderer:
         return d_xyz, d_rgb, d_alpha
 
 
+class BatchRenderer:
+    """Owns a workspace for rendering one fan soup into several views of any sizes with
+    one pass of the pipeline (ms_batch_render).  Outputs of all views live in one flat
+    device buffer (view v at pixel offset pix_base[v]), so the loss over the batch is
+    one launch; `images(flat)` gives per-view H x W x 4 views of it."""
+
+    def __init__(self, n_fans: int, K: int, cams, params=None, device="cuda"):
+        cams = list(cams)
+        if not 1 <= len(cams) <= _lib.MAX_VIEWS:
+            raise ValueError(f"1..{_lib.MAX_VIEWS} views")
+        self.n_fans, self.K, self.n_views = int(n_fans), int(K), len(cams)
+        self.cams = (_lib.Camera * self.n_views)(
+            *[c if isinstance(c, _lib.Camera) else camera_struct(c) for c in cams])
+        self.params = params if params is not None else render_params()
+        self.device = torch.device(device)
+        self.pix_base = []
+        n = 0
+        for c in self.cams:
+            self.pix_base.append(n)
+            n += c.width * c.height
+        self.n_pixels = n
+        self._alloc()
+
+    def _alloc(self):
+        n = lib().ms_batch_workspace_size(self.n_fans, self.K, self.cams, self.n_views, C.byref(self.params))
+        if n == 0:
+            raise ValueError("invalid render configuration")
+        self.ws = None
+        self.ws = torch.empty(int(n), dtype=torch.uint8, device=self.device)
+
+    def new_flat(self, fill=None):
+        t = torch.empty(self.n_pixels, 4, device=self.device, dtype=torch.float32)
+        if fill is not None:
+            t.fill_(fill)
+        return t
+
+    def images(self, flat):
+        """Per-view (H, W, 4) views of a flat n_pixels x 4 buffer."""
+        return [flat[b:b + c.width * c.height].view(c.height, c.width, 4) for b, c in zip(self.pix_base, self.cams)]
+
+    def _ptrs(self, flat):
+        if flat.shape != (self.n_pixels, 4) or not flat.is_contiguous() or not flat.is_cuda:
+            raise ValueError("expected a contiguous device buffer of n_pixels x 4 floats")
+        base = flat.data_ptr()
+        return (C.c_void_p * self.n_views)(*[base + 16 * b for b in self.pix_base])
+
+    def info(self, stream=None):
+        inf = _lib.RenderInfo()
+        st = lib().ms_render_get_info(_ptr(self.ws), C.byref(inf), _stream(stream))
+        return st, inf
+
+    def forward(self, xyz, rgb, alpha, flat=None, check_status=True, stream=None):
+        if flat is None:
+            flat = self.new_flat()
+        outs = self._ptrs(flat)
+        for _ in range(4):
+            check(lib().ms_batch_render(_ptr(xyz), _ptr(rgb), _ptr(alpha), self.n_fans, self.K, self.cams,
+                                        self.n_views, C.byref(self.params), outs, _ptr(self.ws), self.ws.numel(),
+                                        _stream(stream)))
+            if not check_status:
+                return flat
+            st, inf = self.info(stream)
+            if st == _lib.MS_ERR_CAPACITY:
+                if inf.pairs > inf.pair_capacity:
+                    self.params.pair_capacity = int(inf.pairs * 1.25) + 4096
+                if inf.frags > inf.frag_capacity:
+                    self.params.frag_capacity = int(inf.frags * 1.25) + 65536
+                self._alloc()
+                continue
+            check(st)
+            self.last_info = inf
+            return flat
+        raise _lib.MSError(_lib.MS_ERR_CAPACITY, "capacity did not converge")
+
+    def autotune(self, xyz, rgb, alpha, reps=3, headroom=0.05, stream=None):
+        """Runs ms_batch_autotune (tile, pending buffer, list capacities) on this scene
+        and adopts the fastest candidate; returns the ms_tune_result."""
+        flat = self.new_flat()
+        dL = torch.full_like(flat, 1.0 / flat.numel())
+        grads = [torch.empty_like(xyz), torch.empty_like(rgb), torch.empty_like(alpha)]
+        sizes = []
+        for tile in (8, 16):
+            for kbuf in (8, 16):
+                p = _lib.RenderParams.from_buffer_copy(self.params)
+                p.tile, p.kbuf = tile, kbuf
+                sizes.append(lib().ms_batch_workspace_size(self.n_fans, self.K, self.cams, self.n_views, C.byref(p)))
+        ws = torch.empty(max(sizes), dtype=torch.uint8, device=self.device)
+        res = _lib.TuneResult()
+        best = _lib.RenderParams()
+        for _ in range(2):
+            st = lib().ms_batch_autotune(_ptr(xyz), _ptr(rgb), _ptr(alpha), self.n_fans, self.K, self.cams,
+                                         self.n_views, C.byref(self.params), self._ptrs(flat), self._ptrs(dL),
+                                         _ptr(grads[0]), _ptr(grads[1]), _ptr(grads[2]), _ptr(ws), ws.numel(),
+                                         int(reps), float(headroom), C.byref(best), C.byref(res), _stream(stream))
+            if st == _lib.MS_OK and all(res.cand_ms[c] != -2.0 for c in range(_lib.TUNE_CANDIDATES)):
+                break
+            want = max(res.cand_ws_bytes[c] for c in range(_lib.TUNE_CANDIDATES))
+            if want <= ws.numel():
+                break
+            ws = None
+            ws = torch.empty(int(want), dtype=torch.uint8, device=self.device)
+        check(st)
+        self.params = best
+        self._alloc()
+        return res
+
+    def backward(self, xyz, rgb, alpha, flat, dL_flat, d_xyz=None, d_rgb=None, d_alpha=None, stream=None):
+        if d_xyz is None:
+            d_xyz = torch.zeros_like(xyz)
+            d_rgb = torch.zeros_like(rgb)
+            d_alpha = torch.zeros_like(alpha)
+        check(lib().ms_batch_render_backward(_ptr(xyz), _ptr(rgb), _ptr(alpha), self.n_fans, self.K, self.cams,
+                                             self.n_views, C.byref(self.params), self._ptrs(flat),
+                                             self._ptrs(dL_flat), _ptr(d_xyz), _ptr(d_rgb), _ptr(d_alpha),
+                                             _ptr(self.ws), self.ws.numel(), _stream(stream)))
+        return d_xyz, d_rgb, d_alpha
+
+
 class RenderFn(torch.autograd.Function):
     """Differentiable render of a fan soup; gradients for vertex positions, colours and
     opacities come from ms_render_backward (visibility held fixed)."""

@@ -82,14 +82,23 @@ static void params_or_default(const ms_render_params *p, ms_render_params &out) 
     if (out.T_eps <= 0.0f) out.T_eps = 1e-5f;
 }
 
-RenderLayout render_layout(int64_t n_fans, int K, const ms_camera &cam, const ms_render_params &p) {
+RenderLayout render_layout(int64_t n_fans, int K, const ms_camera *cams, int n_views, const ms_render_params &p) {
     RenderLayout L;
     memset(&L, 0, sizeof(L));
     L.tile = p.tile;
     L.kbuf = p.kbuf;
-    L.tiles_x = (cam.width + p.tile - 1) / p.tile;
-    L.tiles_y = (cam.height + p.tile - 1) / p.tile;
-    L.n_tiles = L.tiles_x * L.tiles_y;
+    L.n_views = n_views;
+    int64_t tiles = 0, npx = 0;
+    for (int v = 0; v < n_views; ++v) {
+        L.tiles_x[v] = (cams[v].width + p.tile - 1) / p.tile;
+        const int ty = (cams[v].height + p.tile - 1) / p.tile;
+        L.tile_base[v] = (int)tiles;
+        L.pix_base[v] = npx;
+        tiles += (int64_t)L.tiles_x[v] * ty;
+        npx += (int64_t)cams[v].width * cams[v].height;
+    }
+    L.n_tiles = (int)tiles;
+    L.npx = npx;
     L.tile_bits = bits_for(L.n_tiles);
     L.depth_bits = p.depth_bits;
     L.key_bits = L.tile_bits + L.depth_bits;
@@ -98,19 +107,19 @@ RenderLayout render_layout(int64_t n_fans, int K, const ms_camera &cam, const ms
     L.V = n_fans * (K + 1);
     int64_t cap = p.pair_capacity;
     if (cap <= 0) {
-        cap = 8 * n_fans;
+        cap = 8 * n_fans * n_views;
         if (cap < 65536) cap = 65536;
         const int64_t most = n_fans * (int64_t)L.n_tiles;
         if (cap > most) cap = most > 0 ? most : 1;
     }
     L.cap = cap;
-    const size_t npx = (size_t)cam.width * cam.height;
     int64_t fcap = p.frag_capacity;
-    if (fcap <= 0) fcap = 8 * (int64_t)npx + 65536;
+    if (fcap <= 0) fcap = 8 * npx + 65536;
     L.frag_cap = fcap;
-    L.bin_blocks = (n_fans + 255) / 256;
+    L.bin_fan_blocks = (n_fans + 255) / 256;
+    L.bin_blocks = L.bin_fan_blocks * n_views;
     L.sort_blocks = (cap + 4095) / 4096;
-    L.scan_blocks = ((int64_t)npx + 2047) / 2048;
+    L.scan_blocks = (npx + 2047) / 2048;
     L.max_items = L.n_tiles + (cap + kItemFans - 1) / kItemFans;
     L.tscan_blocks = ((int64_t)L.n_tiles + 2047) / 2048;
     size_t o = 0;
@@ -129,38 +138,139 @@ RenderLayout render_layout(int64_t n_fans, int K, const ms_camera &cam, const ms
     L.off_tile_ibase = o;        o = align_up(o + 4 * (size_t)L.n_tiles, 256);
     L.off_items = o;             o = align_up(o + 16 * (size_t)L.max_items, 256);
     L.off_icnt = o;              o = align_up(o + 4 * (size_t)L.max_items * p.tile * p.tile, 256);
-    L.off_counts = o;            o = align_up(o + 4 * npx, 256);
-    L.off_offsets = o;           o = align_up(o + 4 * npx, 256);
+    L.off_counts = o;            o = align_up(o + 4 * (size_t)npx, 256);
+    L.off_offsets = o;           o = align_up(o + 4 * (size_t)npx, 256);
     L.off_frags = o;             o = align_up(o + 16 * kRecBwd * (size_t)fcap, 256);
-    L.off_tfinal = o;            o = align_up(o + 4 * npx, 256);
-    L.off_ncommit = o;           o = align_up(o + 4 * npx, 256);
+    L.off_tfinal = o;            o = align_up(o + 4 * (size_t)npx, 256);
+    L.off_ncommit = o;           o = align_up(o + 4 * (size_t)npx, 256);
     L.off_grad = o;              o = align_up(o + 32 * (size_t)L.V, 256);
     L.total = o;
     return L;
 }
 
+static ms_status check_cameras(const ms_camera *cams, int n_views) {
+    if (!cams) return fail(MS_ERR_INVALID, "camera is NULL");
+    if (n_views < 1 || n_views > kMaxViews) return fail(MS_ERR_INVALID, "n_views=%d outside 1..%d", n_views, kMaxViews);
+    for (int v = 0; v < n_views; ++v) {
+        const ms_camera *cam = cams + v;
+        if (cam->width <= 0 || cam->height <= 0 || cam->width > 32768 || cam->height > 32768)
+            return fail(MS_ERR_INVALID, "view %d: image size %dx%d", v, cam->width, cam->height);
+        if (!(cam->znear > 0.0f)) return fail(MS_ERR_INVALID, "view %d: znear must be > 0", v);
+        if (!(cam->fx != 0.0f && cam->fy != 0.0f)) return fail(MS_ERR_INVALID, "view %d: zero focal length", v);
+    }
+    return MS_OK;
+}
+
 static ms_status check_render_args(const float *xyz, const float *rgb, const float *alpha, int64_t n_fans, int K,
-                                   const ms_camera *cam, const ms_render_params &p, const void *ws, size_t ws_bytes,
-                                   RenderLayout &L) {
-    if (!cam) return fail(MS_ERR_INVALID, "camera is NULL");
+                                   const ms_camera *cams, int n_views, const ms_render_params &p, const void *ws,
+                                   size_t ws_bytes, RenderLayout &L) {
+    ms_status s = check_cameras(cams, n_views);
+    if (s != MS_OK) return s;
     if (K < 3 || K > kMaxK) return fail(MS_ERR_INVALID, "K=%d outside 3..%d", K, kMaxK);
     if (n_fans < 0) return fail(MS_ERR_INVALID, "n_fans < 0");
     if (n_fans > 0 && (!xyz || !rgb || !alpha)) return fail(MS_ERR_INVALID, "scene pointer is NULL");
     if (n_fans * (int64_t)(K + 1) >= (1ll << 32)) return fail(MS_ERR_INVALID, "too many vertices");
-    if (cam->width <= 0 || cam->height <= 0 || cam->width > 32768 || cam->height > 32768)
-        return fail(MS_ERR_INVALID, "image size %dx%d", cam->width, cam->height);
-    if (!(cam->znear > 0.0f)) return fail(MS_ERR_INVALID, "znear must be > 0");
-    if (!(cam->fx != 0.0f && cam->fy != 0.0f)) return fail(MS_ERR_INVALID, "zero focal length");
     if (p.tile == 32) return fail(MS_ERR_UNSUPPORTED, "tile 32 is not built (one pixel per thread needs 1024 threads)");
     if (p.tile != 8 && p.tile != 16) return fail(MS_ERR_INVALID, "tile %d not in {8,16}", p.tile);
     if (p.kbuf != 8 && p.kbuf != 16) return fail(MS_ERR_INVALID, "kbuf %d not in {8,16}", p.kbuf);
     if (p.depth_bits < 8 || p.depth_bits > 31) return fail(MS_ERR_INVALID, "depth_bits %d", p.depth_bits);
-    L = render_layout(n_fans, K, *cam, p);
+    L = render_layout(n_fans, K, cams, n_views, p);
     if (L.key_bits > 64) return fail(MS_ERR_INVALID, "sort key needs %d bits", L.key_bits);
     if (L.cap >= (1ll << 30)) return fail(MS_ERR_INVALID, "pair capacity %lld >= 2^30", (long long)L.cap);
+    if (L.frag_cap >= (1ll << 32)) return fail(MS_ERR_INVALID, "fragment capacity %lld >= 2^32", (long long)L.frag_cap);
     if (!ws) return fail(MS_ERR_INVALID, "workspace is NULL");
     if (reinterpret_cast<uintptr_t>(ws) & 255) return fail(MS_ERR_INVALID, "workspace not 256-byte aligned");
     if (ws_bytes < L.total) return fail(MS_ERR_INVALID, "workspace %zu bytes < %zu needed", ws_bytes, L.total);
+    return MS_OK;
+}
+
+static ViewTable make_views(const ms_camera *cams, int n_views, const RenderLayout &L, float *const *out,
+                            const float *const *out_fwd, const float *const *dL) {
+    ViewTable t;
+    memset(&t, 0, sizeof(t));
+    t.n = n_views;
+    for (int v = 0; v < n_views; ++v) {
+        t.v[v].cam = make_cam(cams[v]);
+        t.v[v].tile_base = (uint32_t)L.tile_base[v];
+        t.v[v].tiles_x = (uint32_t)L.tiles_x[v];
+        t.v[v].pix_base = (unsigned long long)L.pix_base[v];
+        t.v[v].out = out ? out[v] : nullptr;
+        t.v[v].out_fwd = out_fwd ? out_fwd[v] : nullptr;
+        t.v[v].dL = dL ? dL[v] : nullptr;
+    }
+    return t;
+}
+
+static bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
+// Forward of any number of views: one binning launch, one sort, one rasterisation
+// and one resolve over the concatenated tile / pixel index space.
+static ms_status render_views(const float *xyz, const float *rgb, const float *alpha, int64_t n_fans, int K,
+                              const ms_camera *cams, int n_views, const ms_render_params *params, float *const *out,
+                              void *workspace, size_t ws_bytes, cudaStream_t st) {
+    ms_render_params p;
+    params_or_default(params, p);
+    RenderLayout L;
+    ms_status s = check_render_args(xyz, rgb, alpha, n_fans, K, cams, n_views, p, workspace, ws_bytes, L);
+    if (s != MS_OK) return s;
+    if (!out) return fail(MS_ERR_INVALID, "output image list is NULL");
+    for (int v = 0; v < n_views; ++v)
+        if (!out[v] || !aligned16(out[v])) return fail(MS_ERR_INVALID, "view %d: output image NULL or not 16-byte aligned", v);
+    char *ws = static_cast<char *>(workspace);
+    cudaError_t e = cudaMemsetAsync(ws, 0, L.off_keys0, st);
+    if (e != cudaSuccess) return cuda_fail(e, "workspace clear");
+    RenderArgs a;
+    memset(&a, 0, sizeof(a));
+    a.xyz = xyz; a.rgb = rgb; a.alpha = alpha; a.n_fans = n_fans; a.K = K; a.prm = p; a.L = L; a.ws = ws;
+    a.vt = make_views(cams, n_views, L, out, nullptr, nullptr);
+    {
+        StageScope sc(MS_STAGE_BIN, st);
+        if ((e = launch_bin(a, st)) != cudaSuccess) return cuda_fail(e, "bin launch");
+    }
+    {
+        StageScope sc(MS_STAGE_SORT, st);
+        if ((e = launch_sort(a, st)) != cudaSuccess) return cuda_fail(e, "sort launch");
+    }
+    {
+        StageScope sc(MS_STAGE_RASTER, st);
+        if ((e = launch_raster_count(a, st)) != cudaSuccess) return cuda_fail(e, "raster count launch");
+        if ((e = launch_raster(a, true, st)) != cudaSuccess) return cuda_fail(e, "raster fill launch");
+        if ((e = launch_resolve(a, false, st)) != cudaSuccess) return cuda_fail(e, "resolve launch");
+    }
+    if (n_fans > 0) count_launches(1 + 3 + L.passes);
+    count_launches(1);   // resolve (raster kernels count themselves)
+    return MS_OK;
+}
+
+static ms_status render_views_backward(const float *xyz, const float *rgb, const float *alpha, int64_t n_fans, int K,
+                                       const ms_camera *cams, int n_views, const ms_render_params *params,
+                                       const float *const *out_fwd, const float *const *dL, float *d_xyz, float *d_rgb,
+                                       float *d_alpha, void *workspace, size_t ws_bytes, cudaStream_t st) {
+    ms_render_params p;
+    params_or_default(params, p);
+    RenderLayout L;
+    ms_status s = check_render_args(xyz, rgb, alpha, n_fans, K, cams, n_views, p, workspace, ws_bytes, L);
+    if (s != MS_OK) return s;
+    if (!out_fwd || !dL) return fail(MS_ERR_INVALID, "image lists are NULL");
+    for (int v = 0; v < n_views; ++v)
+        if (!out_fwd[v] || !dL[v] || !aligned16(out_fwd[v]) || !aligned16(dL[v]))
+            return fail(MS_ERR_INVALID, "view %d: image NULL or not 16-byte aligned", v);
+    if (n_fans > 0 && (!d_xyz || !d_rgb || !d_alpha)) return fail(MS_ERR_INVALID, "gradient pointer is NULL");
+    char *ws = static_cast<char *>(workspace);
+    StageScope sc(MS_STAGE_RASTER_BWD, st);
+    cudaError_t e = cudaMemsetAsync(ws + L.off_grad, 0, 32 * (size_t)L.V, st);
+    if (e != cudaSuccess) return cuda_fail(e, "gradient clear");
+    RenderArgs a;
+    memset(&a, 0, sizeof(a));
+    a.xyz = xyz; a.rgb = rgb; a.alpha = alpha; a.n_fans = n_fans; a.K = K; a.prm = p; a.L = L; a.ws = ws;
+    a.d_xyz = d_xyz; a.d_rgb = d_rgb; a.d_alpha = d_alpha;
+    a.vt = make_views(cams, n_views, L, nullptr, out_fwd, dL);
+    // the fragment records are regenerated from the sorted tile lists (not kept from the
+    // forward); transmittance is recomputed during the resolve
+    if ((e = launch_raster_fill_bwd(a, st)) != cudaSuccess) return cuda_fail(e, "raster fill launch");
+    if ((e = launch_resolve(a, true, st)) != cudaSuccess) return cuda_fail(e, "resolve backward launch");
+    if ((e = launch_grad_scatter(a, st)) != cudaSuccess) return cuda_fail(e, "gradient scatter launch");
+    count_launches(1 + (L.V > 0 ? 1 : 0));   // resolve, scatter (the fill counts itself)
     return MS_OK;
 }
 
@@ -238,78 +348,48 @@ MS_API ms_status ms_mesh_build(const float *means, const float *log_scales, cons
 }
 
 MS_API size_t ms_render_workspace_size(int64_t n_fans, int32_t K, const ms_camera *cam, const ms_render_params *params) {
-    if (!cam || K < 3 || K > kMaxK || n_fans < 0) return 0;
+    return ms_batch_workspace_size(n_fans, K, cam, 1, params);
+}
+
+MS_API size_t ms_batch_workspace_size(int64_t n_fans, int32_t K, const ms_camera *cams, int32_t n_views,
+                                      const ms_render_params *params) {
+    if (!cams || K < 3 || K > kMaxK || n_fans < 0 || n_views < 1 || n_views > kMaxViews) return 0;
     ms_render_params p;
     params_or_default(params, p);
-    return render_layout(n_fans, K, *cam, p).total;
+    return render_layout(n_fans, K, cams, n_views, p).total;
 }
 
 MS_API ms_status ms_render(const float *xyz, const float *rgb, const float *alpha, int64_t n_fans, int32_t K,
                            const ms_camera *cam, const ms_render_params *params, float *out_rgba, void *workspace,
                            size_t ws_bytes, void *stream) {
-    ms_render_params p;
-    params_or_default(params, p);
-    RenderLayout L;
-    ms_status s = check_render_args(xyz, rgb, alpha, n_fans, K, cam, p, workspace, ws_bytes, L);
-    if (s != MS_OK) return s;
-    if (!out_rgba) return fail(MS_ERR_INVALID, "out_rgba is NULL");
-    if (reinterpret_cast<uintptr_t>(out_rgba) & 15) return fail(MS_ERR_INVALID, "out_rgba must be 16-byte aligned");
-    cudaStream_t st = (cudaStream_t)stream;
-    char *ws = static_cast<char *>(workspace);
-    cudaError_t e = cudaMemsetAsync(ws, 0, L.off_keys0, st);
-    if (e != cudaSuccess) return cuda_fail(e, "workspace clear");
-    RenderArgs a;
-    memset(&a, 0, sizeof(a));
-    a.xyz = xyz; a.rgb = rgb; a.alpha = alpha; a.n_fans = n_fans; a.K = K; a.cam = cam; a.prm = p; a.L = L;
-    a.ws = ws; a.out_rgba = out_rgba;
-    {
-        StageScope sc(MS_STAGE_BIN, st);
-        if ((e = launch_bin(a, st)) != cudaSuccess) return cuda_fail(e, "bin launch");
-    }
-    {
-        StageScope sc(MS_STAGE_SORT, st);
-        if ((e = launch_sort(a, st)) != cudaSuccess) return cuda_fail(e, "sort launch");
-    }
-    {
-        StageScope sc(MS_STAGE_RASTER, st);
-        if ((e = launch_raster_count(a, st)) != cudaSuccess) return cuda_fail(e, "raster count launch");
-        if ((e = launch_raster(a, true, st)) != cudaSuccess) return cuda_fail(e, "raster fill launch");
-        if ((e = launch_resolve(a, false, st)) != cudaSuccess) return cuda_fail(e, "resolve launch");
-    }
-    if (n_fans > 0) count_launches(1 + 3 + L.passes);
-    count_launches(1);   // resolve (raster kernels count themselves)
-    return MS_OK;
+    float *out[1] = {out_rgba};
+    return render_views(xyz, rgb, alpha, n_fans, K, cam, 1, params, out, workspace, ws_bytes, (cudaStream_t)stream);
 }
 
 MS_API ms_status ms_render_backward(const float *xyz, const float *rgb, const float *alpha, int64_t n_fans, int32_t K,
                                     const ms_camera *cam, const ms_render_params *params, const float *out_rgba,
                                     const float *dL_drgba, float *d_xyz, float *d_rgb, float *d_alpha, void *workspace,
                                     size_t ws_bytes, void *stream) {
-    ms_render_params p;
-    params_or_default(params, p);
-    RenderLayout L;
-    ms_status s = check_render_args(xyz, rgb, alpha, n_fans, K, cam, p, workspace, ws_bytes, L);
-    if (s != MS_OK) return s;
-    if (!out_rgba || !dL_drgba) return fail(MS_ERR_INVALID, "out_rgba / dL_drgba is NULL");
-    if ((reinterpret_cast<uintptr_t>(out_rgba) | reinterpret_cast<uintptr_t>(dL_drgba)) & 15)
-        return fail(MS_ERR_INVALID, "out_rgba / dL_drgba must be 16-byte aligned");
-    if (n_fans > 0 && (!d_xyz || !d_rgb || !d_alpha)) return fail(MS_ERR_INVALID, "gradient pointer is NULL");
-    cudaStream_t st = (cudaStream_t)stream;
-    char *ws = static_cast<char *>(workspace);
-    StageScope sc(MS_STAGE_RASTER_BWD, st);
-    cudaError_t e = cudaMemsetAsync(ws + L.off_grad, 0, 32 * (size_t)L.V, st);
-    if (e != cudaSuccess) return cuda_fail(e, "gradient clear");
-    RenderArgs a;
-    memset(&a, 0, sizeof(a));
-    a.xyz = xyz; a.rgb = rgb; a.alpha = alpha; a.n_fans = n_fans; a.K = K; a.cam = cam; a.prm = p; a.L = L;
-    a.ws = ws; a.out_fwd = out_rgba; a.dL = dL_drgba; a.d_xyz = d_xyz; a.d_rgb = d_rgb; a.d_alpha = d_alpha;
-    // the fragment records are regenerated from the sorted tile lists (not kept from the
-    // forward); transmittance is recomputed during the resolve
-    if ((e = launch_raster_fill_bwd(a, st)) != cudaSuccess) return cuda_fail(e, "raster fill launch");
-    if ((e = launch_resolve(a, true, st)) != cudaSuccess) return cuda_fail(e, "resolve backward launch");
-    if ((e = launch_grad_scatter(a, st)) != cudaSuccess) return cuda_fail(e, "gradient scatter launch");
-    count_launches(1 + (L.V > 0 ? 1 : 0));   // resolve, scatter (the fill counts itself)
-    return MS_OK;
+    const float *of[1] = {out_rgba};
+    const float *dl[1] = {dL_drgba};
+    return render_views_backward(xyz, rgb, alpha, n_fans, K, cam, 1, params, of, dl, d_xyz, d_rgb, d_alpha, workspace,
+                                 ws_bytes, (cudaStream_t)stream);
+}
+
+MS_API ms_status ms_batch_render(const float *xyz, const float *rgb, const float *alpha, int64_t n_fans, int32_t K,
+                                 const ms_camera *cams, int32_t n_views, const ms_render_params *params,
+                                 float *const *out_rgba, void *workspace, size_t ws_bytes, void *stream) {
+    return render_views(xyz, rgb, alpha, n_fans, K, cams, n_views, params, out_rgba, workspace, ws_bytes,
+                        (cudaStream_t)stream);
+}
+
+MS_API ms_status ms_batch_render_backward(const float *xyz, const float *rgb, const float *alpha, int64_t n_fans,
+                                          int32_t K, const ms_camera *cams, int32_t n_views,
+                                          const ms_render_params *params, const float *const *out_rgba,
+                                          const float *const *dL_drgba, float *d_xyz, float *d_rgb, float *d_alpha,
+                                          void *workspace, size_t ws_bytes, void *stream) {
+    return render_views_backward(xyz, rgb, alpha, n_fans, K, cams, n_views, params, out_rgba, dL_drgba, d_xyz, d_rgb,
+                                 d_alpha, workspace, ws_bytes, (cudaStream_t)stream);
 }
 
 MS_API ms_status ms_render_get_info(const void *workspace, ms_render_info *info, void *stream) {

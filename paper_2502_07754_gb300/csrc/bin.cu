@@ -16,13 +16,29 @@ namespace {
 constexpr int kBinThreads = 256;
 constexpr unsigned long long kFlagAgg = 1ull << 62, kFlagPre = 2ull << 62, kValMask = (1ull << 62) - 1;
 
-__global__ void __launch_bounds__(kBinThreads) bin_kernel(const float *__restrict__ xyz, int64_t n_fans, int K,
-                                                          CamDev cam, int tile_shift, int tiles_x,
-                                                          int depth_bits, int64_t cap, int64_t nblocks,
-                                                          unsigned n_tiles, unsigned sort_bits,
-                                                          Status *st, unsigned long long *state,
-                                                          unsigned long long *__restrict__ keys,
-                                                          uint32_t *__restrict__ vals) {
+struct BinArgs {
+    const float *xyz;
+    int64_t n_fans;
+    int K, tile_shift, depth_bits;
+    int64_t cap, nblocks, fan_blocks;
+    unsigned n_tiles, sort_bits;
+    Status *st;
+    unsigned long long *state, *keys;
+    uint32_t *vals;
+    ViewTable vt;
+};
+
+// Blocks take virtual ids in start order; id = view * fan_blocks + fan block, so pairs
+// come out view by view and, within a view, in fan order.
+__global__ void __launch_bounds__(kBinThreads) bin_kernel(const __grid_constant__ BinArgs a) {
+    const float *__restrict__ xyz = a.xyz;
+    const int64_t n_fans = a.n_fans;
+    const int K = a.K, tile_shift = a.tile_shift, depth_bits = a.depth_bits;
+    const int64_t cap = a.cap, nblocks = a.nblocks;
+    Status *st = a.st;
+    unsigned long long *state = a.state;
+    unsigned long long *__restrict__ keys = a.keys;
+    uint32_t *__restrict__ vals = a.vals;
     extern __shared__ float s_xyz[];   // kBinThreads * (K+1) * 3
     __shared__ uint32_t s_off[kBinThreads + 1];
     __shared__ uint32_t s_rect[kBinThreads][2];   // (tx0 | ty0 << 16), (w | h << 16)
@@ -40,8 +56,11 @@ __global__ void __launch_bounds__(kBinThreads) bin_kernel(const float *__restric
     }
     __syncthreads();
     const int64_t vid = s_vid;
-    const int64_t f0 = vid * kBinThreads;
+    const int view = (int)(vid / a.fan_blocks);
+    const int64_t f0 = (vid - (int64_t)view * a.fan_blocks) * kBinThreads;
     const int nloc = (int)min64(kBinThreads, n_fans - f0);
+    const CamDev &cam = a.vt.v[view].cam;
+    const unsigned tiles_x = a.vt.v[view].tiles_x, tile_base = a.vt.v[view].tile_base;
 
     // Coalesced staging of the block's vertices.
     {
@@ -149,8 +168,8 @@ __global__ void __launch_bounds__(kBinThreads) bin_kernel(const float *__restric
         if (vid == nblocks - 1) st->pairs = excl + total;
         if (vid == 0) {
             st->cap = (unsigned long long)cap;
-            st->n_tiles = n_tiles;
-            st->sort_bits = sort_bits;
+            st->n_tiles = a.n_tiles;
+            st->sort_bits = a.sort_bits;
         }
         if (s_culled) atomicAdd(&st->culled, (unsigned long long)s_culled);
     }
@@ -171,7 +190,7 @@ __global__ void __launch_bounds__(kBinThreads) bin_kernel(const float *__restric
         const uint32_t r0 = s_rect[lo][0], r1 = s_rect[lo][1];
         const uint32_t w = r1 & 0xFFFFu;
         const uint32_t tx = (r0 & 0xFFFFu) + k % w, ty = (r0 >> 16) + k / w;
-        const unsigned long long tile = (unsigned long long)ty * tiles_x + tx;
+        const unsigned long long tile = tile_base + (unsigned long long)ty * tiles_x + tx;
         keys[idx] = ((tile << depth_bits) | s_q[lo]) & tmask;
         vals[idx] = (uint32_t)(f0 + lo);
     }
@@ -179,18 +198,29 @@ __global__ void __launch_bounds__(kBinThreads) bin_kernel(const float *__restric
 
 }  // namespace
 
-cudaError_t launch_bin(const RenderArgs &a, cudaStream_t st) {
-    const RenderLayout &L = a.L;
-    if (a.n_fans == 0) return cudaSuccess;
-    const size_t smem = sizeof(float) * kBinThreads * (a.K + 1) * 3;
+cudaError_t launch_bin(const RenderArgs &ra, cudaStream_t st) {
+    const RenderLayout &L = ra.L;
+    if (ra.n_fans == 0) return cudaSuccess;
+    const size_t smem = sizeof(float) * kBinThreads * (ra.K + 1) * 3;
     cudaFuncSetAttribute(bin_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    int shift = 0;
-    while ((1 << shift) < L.tile) ++shift;
-    bin_kernel<<<(unsigned)L.bin_blocks, kBinThreads, smem, st>>>(
-        a.xyz, a.n_fans, a.K, make_cam(*a.cam), shift, L.tiles_x, L.depth_bits, L.cap, L.bin_blocks,
-        (unsigned)L.n_tiles, (unsigned)(8 * L.passes),
-        reinterpret_cast<Status *>(a.ws + L.off_status), reinterpret_cast<unsigned long long *>(a.ws + L.off_bin_state),
-        reinterpret_cast<unsigned long long *>(a.ws + L.off_keys0), reinterpret_cast<uint32_t *>(a.ws + L.off_vals0));
+    BinArgs a;
+    a.xyz = ra.xyz;
+    a.n_fans = ra.n_fans;
+    a.K = ra.K;
+    a.tile_shift = 0;
+    while ((1 << a.tile_shift) < L.tile) ++a.tile_shift;
+    a.depth_bits = L.depth_bits;
+    a.cap = L.cap;
+    a.nblocks = L.bin_blocks;
+    a.fan_blocks = L.bin_fan_blocks;
+    a.n_tiles = (unsigned)L.n_tiles;
+    a.sort_bits = (unsigned)(8 * L.passes);
+    a.st = reinterpret_cast<Status *>(ra.ws + L.off_status);
+    a.state = reinterpret_cast<unsigned long long *>(ra.ws + L.off_bin_state);
+    a.keys = reinterpret_cast<unsigned long long *>(ra.ws + L.off_keys0);
+    a.vals = reinterpret_cast<uint32_t *>(ra.ws + L.off_vals0);
+    a.vt = ra.vt;
+    bin_kernel<<<(unsigned)L.bin_blocks, kBinThreads, smem, st>>>(a);
     return cudaGetLastError();
 }
 

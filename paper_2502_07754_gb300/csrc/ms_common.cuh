@@ -58,6 +58,40 @@ inline CamDev make_cam(const ms_camera &c) {
     return d;
 }
 
+// Views of one render call.  Tiles and pixels of all views form one index space: view v
+// owns global tiles [tile_base, tile_base + tiles) and pixels [pix_base, pix_base + W H).
+// The table travels to the kernels as a __grid_constant__ parameter.
+constexpr int kMaxViews = MS_MAX_VIEWS;
+struct ViewDev {
+    CamDev cam;
+    uint32_t tile_base, tiles_x;
+    unsigned long long pix_base;
+    float *out;               // forward output image, H x W x 4
+    const float *dL;          // backward: dL / d image
+    const float *out_fwd;     // backward: the forward image
+};
+struct ViewTable {
+    int n;
+    ViewDev v[kMaxViews];
+};
+
+__device__ __forceinline__ int view_of_tile(const ViewTable &t, uint32_t tile) {
+    int lo = 0, hi = t.n;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (t.v[mid].tile_base <= tile) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+__device__ __forceinline__ int view_of_pixel(const ViewTable &t, unsigned long long pix) {
+    int lo = 0, hi = t.n;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (t.v[mid].pix_base <= pix) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
 // ---------------------------------------------------------------------------------
 // Decisions (binary32, no contraction)
 // ---------------------------------------------------------------------------------

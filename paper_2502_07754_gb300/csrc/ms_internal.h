@@ -5,10 +5,10 @@
 #include <stdint.h>
 
 #include "../../include/meshsplats.h"
+#include "ms_common.cuh"
 
 namespace ms {
 
-struct CamDev;
 
 struct MeshBuildConst {
     int K;
@@ -26,29 +26,29 @@ cudaError_t launch_mesh_build(const float *means, const float *log_scales, const
                               const float *corr, float *xyz, float *rgb, float *alpha, cudaStream_t st);
 
 // Render workspace layout (byte offsets from the workspace base, 256-byte aligned).
+// Tiles and pixels of all views form one index space (see ViewTable).
 struct RenderLayout {
-    int tile, tiles_x, tiles_y, n_tiles, tile_bits, depth_bits, key_bits, passes, kbuf;
-    int64_t n_fans, V, cap, frag_cap;
-    int64_t bin_blocks, sort_blocks, scan_blocks, tscan_blocks, max_items;
+    int tile, n_views, n_tiles, tile_bits, depth_bits, key_bits, passes, kbuf;
+    int tiles_x[kMaxViews], tile_base[kMaxViews];
+    int64_t pix_base[kMaxViews];
+    int64_t npx, n_fans, V, cap, frag_cap;
+    int64_t bin_fan_blocks, bin_blocks, sort_blocks, scan_blocks, tscan_blocks, max_items;
     size_t off_status, off_bin_state, off_keys0, off_keys1, off_vals0, off_vals1, off_hist, off_lookback,
         off_ranges, off_scan_state, off_tscan_state, off_tile_nitems, off_tile_ibase, off_items, off_icnt,
         off_counts, off_offsets, off_frags, off_tfinal, off_ncommit, off_grad, total;
 };
 
-RenderLayout render_layout(int64_t n_fans, int K, const ms_camera &cam, const ms_render_params &p);
+RenderLayout render_layout(int64_t n_fans, int K, const ms_camera *cams, int n_views, const ms_render_params &p);
 
 struct RenderArgs {
     const float *xyz, *rgb, *alpha;
     int64_t n_fans;
     int K;
-    const ms_camera *cam;
+    ViewTable vt;              // cameras, index-space bases, per-view image pointers
     ms_render_params prm;
     RenderLayout L;
     char *ws;
-    float *out_rgba;
-    // backward
-    const float *out_fwd, *dL;
-    float *d_xyz, *d_rgb, *d_alpha;
+    float *d_xyz, *d_rgb, *d_alpha;   // backward outputs
 };
 
 cudaError_t launch_bin(const RenderArgs &a, cudaStream_t st);

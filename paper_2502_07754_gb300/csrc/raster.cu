@@ -21,8 +21,9 @@ namespace ms {
 namespace {
 
 struct RastArgs {
-    SceneDev sc;
-    int tiles_x, depth_bits;
+    const float *xyz, *rgb, *alpha;
+    int K, depth_bits;
+    ViewTable vt;
     const unsigned long long *keys;
     const uint32_t *vals;
     const uint4 *items;        // (tile, start, end, index within tile)
@@ -48,21 +49,33 @@ __host__ __device__ __forceinline__ size_t warp_smem_bytes(int K) {
 }
 
 template <int TILE, int STG, int KT, int MODE>
-__global__ void __launch_bounds__(kRastWarps * 32) raster_kernel(RastArgs a) {
+__global__ void __launch_bounds__(kRastWarps * 32) raster_kernel(const __grid_constant__ RastArgs a) {
     constexpr bool FILL = MODE != kCount;   // passes that address records
     extern __shared__ __align__(16) char smem[];
-    const int K = KT > 0 ? KT : a.sc.K;
+    const int K = KT > 0 ? KT : a.K;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t item = blockIdx.x * kRastWarps + warp;
     if (item >= a.st->n_items) return;   // whole warp; nothing below synchronises the block
     const uint4 it = a.items[item];
-    const int tile = (int)it.x;
+    const int view = view_of_tile(a.vt, it.x);
+    const ViewDev &vw = a.vt.v[view];
+    SceneDev sc;
+    sc.xyz = a.xyz;
+    sc.rgb = a.rgb;
+    sc.alpha = a.alpha;
+    sc.K = K;
+    sc.cam = &vw.cam;
+    sc.W = vw.cam.width;
+    sc.H = vw.cam.height;
+    const int tile = (int)(it.x - vw.tile_base);
+    const int tiles_x = (int)vw.tiles_x;
+    const unsigned long long pix_base = vw.pix_base;
     char *mine = smem + (size_t)warp * warp_smem_bytes<TILE, STG, MODE>(K);
     uint32_t *s_cnt = reinterpret_cast<uint32_t *>(mine);   // [TILE*TILE] fragments so far
     uint32_t *s_base = s_cnt + TILE * TILE;                   // [TILE*TILE] record offsets (fill)
     const Stage S = stage_ptrs(mine + (size_t)TILE * TILE * 4 * (FILL ? 2 : 1), STG, K, MODE);
-    const int tx0 = (tile % a.tiles_x) * TILE, ty0 = (tile / a.tiles_x) * TILE;
-    const int tx1 = min(tx0 + TILE, a.sc.W) - 1, ty1 = min(ty0 + TILE, a.sc.H) - 1;
+    const int tx0 = (tile % tiles_x) * TILE, ty0 = (tile / tiles_x) * TILE;
+    const int tx1 = min(tx0 + TILE, sc.W) - 1, ty1 = min(ty0 + TILE, sc.H) - 1;
     uint32_t *icnt = a.icnt + (size_t)item * TILE * TILE;
     for (int i = lane; i < TILE * TILE; i += 32) {
         s_cnt[i] = 0;
@@ -70,7 +83,7 @@ __global__ void __launch_bounds__(kRastWarps * 32) raster_kernel(RastArgs a) {
             const int x = tx0 + (i % TILE), y = ty0 + (i / TILE);
             uint32_t b = 0xffffffffu;
             if (x <= tx1 && y <= ty1) {
-                const size_t pix = (size_t)y * a.sc.W + x;
+                const size_t pix = pix_base + (size_t)y * sc.W + x;
                 const int64_t o = a.offsets[pix];
                 // a pixel whose records would not fit gets none (the overflow is reported)
                 if (o + a.counts[pix] <= a.frag_cap) b = (uint32_t)o + icnt[i];
@@ -85,7 +98,7 @@ __global__ void __launch_bounds__(kRastWarps * 32) raster_kernel(RastArgs a) {
         if (lane < cnt) {
             const uint32_t li = cb + lane;
             const uint32_t q = (uint32_t)(__ldg(a.keys + li) & ((1ull << a.depth_bits) - 1ull));
-            stage_fan(a.sc, S, STG, K, lane, __ldg(a.vals + li), q, MODE);
+            stage_fan(sc, S, STG, K, lane, __ldg(a.vals + li), q, MODE);
         }
         __syncwarp();
         for (int f = 0; f < cnt; ++f) {
@@ -277,8 +290,9 @@ __global__ void tile_item_emit_kernel(const uint2 *__restrict__ ranges, int n_ti
 // at a time so a tile with many items is not latency-bound.
 template <int TILE>
 __global__ void __launch_bounds__(TILE *TILE) item_prefix_kernel(const uint32_t *__restrict__ nitems,
-                                                                 const uint32_t *__restrict__ ibase, int tiles_x,
-                                                                 int W, int H, uint32_t *__restrict__ icnt,
+                                                                 const uint32_t *__restrict__ ibase,
+                                                                 const __grid_constant__ ViewTable vt,
+                                                                 uint32_t *__restrict__ icnt,
                                                                  uint32_t *__restrict__ counts) {
     const int t = blockIdx.x, i = threadIdx.x;
     const uint32_t n = nitems[t], b = ibase[t];
@@ -299,8 +313,10 @@ __global__ void __launch_bounds__(TILE *TILE) item_prefix_kernel(const uint32_t 
         c[(size_t)k * TILE * TILE] = run;
         run += v;
     }
-    const int x = (t % tiles_x) * TILE + (i % TILE), y = (t / tiles_x) * TILE + (i / TILE);
-    if (x < W && y < H) counts[(size_t)y * W + x] = run;
+    const ViewDev &vw = vt.v[view_of_tile(vt, (uint32_t)t)];
+    const int lt = t - (int)vw.tile_base, tiles_x = (int)vw.tiles_x;
+    const int x = (lt % tiles_x) * TILE + (i % TILE), y = (lt / tiles_x) * TILE + (i / TILE);
+    if (x < vw.cam.width && y < vw.cam.height) counts[vw.pix_base + (size_t)y * vw.cam.width + x] = run;
 }
 
 template <int TILE, int KT, int MODE>
@@ -328,14 +344,11 @@ cudaError_t launch_dispatch(const RastArgs &ra, const RenderLayout &L, int K, cu
 RastArgs make_args(const RenderArgs &ra) {
     const RenderLayout &L = ra.L;
     RastArgs a;
-    a.sc.xyz = ra.xyz;
-    a.sc.rgb = ra.rgb;
-    a.sc.alpha = ra.alpha;
-    a.sc.K = ra.K;
-    a.sc.cam = make_cam(*ra.cam);
-    a.sc.W = ra.cam->width;
-    a.sc.H = ra.cam->height;
-    a.tiles_x = L.tiles_x;
+    a.xyz = ra.xyz;
+    a.rgb = ra.rgb;
+    a.alpha = ra.alpha;
+    a.K = ra.K;
+    a.vt = ra.vt;
     a.depth_bits = L.depth_bits;
     a.keys = reinterpret_cast<const unsigned long long *>(ra.ws + (L.passes & 1 ? L.off_keys1 : L.off_keys0));
     a.vals = reinterpret_cast<const uint32_t *>(ra.ws + (L.passes & 1 ? L.off_vals1 : L.off_vals0));
@@ -370,12 +383,12 @@ cudaError_t launch_raster_count(const RenderArgs &ra, cudaStream_t st) {
     cudaError_t e = launch_dispatch<kCount>(a, L, ra.K, st);
     if (e != cudaSuccess) return e;
     if (L.tile == 8)
-        item_prefix_kernel<8><<<L.n_tiles, 64, 0, st>>>(nitems, ibase, L.tiles_x, ra.cam->width, ra.cam->height, a.icnt,
+        item_prefix_kernel<8><<<L.n_tiles, 64, 0, st>>>(nitems, ibase, ra.vt, a.icnt,
                                                         reinterpret_cast<uint32_t *>(ws + L.off_counts));
     else
-        item_prefix_kernel<16><<<L.n_tiles, 256, 0, st>>>(nitems, ibase, L.tiles_x, ra.cam->width, ra.cam->height,
-                                                          a.icnt, reinterpret_cast<uint32_t *>(ws + L.off_counts));
-    const int64_t n = (int64_t)ra.cam->width * ra.cam->height;
+        item_prefix_kernel<16><<<L.n_tiles, 256, 0, st>>>(nitems, ibase, ra.vt, a.icnt,
+                                                          reinterpret_cast<uint32_t *>(ws + L.off_counts));
+    const int64_t n = L.npx;
     scan_u32_kernel<<<(unsigned)L.scan_blocks, kScanThreads, 0, st>>>(
         reinterpret_cast<const uint32_t *>(ws + L.off_counts), reinterpret_cast<uint32_t *>(ws + L.off_offsets), n,
         L.scan_blocks, reinterpret_cast<unsigned long long *>(ws + L.off_scan_state), &status->scan_ticket,

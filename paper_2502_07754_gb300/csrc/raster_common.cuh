@@ -11,7 +11,7 @@ namespace ms {
 struct SceneDev {
     const float *xyz, *rgb, *alpha;
     int K;
-    CamDev cam;
+    const CamDev *cam;   // points into the kernel's __grid_constant__ view table
     int W, H;
 };
 
@@ -161,7 +161,7 @@ __device__ __forceinline__ void stage_fan(const SceneDev &a, const Stage &s, int
     const float *p = a.xyz + (size_t)fan * KV * 3;
     uint32_t vmask = 0;
     for (int k = 0; k < KV; ++k) {
-        const DVert d = decide_vertex(a.cam, __ldg(p + 3 * k), __ldg(p + 3 * k + 1), __ldg(p + 3 * k + 2));
+        const DVert d = decide_vertex(*a.cam, __ldg(p + 3 * k), __ldg(p + 3 * k + 1), __ldg(p + 3 * k + 2));
         s.vx[k * CH + slot] = d.xs;
         s.vy[k * CH + slot] = d.ys;
         s.vz[k * CH + slot] = d.Z;
@@ -212,7 +212,7 @@ __device__ __forceinline__ void stage_fan(const SceneDev &a, const Stage &s, int
     s.rect[slot] = make_int4(r.i0, r.i1, r.j0, r.j1);
     if (level < kStageValues) return;
     const float m[3] = {__ldg(p), __ldg(p + 1), __ldg(p + 2)};
-    const CentreProj cp = project_centre(a.cam, m);
+    const CentreProj cp = project_centre(*a.cam, m);
     s.cxh[slot] = cp.xh;
     s.cxl[slot] = cp.xl;
     s.cyh[slot] = cp.yh;
@@ -221,7 +221,7 @@ __device__ __forceinline__ void stage_fan(const SceneDev &a, const Stage &s, int
         const float d[3] = {__ldg(p + 3 * (1 + i)) - m[0], __ldg(p + 3 * (1 + i) + 1) - m[1],
                             __ldg(p + 3 * (1 + i) + 2) - m[2]};
         float du, dv, X, Y, Z;
-        vertex_offset(a.cam, cp, d, du, dv, X, Y, Z);
+        vertex_offset(*a.cam, cp, d, du, dv, X, Y, Z);
         s.du[i * CH + slot] = du;
         s.dv[i * CH + slot] = dv;
         if (level >= kStageGrad) {

@@ -24,18 +24,18 @@ namespace ms {
 namespace {
 
 struct ResolveArgs {
-    SceneDev sc;
+    int K;
+    int64_t npx;
     const uint32_t *counts, *offsets;
     float4 *frags;
     int64_t frag_cap;
     int depth_bits;
     float T_eps, bg0, bg1, bg2;
     Status *st;
-    float *out;
     float *tfinal;
     uint32_t *ncommit;
-    const float *out_fwd, *dL;
     float4 *grad;
+    ViewTable vt;
 };
 
 // Chain rule from one composited fragment's dL/dc (gc0..2) and dL/da (ga) to its three
@@ -44,8 +44,8 @@ struct ResolveArgs {
 // mu_k = w_k / W with w_k = E_k / Z_k, E_k = cross(u_a, u_b) for the edge opposite k;
 // screen position -> view space -> world space through R_cw^T.  Gradients go to the
 // (xyz, alpha | rgb, 0) scratch with two 16-byte vector atomics per vertex.
-__device__ __forceinline__ void chain_to_vertices(const ResolveArgs &a, const float4 *r, uint32_t tri, float gc0,
-                                                  float gc1, float gc2, float ga) {
+__device__ __forceinline__ void chain_to_vertices(const ResolveArgs &a, const CamDev &c, const float4 *r,
+                                                  uint32_t tri, float gc0, float gc1, float gc2, float ga) {
     const float4 r2 = r[2], r3 = r[3], r4 = r[4], r5 = r[5], r6 = r[6], r7 = r[7], r8 = r[8], r9 = r[9];
     const float mu[3] = {r2.x, r2.y, r2.z};
     const float iW = 1.0f / r2.w;
@@ -73,10 +73,9 @@ __device__ __forceinline__ void chain_to_vertices(const ResolveArgs &a, const fl
         guy[ib] += gE * ux[ia];
         gux[ib] -= gE * uy[ia];
     }
-    const int K = a.sc.K, KV = K + 1;
+    const int K = a.K, KV = K + 1;
     const uint32_t fan = tri / (uint32_t)K, j = tri - fan * (uint32_t)K;
     const uint32_t vid[3] = {fan * KV, fan * KV + 1 + j, fan * KV + 1 + (j + 1 == (uint32_t)K ? 0 : j + 1)};
-    const CamDev &c = a.sc.cam;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         const float gX = gux[k] * c.fx * iz[k];
@@ -101,13 +100,12 @@ __device__ __forceinline__ bool frag_less(float za, uint32_t ta, float zb, uint3
 }
 
 template <int KB, bool BWD>
-__global__ void __launch_bounds__(256) resolve_kernel(ResolveArgs a) {
-    const int64_t npx = (int64_t)a.sc.W * a.sc.H;
+__global__ void __launch_bounds__(256) resolve_kernel(const __grid_constant__ ResolveArgs a) {
     const int64_t pix0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool valid = pix0 < npx;
+    const bool valid = pix0 < a.npx;
     const int64_t pix = valid ? pix0 : 0;
-    const int px = (int)(pix % a.sc.W), py = (int)(pix / a.sc.W);
-    const float pxc = (float)px + 0.5f, pyc = (float)py + 0.5f;
+    const ViewDev &vw = a.vt.v[view_of_pixel(a.vt, (unsigned long long)pix)];
+    const int64_t lpix = pix - (int64_t)vw.pix_base;   // index within the view's image
     int n = valid ? (int)a.counts[pix] : 0;
     const int64_t off = a.offsets[pix];
     if (off + n > a.frag_cap) n = 0;   // the buffer overflowed: reported through the status block
@@ -115,7 +113,7 @@ __global__ void __launch_bounds__(256) resolve_kernel(ResolveArgs a) {
     float4 *rec = a.frags + (size_t)RS * off;
 
     float T = 1.0f, C0 = 0.0f, C1 = 0.0f, C2 = 0.0f;
-    float kz[KB], kr[KB], kg[KB], kb[KB], ka[KB];
+    float kz[KB];              // pending fragments sorted by (depth, triangle)
     uint32_t kt[KB], ki[KB];   // triangle id, record index
     int nb = 0;
     float fz = 0.0f;           // last committed (depth, triangle); depths are > 0
@@ -131,22 +129,27 @@ __global__ void __launch_bounds__(256) resolve_kernel(ResolveArgs a) {
     if (BWD && valid) {
         ncom_limit = a.ncommit[pix];
         Tout = a.tfinal[pix];
-        const float4 g = reinterpret_cast<const float4 *>(a.dL)[pix];
-        const float4 ov = reinterpret_cast<const float4 *>(a.out_fwd)[pix];
+        const float4 g = reinterpret_cast<const float4 *>(vw.dL)[lpix];
+        const float4 ov = reinterpret_cast<const float4 *>(vw.out_fwd)[lpix];
         gR = g.x; gG = g.y; gB = g.z; gA = g.w;
         oR = ov.x; oG = ov.y; oB = ov.z;
         if (ncom_limit == 0) done = true;
     }
 
     auto commit_front = [&]() {
-        const float al = ka[0], c0 = kr[0], c1 = kg[0], c2 = kb[0];
+        // colour and opacity are re-read from the record (an L1 / L2 hit) rather than
+        // carried in the pending buffer, which keeps the buffer at three registers a slot
+        const float4 *rc = rec + (size_t)RS * ki[0];
+        const float al = rc[0].w;
+        const float4 col = rc[1];
+        const float c0 = col.x, c1 = col.y, c2 = col.z;
         const float w = T * al;
         if (BWD) {
             const float nC0 = C0 + w * c0, nC1 = C1 + w * c1, nC2 = C2 + w * c2;
             const float inv = 1.0f / fmaxf(1.0f - al, 1e-6f);
             const float ga = gR * (T * c0 - (oR - nC0) * inv) + gG * (T * c1 - (oG - nC1) * inv) +
                              gB * (T * c2 - (oB - nC2) * inv) + gA * Tout * inv;
-            chain_to_vertices(a, rec + (size_t)RS * ki[0], kt[0], gR * w, gG * w, gB * w, ga);
+            chain_to_vertices(a, vw.cam, rc, kt[0], gR * w, gG * w, gB * w, ga);
             C0 = nC0; C1 = nC1; C2 = nC2;
         } else {
             C0 += w * c0;
@@ -161,7 +164,6 @@ __global__ void __launch_bounds__(256) resolve_kernel(ResolveArgs a) {
 #pragma unroll
         for (int i = 0; i + 1 < KB; ++i) {
             kz[i] = kz[i + 1]; kt[i] = kt[i + 1]; ki[i] = ki[i + 1];
-            kr[i] = kr[i + 1]; kg[i] = kg[i + 1]; kb[i] = kb[i + 1]; ka[i] = ka[i + 1];
         }
         --nb;
         if (BWD ? (ncom >= ncom_limit) : (T < a.T_eps)) {
@@ -200,24 +202,20 @@ __global__ void __launch_bounds__(256) resolve_kernel(ResolveArgs a) {
                     continue;
                 }
             }
-            const float4 r1 = rec[RS * i + 1];
             bool placed = false;
 #pragma unroll
             for (int s = KB - 1; s >= 1; --s) {
                 if (s <= nb && !placed) {
                     if (frag_less(z, tri, kz[s - 1], kt[s - 1])) {
                         kz[s] = kz[s - 1]; kt[s] = kt[s - 1]; ki[s] = ki[s - 1];
-                        kr[s] = kr[s - 1]; kg[s] = kg[s - 1]; kb[s] = kb[s - 1]; ka[s] = ka[s - 1];
                     } else {
                         kz[s] = z; kt[s] = tri; ki[s] = (uint32_t)i;
-                        kr[s] = r1.x; kg[s] = r1.y; kb[s] = r1.z; ka[s] = r0.w;
                         placed = true;
                     }
                 }
             }
             if (!placed) {
                 kz[0] = z; kt[0] = tri; ki[0] = (uint32_t)i;
-                kr[0] = r1.x; kg[0] = r1.y; kb[0] = r1.z; ka[0] = r0.w;
             }
             ++nb;
         }
@@ -231,7 +229,7 @@ __global__ void __launch_bounds__(256) resolve_kernel(ResolveArgs a) {
     }
     if (!BWD) {
         if (valid) {
-            reinterpret_cast<float4 *>(a.out)[pix] =
+            reinterpret_cast<float4 *>(vw.out)[lpix] =
                 make_float4(C0 + T * a.bg0, C1 + T * a.bg1, C2 + T * a.bg2, 1.0f - T);
             a.tfinal[pix] = T;
             a.ncommit[pix] = ncom;
@@ -269,15 +267,9 @@ __global__ void grad_scatter_kernel(const float4 *__restrict__ g, int64_t V, flo
 
 cudaError_t launch_resolve(const RenderArgs &ra, bool backward, cudaStream_t st) {
     const RenderLayout &L = ra.L;
-    const int64_t npx = (int64_t)ra.cam->width * ra.cam->height;
     ResolveArgs a;
-    a.sc.xyz = ra.xyz;
-    a.sc.rgb = ra.rgb;
-    a.sc.alpha = ra.alpha;
-    a.sc.K = ra.K;
-    a.sc.cam = make_cam(*ra.cam);
-    a.sc.W = ra.cam->width;
-    a.sc.H = ra.cam->height;
+    a.K = ra.K;
+    a.npx = L.npx;
     a.counts = reinterpret_cast<const uint32_t *>(ra.ws + L.off_counts);
     a.offsets = reinterpret_cast<const uint32_t *>(ra.ws + L.off_offsets);
     a.frags = reinterpret_cast<float4 *>(ra.ws + L.off_frags);
@@ -288,13 +280,11 @@ cudaError_t launch_resolve(const RenderArgs &ra, bool backward, cudaStream_t st)
     a.bg1 = ra.prm.bg[1];
     a.bg2 = ra.prm.bg[2];
     a.st = reinterpret_cast<Status *>(ra.ws + L.off_status);
-    a.out = ra.out_rgba;
     a.tfinal = reinterpret_cast<float *>(ra.ws + L.off_tfinal);
     a.ncommit = reinterpret_cast<uint32_t *>(ra.ws + L.off_ncommit);
-    a.out_fwd = ra.out_fwd;
-    a.dL = ra.dL;
     a.grad = reinterpret_cast<float4 *>(ra.ws + L.off_grad);
-    return backward ? launch_k<true>(a, L.kbuf, npx, st) : launch_k<false>(a, L.kbuf, npx, st);
+    a.vt = ra.vt;
+    return backward ? launch_k<true>(a, L.kbuf, L.npx, st) : launch_k<false>(a, L.kbuf, L.npx, st);
 }
 
 cudaError_t launch_grad_scatter(const RenderArgs &ra, cudaStream_t st) {
