@@ -46,6 +46,7 @@ def parse():
     p.add_argument("--gaussians", type=int, default=0, help="override the Gaussian count (profiling cases)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-autotune", action="store_true")
     return p.parse_args()
 
 
@@ -203,6 +204,50 @@ def run_reference(args, ws, rank):
 
 # --------------------------------------------------------------------------- GPU arm
 
+def stage_report(stage_ms, stage_n, info, sc, V, K, npx, local):
+    """Per-stage achieved rate against its roofline, and the dominant stage's roofline
+    entry.  Algorithmic work per launch: HBM bytes for the streaming stages, FP32
+    lane-operations for the rasterisation / resolve (unit figures in the design notes)."""
+    import torch
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    per_launch = {STAGES[i]: stage_ms[i] / max(stage_n[i], 1) for i in range(7)}
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    alu_peak = n_sm * 128 * sm_max * 1e6 / 1e12           # FP32 lane-ops per second, TOP/s
+    cov_ops = info.rect_tests * 10 * K + info.fragments * 40
+    comp_ops = {"raster": 2 * cov_ops, "raster_bwd": cov_ops + info.commits * 120}
+    nb = (sc.sh_degree + 1) ** 2 * 3 * (2 if sc.sh_bf16 else 4)
+    hbm_bytes = {"mesh_build": sc.n * (44 + nb) + V * 28,
+                 "bin": V * 12 + info.pairs * 12,
+                 "sort": info.pairs * (8 + 24 * ((info.sort_bits + 7) // 8)),
+                 "loss": npx * 48,
+                 "adam": V * 7 * 28}
+    stages = {}
+    for s_ in STAGES:
+        t = per_launch[s_]
+        if t <= 0:
+            continue
+        if s_ in hbm_bytes:
+            ach = hbm_bytes[s_] / (t * 1e-3) / 1e9
+            stages[s_] = {"ms": t, "bound": "hbm", "achieved": ach, "unit": "GB/s", "frac": ach / hbm}
+        else:
+            ach = comp_ops[s_] / (t * 1e-3) / 1e12
+            stages[s_] = {"ms": t, "bound": "alu", "achieved": ach, "unit": "TOP/s", "frac": ach / alu_peak}
+    dom = max(stages, key=lambda s_: stages[s_]["ms"])
+    d = stages[dom]
+    roof = {"kernel": dom, "bound": d["bound"], "achieved": d["achieved"],
+            "peak": hbm if d["bound"] == "hbm" else alu_peak, "unit": d["unit"], "frac": d["frac"],
+            "peak_source": ("measured hbm_gbs (MEASURED_PEAKS.json)" if d["bound"] == "hbm" else
+                            f"{n_sm} SMs x 128 FP32 lanes x {sm_max:.0f} MHz (max SM clock)"),
+            "traffic": TRAFFIC.get(dom)}
+    return stages, roof
+
+
 def run_ours(args, ws, rank, local):
     import torch
 
@@ -325,44 +370,7 @@ def run_ours(args, ws, rank, local):
 
     if rank != 0:
         return
-    # ---- roofline of the dominant kernel
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except OSError:
-        pass
-    hbm = float(peaks.get("hbm_gbs", 6800.0))
-    per_launch = {STAGES[i]: stage_ms[i] / max(stage_n[i], 1) for i in range(7)}
-    clocks = clk.summary()
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    props = torch.cuda.get_device_properties(local)
-    n_sm = props.multi_processor_count
-    alu_peak = n_sm * 128 * sm_max * 1e6 / 1e12           # FP32 lane-ops per second, TOP/s
-    # algorithmic work per launch (unit figures stated in the design notes)
-    cov_ops = info.rect_tests * 10 * K + info.fragments * 40
-    comp_ops = {"raster": 2 * cov_ops, "raster_bwd": cov_ops + info.commits * 120}
-    nb = (sc.sh_degree + 1) ** 2 * 3 * (2 if sc.sh_bf16 else 4)
-    hbm_bytes = {"mesh_build": sc.n * (44 + nb) + V * 28,
-                 "bin": V * 12 + info.pairs * 12,
-                 "sort": info.pairs * (8 + 24 * ((info.sort_bits + 7) // 8)),
-                 "loss": W * H * 48,
-                 "adam": V * 7 * 28}
-    stages = {}
-    for s_ in STAGES:
-        t = per_launch[s_]
-        if s_ in hbm_bytes:
-            ach = hbm_bytes[s_] / (t * 1e-3) / 1e9
-            stages[s_] = {"ms": t, "bound": "hbm", "achieved": ach, "unit": "GB/s", "frac": ach / hbm}
-        else:
-            ach = comp_ops[s_] / (t * 1e-3) / 1e12
-            stages[s_] = {"ms": t, "bound": "alu", "achieved": ach, "unit": "TOP/s", "frac": ach / alu_peak}
-    dom = max(STAGES, key=lambda s_: per_launch[s_])
-    d = stages[dom]
-    roof = {"kernel": dom, "bound": d["bound"], "achieved": d["achieved"],
-            "peak": hbm if d["bound"] == "hbm" else alu_peak, "unit": d["unit"], "frac": d["frac"],
-            "peak_source": ("measured hbm_gbs (MEASURED_PEAKS.json)" if d["bound"] == "hbm" else
-                            f"{n_sm} SMs x 128 FP32 lanes x {sm_max:.0f} MHz (max SM clock)"),
-            "traffic": TRAFFIC.get(dom)}
+    stages, roof = stage_report(stage_ms, stage_n, info, sc, V, K, W * H, local)
     line = {"metric": METRIC, "value": ws * mpix(W, H, step_ms), "unit": "Mpix/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -371,9 +379,163 @@ def run_ours(args, ws, rank, local):
                        "step": "mesh_build+render+l1+render_backward+adam",
                        "l2": "flushed before every timed step (256 MB write)", "parallelism": "replicas"},
             "fwd_mpix_s": ws * mpix(W, H, fwd_ms), "fwd_ms": fwd_ms,
-            "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks, "roofline": roof, "stages": stages,
+            "e2e": e2e, "gpu_launches": int(launches), "clocks": clk.summary(), "roofline": roof, "stages": stages,
             "work": {"pairs": info.pairs, "rect_tests": info.rect_tests, "fragments": info.fragments,
                      "commits": info.commits, "extra_passes": info.extra_passes, "sort_bits": info.sort_bits}}
+    if not args.no_cpu_baseline and ws == 1:
+        line["cpu_baseline"] = cpu_baseline(w, K)
+    print(json.dumps(line), flush=True)
+
+
+def run_batch(args, ws, rank, local):
+    """The batched multi-view step: 16 cameras of mixed resolution over one fan soup.
+    One step = fan conversion, batch render of all views, L1 over all views, batch
+    adjoint and Adam, captured once in a CUDA graph and replayed; tile size, pending
+    buffer and list capacities come from the autotuner.  `value` = pixels of all views
+    per second of the forward+backward step."""
+    import torch
+
+    import synthetic
+    import paper_2502_07754_gb300 as ms
+    from paper_2502_07754_gb300 import _lib
+
+    torch.cuda.set_device(local)
+    if rank == 0:
+        _lib.lib()
+    barrier(ws)
+    L = _lib.lib(build_if_missing=False)
+    w = synthetic.workload(args.workload, n=args.gaussians or None)
+    sc, K, cams = w.scene, w.K, w.cameras
+    centre = cams[0].C          # SH colours are evaluated once per step for the shared soup
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    sh_host = sc.sh.view(np.int16) if sc.sh_bf16 else sc.sh
+    G = [dev(sc.means), dev(sc.log_scales), dev(sc.quats), dev(sc.opacity), dev(sh_host)]
+    br = ms.BatchRenderer(sc.n, K, cams)
+    npx = br.n_pixels
+
+    tg = w.target_scene
+    tG = [dev(tg.means), dev(tg.log_scales), dev(tg.quats), dev(tg.opacity), G[4]]
+    target = br.forward(*ms.mesh_build(*tG, tg.sh_degree, K=K, cam_center=centre)).clone()
+    del tG
+
+    xyz, rgb, a = ms.mesh_build(*G, sc.sh_degree, K=K, cam_center=centre)
+    br.forward(xyz, rgb, a)
+    tune = None
+    if not args.no_autotune:
+        tune = br.autotune(xyz, rgb, a, reps=2, headroom=0.05)
+    V = xyz.shape[0]
+    flat = br.new_flat()
+    grads = [torch.zeros_like(xyz), torch.zeros_like(rgb), torch.zeros_like(a)]
+    adam = ms.FanAdam(xyz, rgb, a, device_step=True)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def step(gs):
+        x, c, al = ms.mesh_build(*gs, sc.sh_degree, K=K, cam_center=centre, out=(xyz, rgb, a))
+        br.forward(x, c, al, flat, check_status=False)
+        loss, dL = ms.l1_loss(flat, target)
+        for t in grads:
+            t.zero_()
+        br.backward(x, c, al, flat, dL, *grads)
+        adam.step(x, c, al, *grads)
+        return loss
+
+    # capture one step in a CUDA graph (after an eager warm-up on a side stream)
+    s_ = torch.cuda.Stream()
+    s_.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s_):
+        step(G)
+    torch.cuda.current_stream().wait_stream(s_)
+    graph = torch.cuda.CUDAGraph()
+    l0 = L.ms_kernel_launches()
+    with torch.cuda.graph(graph):
+        loss_g = step(G)
+    launches = L.ms_kernel_launches() - l0
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        graph.replay()
+    torch.cuda.synchronize()
+    st, info = br.info()
+    _lib.check(st)
+
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    barrier(ws)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for i in range(args.steps):
+            flush.zero_()
+            ev0[i].record(stream)
+            graph.replay()
+            ev1[i].record(stream)
+        torch.cuda.synchronize()
+    barrier(ws)
+    step_ms = max_over_ranks(sum(a_.elapsed_time(b_) for a_, b_ in zip(ev0, ev1)) / args.steps, ws)
+    st, info = br.info()
+    _lib.check(st)
+
+    # forward-only batch render (eager call)
+    f0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    f1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    for i in range(args.steps):
+        flush.zero_()
+        f0[i].record(stream)
+        br.forward(xyz, rgb, a, flat, check_status=False)
+        f1[i].record(stream)
+    torch.cuda.synchronize()
+    fwd_ms = max_over_ranks(sum(a_.elapsed_time(b_) for a_, b_ in zip(f0, f1)) / args.steps, ws)
+
+    # per-stage times from eager steps with the stage profiler on (not the headline number)
+    L.ms_profile_read(None, None, 0)
+    L.ms_profile_enable(1)
+    for _ in range(3):
+        flush.zero_()
+        step(G)
+    torch.cuda.synchronize()
+    L.ms_profile_enable(0)
+    stage_ms = (C.c_double * 7)()
+    stage_n = (C.c_int64 * 7)()
+    _lib.check(L.ms_profile_read(stage_ms, stage_n, 7))
+
+    e2e = None
+    if not args.no_e2e:
+        hostG = [torch.from_numpy(np.ascontiguousarray(a_)).pin_memory() for a_ in
+                 (sc.means, sc.log_scales, sc.quats, sc.opacity, sh_host)]
+        loss_host = torch.empty(1, dtype=torch.float32).pin_memory()
+        h2d = sum(h.numel() * h.element_size() for h in hostG)
+        e0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        e1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        for i in range(args.steps):
+            flush.zero_()
+            e0[i].record(stream)
+            for d_, h_ in zip(G, hostG):
+                d_.copy_(h_, non_blocking=True)
+            graph.replay()
+            loss_host.copy_(loss_g, non_blocking=True)
+            e1[i].record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = max_over_ranks(sum(a_.elapsed_time(b_) for a_, b_ in zip(e0, e1)) / args.steps, ws)
+        e2e = {"value": ws * npx / (e2e_ms * 1e-3) / 1e6, "unit": "Mpix/s", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": 4, "ms_per_step": e2e_ms}
+    if rank != 0:
+        return
+    stages, roof = stage_report(stage_ms, stage_n, info, sc, V, K, npx, local)
+    res = sorted({(c.width, c.height) for c in cams})
+    line = {"metric": METRIC, "value": ws * npx / (step_ms * 1e-3) / 1e6, "unit": "Mpix/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w.name, "gaussians": sc.n, "K": K, "views": len(cams), "pixels": npx,
+                       "resolutions": [f"{a_}x{b_}" for a_, b_ in res],
+                       "sh": f"degree {sc.sh_degree} {'bf16' if sc.sh_bf16 else 'f32'}",
+                       "step": "mesh_build+batch_render+l1+batch_render_backward+adam in one CUDA graph",
+                       "tile": int(br.params.tile), "kbuf": int(br.params.kbuf),
+                       "l2": "flushed before every timed step (256 MB write)", "parallelism": "replicas"},
+            "fwd_mpix_s": ws * npx / (fwd_ms * 1e-3) / 1e6, "fwd_ms": fwd_ms,
+            "e2e": e2e, "gpu_launches": int(launches), "clocks": clk.summary(), "roofline": roof, "stages": stages,
+            "work": {"pairs": info.pairs, "rect_tests": info.rect_tests, "fragments": info.fragments,
+                     "commits": info.commits, "extra_passes": info.extra_passes, "sort_bits": info.sort_bits}}
+    if tune is not None:
+        line["autotune"] = {"cand_ms": [round(x, 3) for x in tune.cand_ms], "best": tune.best,
+                            "candidates": "tile 8<<(c//2) x kbuf 8<<(c%2); -1 = not built"}
     if not args.no_cpu_baseline and ws == 1:
         line["cpu_baseline"] = cpu_baseline(w, K)
     print(json.dumps(line), flush=True)
@@ -388,7 +550,10 @@ def main():
         run_reference(args, ws, rank)
         return
     ws, rank, local = dist_setup()
-    run_ours(args, ws, rank, local)
+    if args.workload == 4:
+        run_batch(args, ws, rank, local)
+    else:
+        run_ours(args, ws, rank, local)
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

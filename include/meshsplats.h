@@ -273,6 +273,17 @@ MS_API ms_status ms_adam_step(float *xyz, float *rgb, float *alpha, const float 
                               float lr_color, float lr_xyz, float beta1, float beta2, float eps, void *stream);
 
 /*
+ * ms_adam_step with the step number kept on the device: *d_step (device int32, 0 before
+ * the first step) is advanced by one on the stream and the bias corrections use the new
+ * value.  A captured CUDA graph of a fine-tune step therefore replays with the right
+ * step number on every launch.
+ */
+MS_API ms_status ms_adam_step_counted(float *xyz, float *rgb, float *alpha, const float *d_xyz, const float *d_rgb,
+                                      const float *d_alpha, float *m, float *v, int64_t V, int32_t *d_step,
+                                      float lr_color, float lr_xyz, float beta1, float beta2, float eps,
+                                      void *stream);
+
+/*
  * Forward render without a caller workspace.  The paper has no counterpart: this entry
  * point exists for callers that cannot allocate device memory -- a plugin whose host
  * application owns the GPU memory budget, code running while a stream is being captured

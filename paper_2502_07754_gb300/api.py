@@ -57,15 +57,21 @@ def render_params(tile=16, kbuf=8, T_eps=1e-5, bg=(0.0, 0.0, 0.0), pair_capacity
 
 
 def mesh_build(means, log_scales, quats, opacity, sh, sh_degree, K=8, scale_mul=SCALE_MUL, opac_mul=OPAC_MUL,
-               axis_rule=1, cam_center=None, corr=None, stream=None):
+               axis_rule=1, cam_center=None, corr=None, stream=None, out=None):
     """Gaussians -> fan soup (xyz, rgb, alpha) on the device.  sh is float32 or a uint16 /
-    int16 / bfloat16 tensor of bfloat16 bits, shape (N, (deg+1)^2, 3)."""
+    int16 / bfloat16 tensor of bfloat16 bits, shape (N, (deg+1)^2, 3).  `out` may give the
+    three output tensors (V x 3, V x 3, V) to write into."""
     N = means.shape[0]
     dev = means.device
     V = N * (K + 1)
-    xyz = torch.empty(V, 3, device=dev, dtype=torch.float32)
-    rgb = torch.empty(V, 3, device=dev, dtype=torch.float32)
-    alpha = torch.empty(V, device=dev, dtype=torch.float32)
+    if out is not None:
+        xyz, rgb, alpha = out
+        if xyz.shape != (V, 3) or rgb.shape != (V, 3) or alpha.shape != (V,):
+            raise ValueError("out tensors do not match N (K+1) vertices")
+    else:
+        xyz = torch.empty(V, 3, device=dev, dtype=torch.float32)
+        rgb = torch.empty(V, 3, device=dev, dtype=torch.float32)
+        alpha = torch.empty(V, device=dev, dtype=torch.float32)
     fp = _lib.FanParams(int(K), float(scale_mul), float(opac_mul), int(axis_rule))
     sh_dtype = 0 if sh.dtype == torch.float32 else 1
     cc = (C.c_float * 3)(*[float(x) for x in cam_center]) if cam_center is not None else None
@@ -283,17 +289,27 @@ def l1_loss(img_rgba, target_rgba, stream=None):
 
 
 class FanAdam:
-    """Adam over the fan soup: colours/opacities at lr_color, positions at exp(-3) lr_color."""
+    """Adam over the fan soup: colours/opacities at lr_color, positions at exp(-3) lr_color.
+    With device_step=True the step number lives on the device (ms_adam_step_counted), so
+    the update can be captured in a CUDA graph and replayed."""
 
-    def __init__(self, xyz, rgb, alpha, lr_color=5e-3, betas=(0.9, 0.999), eps=1e-15):
+    def __init__(self, xyz, rgb, alpha, lr_color=5e-3, betas=(0.9, 0.999), eps=1e-15, device_step=False):
         self.V = xyz.shape[0]
         self.lr_color = lr_color
         self.betas, self.eps = betas, eps
         self.m = torch.zeros(7 * self.V, device=xyz.device)
         self.v = torch.zeros(7 * self.V, device=xyz.device)
         self.t = 0
+        self.d_step = torch.zeros(1, dtype=torch.int32, device=xyz.device) if device_step else None
 
     def step(self, xyz, rgb, alpha, d_xyz, d_rgb, d_alpha, stream=None):
+        if self.d_step is not None:
+            check(lib().ms_adam_step_counted(_ptr(xyz), _ptr(rgb), _ptr(alpha), _ptr(d_xyz), _ptr(d_rgb),
+                                             _ptr(d_alpha), _ptr(self.m), _ptr(self.v), self.V, _ptr(self.d_step),
+                                             float(self.lr_color), float(self.lr_color * LR_XYZ_RATIO),
+                                             float(self.betas[0]), float(self.betas[1]), float(self.eps),
+                                             _stream(stream)))
+            return
         self.t += 1
         check(lib().ms_adam_step(_ptr(xyz), _ptr(rgb), _ptr(alpha), _ptr(d_xyz), _ptr(d_rgb), _ptr(d_alpha),
                                  _ptr(self.m), _ptr(self.v), self.V, self.t, float(self.lr_color),

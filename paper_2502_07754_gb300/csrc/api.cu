@@ -440,21 +440,37 @@ MS_API ms_status ms_l1_loss(const float *img_rgba, const float *target_rgba, int
     return MS_OK;
 }
 
-MS_API ms_status ms_adam_step(float *xyz, float *rgb, float *alpha, const float *d_xyz, const float *d_rgb,
-                              const float *d_alpha, float *m, float *v, int64_t V, int32_t step, float lr_color,
-                              float lr_xyz, float beta1, float beta2, float eps, void *stream) {
-    if (V < 0 || step < 1) return fail(MS_ERR_INVALID, "bad V or step");
+static ms_status adam_common(float *xyz, float *rgb, float *alpha, const float *d_xyz, const float *d_rgb,
+                             const float *d_alpha, float *m, float *v, int64_t V, int32_t step, int32_t *d_step,
+                             float lr_color, float lr_xyz, float beta1, float beta2, float eps, void *stream) {
     if (V > 0 && (!xyz || !rgb || !alpha || !d_xyz || !d_rgb || !d_alpha || !m || !v))
         return fail(MS_ERR_INVALID, "NULL pointer");
     cudaError_t e;
     {
         StageScope sc(MS_STAGE_ADAM, (cudaStream_t)stream);
-        e = launch_adam(xyz, rgb, alpha, d_xyz, d_rgb, d_alpha, m, v, V, step, lr_color, lr_xyz, beta1, beta2, eps,
-                        (cudaStream_t)stream);
+        e = launch_adam(xyz, rgb, alpha, d_xyz, d_rgb, d_alpha, m, v, V, step, d_step, lr_color, lr_xyz, beta1, beta2,
+                        eps, (cudaStream_t)stream);
     }
     if (e != cudaSuccess) return cuda_fail(e, "adam launch");
-    if (V > 0) count_launches(1);
+    count_launches((V > 0 ? 1 : 0) + (d_step ? 1 : 0));
     return MS_OK;
+}
+
+MS_API ms_status ms_adam_step(float *xyz, float *rgb, float *alpha, const float *d_xyz, const float *d_rgb,
+                              const float *d_alpha, float *m, float *v, int64_t V, int32_t step, float lr_color,
+                              float lr_xyz, float beta1, float beta2, float eps, void *stream) {
+    if (V < 0 || step < 1) return fail(MS_ERR_INVALID, "bad V or step");
+    return adam_common(xyz, rgb, alpha, d_xyz, d_rgb, d_alpha, m, v, V, step, nullptr, lr_color, lr_xyz, beta1, beta2,
+                       eps, stream);
+}
+
+MS_API ms_status ms_adam_step_counted(float *xyz, float *rgb, float *alpha, const float *d_xyz, const float *d_rgb,
+                                      const float *d_alpha, float *m, float *v, int64_t V, int32_t *d_step,
+                                      float lr_color, float lr_xyz, float beta1, float beta2, float eps,
+                                      void *stream) {
+    if (V < 0 || !d_step) return fail(MS_ERR_INVALID, "bad V or NULL step counter");
+    return adam_common(xyz, rgb, alpha, d_xyz, d_rgb, d_alpha, m, v, V, 1, d_step, lr_color, lr_xyz, beta1, beta2,
+                       eps, stream);
 }
 
 MS_API void ms_profile_enable(int32_t on) { g_prof = on != 0; }

@@ -11,17 +11,19 @@ struct FanRect {
     bool empty;
 };
 
-// Pixel centres i + 0.5 within [min x - 0.5, max x + 0.5] (and the same in y) of the
-// vertices of the fan's valid triangles.  The half-pixel margin exceeds the binary32
-// rounding of the edge test for coordinates within the +-2^17 guard band, so no
-// covered centre falls outside.  min/max are order independent, so every caller that
-// feeds the same vertex set gets the same rectangle.
+// Pixel centres i + 0.5 within [min x - 0.25, max x + 0.25] (and the same in y) of the
+// vertices of the fan's valid triangles.  Bound on the binary32 edge test: a centre p it
+// accepts lies within 2.1 * 2^-24 * (|p - a|_1) of each edge line (a = the edge's lower
+// vertex), plus the turn of the rounded edge direction, < 0.07 + 0.03 px for anything in
+// the +-2^17 guard band; the quarter-pixel margin exceeds that, so no covered centre
+// falls outside.  min/max are order independent, so every caller that feeds the same
+// vertex set gets the same rectangle.
 __device__ __forceinline__ FanRect rect_from_bounds(float mnx, float mxx, float mny, float mxy, int W, int H) {
     FanRect r;
-    r.i0 = max((int)floorf(mnx - 1.0f), 0);
-    r.i1 = min((int)floorf(mxx), W - 1);
-    r.j0 = max((int)floorf(mny - 1.0f), 0);
-    r.j1 = min((int)floorf(mxy), H - 1);
+    r.i0 = max((int)ceilf(mnx - 0.75f), 0);
+    r.i1 = min((int)floorf(mxx - 0.25f), W - 1);
+    r.j0 = max((int)ceilf(mny - 0.75f), 0);
+    r.j1 = min((int)floorf(mxy - 0.25f), H - 1);
     r.empty = r.i0 > r.i1 || r.j0 > r.j1;
     return r;
 }

@@ -77,7 +77,7 @@ struct StageScope {
 
 cudaError_t launch_l1(const float *img, const float *tgt, int64_t n_pixels, float *dL, float *loss, cudaStream_t st);
 cudaError_t launch_adam(float *xyz, float *rgb, float *alpha, const float *dx, const float *dc, const float *da,
-                        float *m, float *v, int64_t V, int step, float lr_c, float lr_x, float b1, float b2, float eps,
-                        cudaStream_t st);
+                        float *m, float *v, int64_t V, int step, int32_t *d_step, float lr_c, float lr_x, float b1,
+                        float b2, float eps, cudaStream_t st);
 
 }  // namespace ms

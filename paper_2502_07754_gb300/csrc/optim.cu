@@ -38,11 +38,17 @@ __device__ __forceinline__ float adam1(float &p, float g, float &m, float &v, fl
     return p;
 }
 
-// Moments are stored as 7 planes of V floats: x, y, z, r, g, b, alpha.
+// Moments are stored as 7 planes of V floats: x, y, z, r, g, b, alpha.  With a device
+// step counter the bias corrections come from *step (already advanced by step_advance).
 __global__ void adam_kernel(float *__restrict__ xyz, float *__restrict__ rgb, float *__restrict__ alpha,
                             const float *__restrict__ dx, const float *__restrict__ dc, const float *__restrict__ da,
                             float *__restrict__ m, float *__restrict__ v, int64_t V, float lr_c, float lr_x, float b1,
-                            float b2, float eps, float bc1, float bc2) {
+                            float b2, float eps, float bc1, float bc2, const int32_t *step) {
+    if (step) {
+        const float t = (float)*step;
+        bc1 = 1.0f - powf(b1, t);
+        bc2 = 1.0f - powf(b2, t);
+    }
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < V; i += (int64_t)gridDim.x * blockDim.x) {
 #pragma unroll
         for (int r = 0; r < 3; ++r) {
@@ -68,6 +74,8 @@ __global__ void adam_kernel(float *__restrict__ xyz, float *__restrict__ rgb, fl
     }
 }
 
+__global__ void step_advance_kernel(int32_t *step) { *step += 1; }
+
 }  // namespace
 
 cudaError_t launch_l1(const float *img, const float *tgt, int64_t n, float *dL, float *loss, cudaStream_t st) {
@@ -80,12 +88,17 @@ cudaError_t launch_l1(const float *img, const float *tgt, int64_t n, float *dL, 
 }
 
 cudaError_t launch_adam(float *xyz, float *rgb, float *alpha, const float *dx, const float *dc, const float *da,
-                        float *m, float *v, int64_t V, int step, float lr_c, float lr_x, float b1, float b2, float eps,
-                        cudaStream_t st) {
+                        float *m, float *v, int64_t V, int step, int32_t *d_step, float lr_c, float lr_x, float b1,
+                        float b2, float eps, cudaStream_t st) {
+    if (d_step) {
+        step_advance_kernel<<<1, 1, 0, st>>>(d_step);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
     if (V == 0) return cudaSuccess;
     const float bc1 = 1.0f - powf(b1, (float)step), bc2 = 1.0f - powf(b2, (float)step);
     const int grid = (int)min64((V + 255) / 256, 16 * 152);
-    adam_kernel<<<grid, 256, 0, st>>>(xyz, rgb, alpha, dx, dc, da, m, v, V, lr_c, lr_x, b1, b2, eps, bc1, bc2);
+    adam_kernel<<<grid, 256, 0, st>>>(xyz, rgb, alpha, dx, dc, da, m, v, V, lr_c, lr_x, b1, b2, eps, bc1, bc2, d_step);
     return cudaGetLastError();
 }
 

@@ -45,7 +45,7 @@ enum RasterMode { kCount = 0, kFill = 1, kFillBwd = 2 };
 
 template <int TILE, int STG, int MODE>
 __host__ __device__ __forceinline__ size_t warp_smem_bytes(int K) {
-    return (size_t)TILE * TILE * 4 * (MODE != kCount ? 2 : 1) + stage_bytes(STG, K, MODE);
+    return (size_t)(TILE * TILE * (MODE != kCount ? 2 : 1) + 32) * 4 + stage_bytes(STG, K, MODE);
 }
 
 template <int TILE, int STG, int KT, int MODE>
@@ -73,7 +73,8 @@ __global__ void __launch_bounds__(kRastWarps * 32) raster_kernel(const __grid_co
     char *mine = smem + (size_t)warp * warp_smem_bytes<TILE, STG, MODE>(K);
     uint32_t *s_cnt = reinterpret_cast<uint32_t *>(mine);   // [TILE*TILE] fragments so far
     uint32_t *s_base = s_cnt + TILE * TILE;                   // [TILE*TILE] record offsets (fill)
-    const Stage S = stage_ptrs(mine + (size_t)TILE * TILE * 4 * (FILL ? 2 : 1), STG, K, MODE);
+    uint32_t *s_nf = s_cnt + TILE * TILE * (FILL ? 2 : 1);    // [32] fragments per lane of a batch
+    const Stage S = stage_ptrs(mine + (size_t)(TILE * TILE * (FILL ? 2 : 1) + 32) * 4, STG, K, MODE);
     const int tx0 = (tile % tiles_x) * TILE, ty0 = (tile / tiles_x) * TILE;
     const int tx1 = min(tx0 + TILE, sc.W) - 1, ty1 = min(ty0 + TILE, sc.H) - 1;
     uint32_t *icnt = a.icnt + (size_t)item * TILE * TILE;
@@ -101,69 +102,112 @@ __global__ void __launch_bounds__(kRastWarps * 32) raster_kernel(const __grid_co
             stage_fan(sc, S, STG, K, lane, __ldg(a.vals + li), q, MODE);
         }
         __syncwarp();
-        for (int f = 0; f < cnt; ++f) {
-            const uint32_t flags = S.flags[f];
-            const int4 r = S.rect[f];
+        // The staged fans' rectangles (clipped to the tile) form one packed (fan, pixel)
+        // index space, fan-major, so every lane tests a pixel even when fans are tiny.
+        int my_n = 0;
+        if (lane < cnt) {
+            const int4 r = S.rect[lane];
             const int rx0 = max(r.x, tx0), rx1 = min(r.y, tx1), ry0 = max(r.z, ty0), ry1 = min(r.w, ty1);
-            if (flags == 0 || rx0 > rx1 || ry0 > ry1) continue;   // warp-uniform
-            const int w = rx1 - rx0 + 1, npx = w * (ry1 - ry0 + 1);
-            const float inv_w = 1.0f / (float)w;
-            for (int base = 0; base < npx; base += 32) {
-                const int idx = base + lane;
-                if (idx < npx) {
-                    ++c_rect;
-                    // (idx + 0.5) / w is at least 1/(2w) away from an integer: exact row
-                    const int yy = (int)(((float)idx + 0.5f) * inv_w);
-                    const int px = rx0 + (idx - yy * w), py = ry0 + yy;
-                    const int lp = (py - ty0) * TILE + (px - tx0);
-                    const float pxc = (float)px + 0.5f, pyc = (float)py + 0.5f;
-                    cover_fan<KT>(S, STG, K, f, flags, pxc, pyc,
-                                  [&](int j, int jn, bool neg, float E0, float E1, float E2) {
-                        const uint32_t slot = s_cnt[lp]++;
-                        ++c_frag;
-                        if (MODE != kCount) {
-                            const uint32_t b = s_base[lp];
-                            if (b == 0xffffffffu) return;
-                            const float izc = S.viz[f];
-                            const float izj = S.viz[(1 + j) * STG + f], izn = S.viz[(1 + jn) * STG + f];
-                            const float zf = dec_depth(S.area[j * STG + f], E0, izc, E1, neg ? izn : izj, E2,
-                                                       neg ? izj : izn, S.vz[f], S.vz[(1 + j) * STG + f],
-                                                       S.vz[(1 + jn) * STG + f]);
-                            // perspective-correct barycentrics from the accurate centre offsets
-                            const float ox = __fsub_rn(S.cxh[f], pxc) + S.cxl[f];
-                            const float oy = __fsub_rn(S.cyh[f], pyc) + S.cyl[f];
-                            const float ujx = ox + S.du[j * STG + f], ujy = oy + S.dv[j * STG + f];
-                            const float unx = ox + S.du[jn * STG + f], uny = oy + S.dv[jn * STG + f];
-                            const float w0 = (ujx * uny - ujy * unx) * izc;
-                            const float w1 = (unx * oy - uny * ox) * izj;
-                            const float w2 = (ox * ujy - oy * ujx) * izn;
-                            const float Wsum = w0 + w1 + w2;
-                            const float iW = 1.0f / Wsum;
-                            const float m0 = w0 * iW, m1 = w1 * iW, m2 = w2 * iW;
-                            const int vc = f, vj = (1 + j) * STG + f, vn = (1 + jn) * STG + f;
-                            const float al = m0 * S.ca[vc] + m1 * S.ca[vj] + m2 * S.ca[vn];
-                            const float c0 = m0 * S.cr[vc] + m1 * S.cr[vj] + m2 * S.cr[vn];
-                            const float c1 = m0 * S.cg[vc] + m1 * S.cg[vj] + m2 * S.cg[vn];
-                            const float c2 = m0 * S.cb[vc] + m1 * S.cb[vj] + m2 * S.cb[vn];
-                            const uint32_t tri = S.fan[f] * (uint32_t)K + (uint32_t)j;
-                            float4 *rec = a.frags + (size_t)(MODE == kFill ? kRecFwd : kRecBwd) * ((size_t)b + slot);
-                            rec[0] = make_float4(zf, __uint_as_float(tri), __uint_as_float(S.q[f]), al);
-                            rec[1] = make_float4(c0, c1, c2, 0.0f);
-                            if (MODE == kFillBwd) {
-                                const float iz0 = 1.0f / S.vZ[vc], iz1 = 1.0f / S.vZ[vj], iz2 = 1.0f / S.vZ[vn];
-                                rec[2] = make_float4(m0, m1, m2, Wsum);
-                                rec[3] = make_float4(ox, oy, ujx, ujy);
-                                rec[4] = make_float4(unx, uny, iz0, iz1);
-                                rec[5] = make_float4(iz2, S.vX[vc], S.vY[vc], S.vX[vj]);
-                                rec[6] = make_float4(S.vY[vj], S.vX[vn], S.vY[vn], S.ca[vc]);
-                                rec[7] = make_float4(S.ca[vj], S.ca[vn], S.cr[vc], S.cg[vc]);
-                                rec[8] = make_float4(S.cb[vc], S.cr[vj], S.cg[vj], S.cb[vj]);
-                                rec[9] = make_float4(S.cr[vn], S.cg[vn], S.cb[vn], 0.0f);
-                            }
-                        }                    });
-                }
-                __syncwarp();   // a later fan may append to the same pixel from another lane
+            if (S.flags[lane] != 0 && rx0 <= rx1 && ry0 <= ry1) my_n = (rx1 - rx0 + 1) * (ry1 - ry0 + 1);
+        }
+        int incl = my_n;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const int excl = incl - my_n;
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        for (int base = 0; base < total; base += 32) {
+            const int idx = base + lane;
+            int f = 0;   // first lane (fan) whose inclusive count exceeds idx
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1) {
+                const int v = __shfl_sync(0xffffffffu, incl, f + step - 1);
+                if (v <= idx) f += step;
             }
+            const int fexcl = __shfl_sync(0xffffffffu, excl, f);
+            uint32_t hits = 0, flags = 0;
+            int lp = -1, px = 0, py = 0;
+            if (idx < total) {
+                ++c_rect;
+                flags = S.flags[f];
+                const int4 r = S.rect[f];
+                const int rx0 = max(r.x, tx0), rx1 = min(r.y, tx1), ry0 = max(r.z, ty0);
+                const int w = rx1 - rx0 + 1, local = idx - fexcl;
+                // (local + 0.5) / w is at least 1/(2w) away from an integer: exact row
+                const int yy = (int)(((float)local + 0.5f) * (1.0f / (float)w));
+                px = rx0 + (local - yy * w);
+                py = ry0 + yy;
+                hits = cover_mask<KT>(S, STG, K, f, flags, (float)px + 0.5f, (float)py + 0.5f);
+                if (hits) lp = (py - ty0) * TILE + (px - tx0);
+            }
+            const int nf = __popc(hits);
+            c_frag += nf;
+            // Lanes that hit the same pixel take consecutive slots in lane order, which is
+            // fan order, so a pixel's records keep the depth-key order of the tile list.
+            const unsigned grp = __match_any_sync(0xffffffffu, lp);
+            if (nf) s_nf[lane] = (uint32_t)nf;
+            __syncwarp();
+            uint32_t slot = 0;
+            if (nf) {
+                uint32_t pre = 0;
+                for (unsigned lower = grp & ((1u << lane) - 1u); lower; lower &= lower - 1)
+                    pre += s_nf[__ffs(lower) - 1];
+                slot = s_cnt[lp] + pre;
+            }
+            __syncwarp();
+            if (nf && (grp >> lane) == 1u) s_cnt[lp] = slot + (uint32_t)nf;   // last lane of its group
+            if (MODE != kCount && nf) {
+                const uint32_t b = s_base[lp];
+                if (b != 0xffffffffu) {
+                    const float pxc = (float)px + 0.5f, pyc = (float)py + 0.5f;
+                    for (uint32_t hm = hits; hm; hm &= hm - 1, ++slot) {
+                        const int j = __ffs(hm) - 1;
+                        const int jn = (j + 1 == K) ? 0 : j + 1;
+                        const bool neg = ((flags >> 16) >> j) & 1u;
+                        float E0, E1, E2;
+                        tri_edges(S, STG, K, f, flags, j, pxc, pyc, E0, E1, E2);
+                        const float izc = S.viz[f];
+                        const float izj = S.viz[(1 + j) * STG + f], izn = S.viz[(1 + jn) * STG + f];
+                        const float zf = dec_depth(S.area[j * STG + f], E0, izc, E1, neg ? izn : izj, E2,
+                                                   neg ? izj : izn, S.vz[f], S.vz[(1 + j) * STG + f],
+                                                   S.vz[(1 + jn) * STG + f]);
+                        // perspective-correct barycentrics from the accurate centre offsets
+                        const float ox = __fsub_rn(S.cxh[f], pxc) + S.cxl[f];
+                        const float oy = __fsub_rn(S.cyh[f], pyc) + S.cyl[f];
+                        const float ujx = ox + S.du[j * STG + f], ujy = oy + S.dv[j * STG + f];
+                        const float unx = ox + S.du[jn * STG + f], uny = oy + S.dv[jn * STG + f];
+                        const float w0 = (ujx * uny - ujy * unx) * izc;
+                        const float w1 = (unx * oy - uny * ox) * izj;
+                        const float w2 = (ox * ujy - oy * ujx) * izn;
+                        const float Wsum = w0 + w1 + w2;
+                        const float iW = 1.0f / Wsum;
+                        const float m0 = w0 * iW, m1 = w1 * iW, m2 = w2 * iW;
+                        const int vc = f, vj = (1 + j) * STG + f, vn = (1 + jn) * STG + f;
+                        const float al = m0 * S.ca[vc] + m1 * S.ca[vj] + m2 * S.ca[vn];
+                        const float c0 = m0 * S.cr[vc] + m1 * S.cr[vj] + m2 * S.cr[vn];
+                        const float c1 = m0 * S.cg[vc] + m1 * S.cg[vj] + m2 * S.cg[vn];
+                        const float c2 = m0 * S.cb[vc] + m1 * S.cb[vj] + m2 * S.cb[vn];
+                        const uint32_t tri = S.fan[f] * (uint32_t)K + (uint32_t)j;
+                        float4 *rec = a.frags + (size_t)(MODE == kFill ? kRecFwd : kRecBwd) * ((size_t)b + slot);
+                        rec[0] = make_float4(zf, __uint_as_float(tri), __uint_as_float(S.q[f]), al);
+                        rec[1] = make_float4(c0, c1, c2, 0.0f);
+                        if (MODE == kFillBwd) {
+                            const float iz0 = 1.0f / S.vZ[vc], iz1 = 1.0f / S.vZ[vj], iz2 = 1.0f / S.vZ[vn];
+                            rec[2] = make_float4(m0, m1, m2, Wsum);
+                            rec[3] = make_float4(ox, oy, ujx, ujy);
+                            rec[4] = make_float4(unx, uny, iz0, iz1);
+                            rec[5] = make_float4(iz2, S.vX[vc], S.vY[vc], S.vX[vj]);
+                            rec[6] = make_float4(S.vY[vj], S.vX[vn], S.vY[vn], S.ca[vc]);
+                            rec[7] = make_float4(S.ca[vj], S.ca[vn], S.cr[vc], S.cg[vc]);
+                            rec[8] = make_float4(S.cb[vc], S.cr[vj], S.cg[vj], S.cb[vj]);
+                            rec[9] = make_float4(S.cr[vn], S.cg[vn], S.cb[vn], 0.0f);
+                        }
+                    }
+                }
+            }
+            __syncwarp();   // the next batch may append to the same pixels
         }
         __syncwarp();
     }

@@ -245,16 +245,14 @@ __device__ __forceinline__ void stage_fan(const SceneDev &a, const Stage &s, int
     }
 }
 
-// Coverage of pixel centre (pxc, pyc) by the K triangles of staged fan f.  For every
-// covered triangle j calls on_frag(j, jn, neg, E0, E1, E2) with the oriented edge values
-// (opposite P0 = centre, P1, P2 of the decision formulas).  Each spoke value is computed
-// once and turned into two pass bits (as the edge c -> b_i and as its reverse; the
-// top-left tie bit of each direction was staged), so a triangle's two spoke tests are a
-// bit test; only triangles passing both get the rim edge.  The result is the
-// conjunction of the three edge tests, as stated.
-template <int KT, class F>
-__device__ __forceinline__ void cover_fan(const Stage &S, int CH, int K, int f, uint32_t flags, float pxc, float pyc,
-                                          F &&on_frag) {
+// Coverage of the pixel centre (pxc, pyc) by staged fan f: bit j is set when triangle j
+// covers it.  Each spoke value is computed once and turned into two pass bits (as the
+// edge c -> b_i and as its reverse; the top-left tie bit of each direction was staged),
+// so a triangle's two spoke tests are a bit test; only triangles passing both get the
+// rim edge.  The result is the conjunction of the three edge tests, as stated.
+template <int KT>
+__device__ __forceinline__ uint32_t cover_mask(const Stage &S, int CH, int K, int f, uint32_t flags, float pxc,
+                                               float pyc) {
     const float xc = S.vx[f], yc = S.vy[f];
     const float qx = __fsub_rn(pxc, xc), qy = __fsub_rn(pyc, yc);
     const uint32_t stie = S.stie[f];
@@ -271,12 +269,11 @@ __device__ __forceinline__ void cover_fan(const Stage &S, int CH, int K, int f, 
     const uint32_t Nn = ((N >> 1) | (N << (K - 1))) & full;
     const uint32_t negm = flags >> 16;
     uint32_t cand = ((P & Nn & ~negm) | (N & Pn & negm)) & flags & full;
-    if (!cand) return;
+    uint32_t hits = 0;
     const uint32_t rtie = S.rtie[f];
     while (cand) {
         const int j = __ffs(cand) - 1;
         cand &= cand - 1;
-        const int jn = (j + 1 == K) ? 0 : j + 1;
         const bool neg = (negm >> j) & 1u;
         const bool wrap = (j + 1 == K);
         const int lo = wrap ? 0 : j;
@@ -285,13 +282,27 @@ __device__ __forceinline__ void cover_fan(const Stage &S, int CH, int K, int f, 
         // oriented rim: b_j -> b_{j+1} for positive orientation, reversed otherwise
         const bool flip = wrap != neg;
         const float E0 = flip ? -Rc : Rc;
-        if (E0 > 0.0f || (E0 == 0.0f && ((rtie >> (flip ? 16 + j : j)) & 1u))) {
-            const float Sj = __fsub_rn(__fmul_rn(S.sdx[j * CH + f], qy), __fmul_rn(S.sdy[j * CH + f], qx));
-            const float Sn = __fsub_rn(__fmul_rn(S.sdx[jn * CH + f], qy), __fmul_rn(S.sdy[jn * CH + f], qx));
-            const float E1 = neg ? -Sj : -Sn, E2 = neg ? Sn : Sj;
-            on_frag(j, jn, neg, E0, E1, E2);
-        }
+        if (E0 > 0.0f || (E0 == 0.0f && ((rtie >> (flip ? 16 + j : j)) & 1u))) hits |= 1u << j;
     }
+    return hits;
+}
+
+// Oriented edge values of triangle j of staged fan f at a pixel centre it covers (E0
+// opposite P0 = centre, E1 opposite P1, E2 opposite P2 of the decision formulas).
+__device__ __forceinline__ void tri_edges(const Stage &S, int CH, int K, int f, uint32_t flags, int j, float pxc,
+                                          float pyc, float &E0, float &E1, float &E2) {
+    const int jn = (j + 1 == K) ? 0 : j + 1;
+    const bool neg = ((flags >> 16) >> j) & 1u;
+    const bool wrap = (j + 1 == K);
+    const int lo = wrap ? 0 : j;
+    const float Rc = dec_edge(S.rdx[j * CH + f], S.rdy[j * CH + f], S.vx[(1 + lo) * CH + f], S.vy[(1 + lo) * CH + f],
+                              pxc, pyc);
+    E0 = (wrap != neg) ? -Rc : Rc;
+    const float qx = __fsub_rn(pxc, S.vx[f]), qy = __fsub_rn(pyc, S.vy[f]);
+    const float Sj = __fsub_rn(__fmul_rn(S.sdx[j * CH + f], qy), __fmul_rn(S.sdy[j * CH + f], qx));
+    const float Sn = __fsub_rn(__fmul_rn(S.sdx[jn * CH + f], qy), __fmul_rn(S.sdy[jn * CH + f], qx));
+    E1 = neg ? -Sj : -Sn;
+    E2 = neg ? Sn : Sj;
 }
 
 }  // namespace ms

@@ -192,3 +192,31 @@ def test_batch_autotune_picks_a_candidate_and_renders_identically(soup):
     assert br.params.pair_capacity >= res.pairs and br.params.frag_capacity >= res.frags
     out = br.forward(X, Cc, A)
     assert torch.equal(out, ref)
+
+
+def test_counted_adam_replays_with_advancing_step():
+    """Adam with the step number on the device, captured once in a CUDA graph and replayed
+    three times, equals three host-numbered Adam steps."""
+    g = torch.Generator(device="cuda").manual_seed(5)
+    V = 10007
+    p1 = [torch.randn(V, 3, device="cuda", generator=g), torch.rand(V, 3, device="cuda", generator=g),
+          torch.rand(V, device="cuda", generator=g)]
+    p2 = [t.clone() for t in p1]
+    grads = [torch.randn(V, 3, device="cuda", generator=g), torch.randn(V, 3, device="cuda", generator=g),
+             torch.randn(V, device="cuda", generator=g)]
+    a1 = ms.FanAdam(*p1, lr_color=1e-2)
+    a2 = ms.FanAdam(*p2, lr_color=1e-2, device_step=True)
+    for _ in range(3):
+        a1.step(*p1, *grads)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    torch.cuda.current_stream().wait_stream(s)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        a2.step(*p2, *grads)
+    for _ in range(3):
+        graph.replay()
+    torch.cuda.synchronize()
+    assert int(a2.d_step.item()) == 3
+    for x, y in zip(p1, p2):
+        assert torch.allclose(x, y, rtol=1e-6, atol=1e-7), (x - y).abs().max().item()
