@@ -42,6 +42,8 @@ def lib():
         L.orc_quat_to_rot.argtypes = [P, P]
         L.orc_fan_tris.argtypes = [C.c_int64, C.c_int32, P]
         L.orc_project.argtypes = [P, P, P, P]
+        L.orc_splat_render.argtypes = [C.c_int64, P, P, P, P, P, C.c_int, C.c_double, P, P, C.c_int, C.c_int,
+                                       C.c_int, C.c_int, C.c_int, P, P]
         _lib = L
     return _lib
 
@@ -160,6 +162,32 @@ def render_backward(xyz, rgb, alpha, tris, cam, dL, bg=(0.0, 0.0, 0.0), window=N
     if rc:
         raise RuntimeError(f"orc_render_backward failed ({rc})")
     return gx, gc, ga
+
+
+def gaussian_colors(scene, cam_center=None):
+    """Colour of every Gaussian (N x 3, FP64): the colour its fan's vertices carry."""
+    _, rgb, _ = mesh_build(scene, K=3, cam_center=cam_center)
+    return np.ascontiguousarray(rgb.reshape(scene.n, 4, 3)[:, 0, :])
+
+
+def splat_render(scene, cam, rgb=None, axis_rule=1, trunc=SCALE_MUL, bg=(0.0, 0.0, 0.0), window=None,
+                 nthreads=0, cam_center=None):
+    """Source-Gaussian render of the window (see ms_oracle_splat.c).  Returns
+    (rgba (h, w, 4) float64, fragments per pixel (h, w) int32)."""
+    if rgb is None:
+        rgb = gaussian_colors(scene, cam_center)
+    x0, y0, x1, y1 = _window(cam, window)
+    out = np.zeros((max(y1 - y0, 0), max(x1 - x0, 0), 4))
+    nfrag = np.zeros(out.shape[:2], np.int32)
+    bgv = np.asarray(bg, np.float64)
+    camc = camera_struct(cam)
+    rc = lib().orc_splat_render(scene.n, _p(_c(scene.means, np.float32)), _p(_c(scene.log_scales, np.float32)),
+                                _p(_c(scene.quats, np.float32)), _p(_c(scene.opacity, np.float32)),
+                                _p(_c(rgb, np.float64)), int(axis_rule), float(trunc), C.byref(camc), _p(bgv),
+                                x0, y0, x1, y1, int(nthreads), _p(out), _p(nfrag))
+    if rc != 0:
+        raise RuntimeError(f"orc_splat_render failed ({rc})")
+    return out, nfrag
 
 
 def l1_loss_grad(rgb_img, target_rgb):

@@ -8,7 +8,7 @@ import subprocess
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB = os.path.join(HERE, "liboracle.so")
-SRC = [os.path.join(HERE, "ms_oracle.c")]
+SRC = [os.path.join(HERE, "ms_oracle.c"), os.path.join(HERE, "ms_oracle_splat.c")]
 
 
 def build(force: bool = False) -> str:

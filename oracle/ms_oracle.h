@@ -85,6 +85,17 @@ int orc_render_backward(int64_t V, const double *xyz, const double *rgb, const d
                         int x0, int y0, int x1, int y1, int nthreads,
                         const double *dL_drgba, double *d_xyz, double *d_rgb, double *d_alpha);
 
+/*
+ * Source-Gaussian render (ms_oracle_splat.c): the scene's flat Gaussians drawn as
+ * truncated Gaussian splats on their planes and composited in depth order -- the image
+ * the fans approximate.  rgb: N x 3 colour per Gaussian.  trunc: truncation radius in
+ * units of the scale (2.7, the fan's scale_mul).  Window and outputs as orc_render.
+ */
+int orc_splat_render(int64_t N, const float *means, const float *log_scales, const float *quats,
+                     const float *opacity, const double *rgb, int axis_rule, double trunc,
+                     const orc_camera *cam, const double bg[3], int x0, int y0, int x1, int y1,
+                     int nthreads, double *out_rgba, int32_t *out_nfrag);
+
 #ifdef __cplusplus
 }
 #endif
