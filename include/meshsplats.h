@@ -221,6 +221,28 @@ MS_API ms_status ms_batch_render_backward(const float *xyz, const float *rgb, co
                                           const float *const *dL_drgba, float *d_xyz, float *d_rgb, float *d_alpha,
                                           void *workspace, size_t ws_bytes, void *stream);
 
+/*
+ * Source-Gaussian render: the flat Gaussians themselves, drawn as truncated splats on
+ * their planes and composited in depth order -- the image the fans approximate (the
+ * Gaussian component of Sec. 3 with mean m, rotation R, scales S and opacity sigma in the
+ * flat GaMeS form).  For pixel ray x = C + t d (d with unit camera z) meeting the plane of
+ * the two kept unit axes u_a, u_b (axis_rule as in ms_fan_params) at local (u, v):
+ * alpha = sigma exp(-(u^2/s_a^2 + v^2/s_b^2)/2), kept where (u/(2.7 s_a))^2 + (v/(2.7 s_b))^2
+ * <= 1 (the ellipse the fan is inscribed in) and t > znear; colour rgb[g]; fragments of a
+ * pixel ordered by (binary32 t, Gaussian index); compositing as in ms_render.  The hit
+ * test runs in FP64.
+ *   means N x 3, log_scales N x 3, quats N x 4 (w, x, y, z; 16-byte aligned), opacity N,
+ *   rgb N x 3: device.  cams: host array of n_views cameras.  out_rgba: host array of
+ *   n_views device images H_v x W_v x 4.  workspace >= ms_splat_workspace_size bytes.
+ * Device-side outcome through ms_render_get_info.
+ */
+MS_API size_t ms_splat_workspace_size(int64_t N, const ms_camera *cams, int32_t n_views,
+                                      const ms_render_params *params);
+MS_API ms_status ms_splat_render(const float *means, const float *log_scales, const float *quats,
+                                 const float *opacity, const float *rgb, int64_t N, int32_t axis_rule,
+                                 const ms_camera *cams, int32_t n_views, const ms_render_params *params,
+                                 float *const *out_rgba, void *workspace, size_t ws_bytes, void *stream);
+
 /* Candidates the autotuner times: tile in {8, 16, 32} x kbuf in {8, 16}. */
 #define MS_TUNE_CANDIDATES 6
 

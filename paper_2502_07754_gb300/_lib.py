@@ -75,6 +75,9 @@ _SIGS = {
                                     C.c_size_t, C.c_int32, C.c_float, _P, _P, _P]),
     "ms_adam_step_counted": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, C.c_int64, _P, C.c_float, C.c_float,
                                        C.c_float, C.c_float, C.c_float, _P]),
+    "ms_splat_workspace_size": (C.c_size_t, [C.c_int64, _P, C.c_int32, _P]),
+    "ms_splat_render": (C.c_int, [_P, _P, _P, _P, _P, C.c_int64, C.c_int32, _P, C.c_int32, _P, _P, _P, C.c_size_t,
+                                  _P]),
     "ms_render_noalloc": (C.c_int, [_P, _P, _P, C.c_int64, C.c_int32, _P, _P, _P, _P, _P]),
     "ms_profile_enable": (None, [C.c_int32]),
     "ms_profile_read": (C.c_int, [_P, _P, C.c_int32]),

@@ -257,6 +257,51 @@ class BatchRenderer:
         return d_xyz, d_rgb, d_alpha
 
 
+class SplatRenderer(BatchRenderer):
+    """Renders the source Gaussians themselves (ms_splat_render) into several views:
+    the reference image that the fans approximate.  Same flat-buffer layout as
+    BatchRenderer."""
+
+    def __init__(self, n_gaussians: int, cams, params=None, device="cuda", axis_rule=1):
+        self.axis_rule = int(axis_rule)
+        super().__init__(n_gaussians, 8, cams, params, device)
+
+    def _alloc(self):
+        n = lib().ms_splat_workspace_size(self.n_fans, self.cams, self.n_views, C.byref(self.params))
+        if n == 0:
+            raise ValueError("invalid render configuration")
+        self.ws = None
+        self.ws = torch.empty(int(n), dtype=torch.uint8, device=self.device)
+
+    def render(self, means, log_scales, quats, opacity, rgb, flat=None, stream=None):
+        """rgb: N x 3 colour per Gaussian (float32, device)."""
+        if flat is None:
+            flat = self.new_flat()
+        outs = self._ptrs(flat)
+        for _ in range(4):
+            check(lib().ms_splat_render(_ptr(means), _ptr(log_scales), _ptr(quats), _ptr(opacity), _ptr(rgb),
+                                        self.n_fans, self.axis_rule, self.cams, self.n_views, C.byref(self.params),
+                                        outs, _ptr(self.ws), self.ws.numel(), _stream(stream)))
+            st, inf = self.info(stream)
+            if st == _lib.MS_ERR_CAPACITY:
+                if inf.pairs > inf.pair_capacity:
+                    self.params.pair_capacity = int(inf.pairs * 1.25) + 4096
+                if inf.frags > inf.frag_capacity:
+                    self.params.frag_capacity = int(inf.frags * 1.25) + 65536
+                self._alloc()
+                continue
+            check(st)
+            self.last_info = inf
+            return flat
+        raise _lib.MSError(_lib.MS_ERR_CAPACITY, "capacity did not converge")
+
+    def forward(self, *a, **k):
+        raise TypeError("SplatRenderer draws Gaussians: use render()")
+
+    def backward(self, *a, **k):
+        raise TypeError("the splat render has no adjoint")
+
+
 class RenderFn(torch.autograd.Function):
     """Differentiable render of a fan soup; gradients for vertex positions, colours and
     opacities come from ms_render_backward (visibility held fixed)."""

@@ -222,6 +222,7 @@ static ms_status render_views(const float *xyz, const float *rgb, const float *a
     RenderArgs a;
     memset(&a, 0, sizeof(a));
     a.xyz = xyz; a.rgb = rgb; a.alpha = alpha; a.n_fans = n_fans; a.K = K; a.prm = p; a.L = L; a.ws = ws;
+    a.key_scale = 1.0f;
     a.vt = make_views(cams, n_views, L, out, nullptr, nullptr);
     {
         StageScope sc(MS_STAGE_BIN, st);
@@ -264,6 +265,7 @@ static ms_status render_views_backward(const float *xyz, const float *rgb, const
     memset(&a, 0, sizeof(a));
     a.xyz = xyz; a.rgb = rgb; a.alpha = alpha; a.n_fans = n_fans; a.K = K; a.prm = p; a.L = L; a.ws = ws;
     a.d_xyz = d_xyz; a.d_rgb = d_rgb; a.d_alpha = d_alpha;
+    a.key_scale = 1.0f;
     a.vt = make_views(cams, n_views, L, nullptr, out_fwd, dL);
     // the fragment records are regenerated from the sorted tile lists (not kept from the
     // forward); transmittance is recomputed during the resolve
@@ -271,6 +273,55 @@ static ms_status render_views_backward(const float *xyz, const float *rgb, const
     if ((e = launch_resolve(a, true, st)) != cudaSuccess) return cuda_fail(e, "resolve backward launch");
     if ((e = launch_grad_scatter(a, st)) != cudaSuccess) return cuda_fail(e, "gradient scatter launch");
     count_launches(1 + (L.V > 0 ? 1 : 0));   // resolve, scatter (the fill counts itself)
+    return MS_OK;
+}
+
+// Source-Gaussian splat render: the polygons circumscribing the splats go through the
+// same binning, sort and work-item machinery as fans; the splat passes then evaluate
+// the Gaussians themselves.  The polygon soup lives after the render layout.
+constexpr double kSplatTrunc = 2.7;           // truncation radius in scales (the fan's scale_mul)
+constexpr float kSplatKeyScale = 0.9990234375f;   // 1 - 2^-10: depth keys stay below every hit
+
+static size_t splat_poly_bytes(int64_t N) { return align_up((size_t)N * (kSplatK + 1) * 12, 256); }
+
+static ms_status splat_views(const float *means, const float *log_scales, const float *quats, const float *opacity,
+                             const float *rgb, int64_t N, int axis_rule, const ms_camera *cams, int n_views,
+                             const ms_render_params *params, float *const *out, void *workspace, size_t ws_bytes,
+                             cudaStream_t st) {
+    ms_render_params p;
+    params_or_default(params, p);
+    if (axis_rule != 0 && axis_rule != 1) return fail(MS_ERR_INVALID, "axis_rule %d", axis_rule);
+    if (N > 0 && (!means || !log_scales || !quats || !opacity || !rgb)) return fail(MS_ERR_INVALID, "NULL pointer");
+    if (N > 0 && (reinterpret_cast<uintptr_t>(quats) & 15)) return fail(MS_ERR_INVALID, "quats must be 16-byte aligned");
+    if (N >= (1ll << 31)) return fail(MS_ERR_INVALID, "too many Gaussians");
+    RenderLayout L;
+    // the layout check sees a placeholder soup pointer: the polygons are made below
+    ms_status s = check_render_args(N > 0 ? means : nullptr, means, means, N, kSplatK, cams, n_views, p, workspace,
+                                    ws_bytes > splat_poly_bytes(N) ? ws_bytes - splat_poly_bytes(N) : 0, L);
+    if (s != MS_OK) return s;
+    if (!out) return fail(MS_ERR_INVALID, "output image list is NULL");
+    for (int v = 0; v < n_views; ++v)
+        if (!out[v] || !aligned16(out[v])) return fail(MS_ERR_INVALID, "view %d: output image NULL or not 16-byte aligned", v);
+    char *ws = static_cast<char *>(workspace);
+    float *poly = reinterpret_cast<float *>(ws + L.total);
+    cudaError_t e = cudaMemsetAsync(ws, 0, L.off_keys0, st);
+    if (e != cudaSuccess) return cuda_fail(e, "workspace clear");
+    RenderArgs a;
+    memset(&a, 0, sizeof(a));
+    a.xyz = poly; a.n_fans = N; a.K = kSplatK; a.prm = p; a.L = L; a.ws = ws;
+    a.splat = true;
+    a.key_scale = kSplatKeyScale;
+    a.spl.means = means; a.spl.log_scales = log_scales; a.spl.quats = quats; a.spl.opacity = opacity;
+    a.spl.rgb = rgb; a.spl.axis_rule = axis_rule; a.spl.trunc = kSplatTrunc;
+    a.vt = make_views(cams, n_views, L, out, nullptr, nullptr);
+    if ((e = launch_splat_polygons(a.spl, N, poly, st)) != cudaSuccess) return cuda_fail(e, "polygon launch");
+    if ((e = launch_bin(a, st)) != cudaSuccess) return cuda_fail(e, "bin launch");
+    if ((e = launch_sort(a, st)) != cudaSuccess) return cuda_fail(e, "sort launch");
+    if ((e = launch_raster_count(a, st)) != cudaSuccess) return cuda_fail(e, "splat count launch");
+    if ((e = launch_raster(a, true, st)) != cudaSuccess) return cuda_fail(e, "splat fill launch");
+    if ((e = launch_resolve(a, false, st)) != cudaSuccess) return cuda_fail(e, "resolve launch");
+    if (N > 0) count_launches(2 + 3 + L.passes);
+    count_launches(1);
     return MS_OK;
 }
 
@@ -390,6 +441,20 @@ MS_API ms_status ms_batch_render_backward(const float *xyz, const float *rgb, co
                                           void *workspace, size_t ws_bytes, void *stream) {
     return render_views_backward(xyz, rgb, alpha, n_fans, K, cams, n_views, params, out_rgba, dL_drgba, d_xyz, d_rgb,
                                  d_alpha, workspace, ws_bytes, (cudaStream_t)stream);
+}
+
+MS_API size_t ms_splat_workspace_size(int64_t N, const ms_camera *cams, int32_t n_views,
+                                      const ms_render_params *params) {
+    const size_t base = ms_batch_workspace_size(N, kSplatK, cams, n_views, params);
+    return base ? base + splat_poly_bytes(N) : 0;
+}
+
+MS_API ms_status ms_splat_render(const float *means, const float *log_scales, const float *quats,
+                                 const float *opacity, const float *rgb, int64_t N, int32_t axis_rule,
+                                 const ms_camera *cams, int32_t n_views, const ms_render_params *params,
+                                 float *const *out_rgba, void *workspace, size_t ws_bytes, void *stream) {
+    return splat_views(means, log_scales, quats, opacity, rgb, N, axis_rule, cams, n_views, params, out_rgba,
+                       workspace, ws_bytes, (cudaStream_t)stream);
 }
 
 MS_API ms_status ms_render_get_info(const void *workspace, ms_render_info *info, void *stream) {

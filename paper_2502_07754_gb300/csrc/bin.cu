@@ -20,6 +20,7 @@ struct BinArgs {
     const float *xyz;
     int64_t n_fans;
     int K, tile_shift, depth_bits;
+    float key_scale;
     int64_t cap, nblocks, fan_blocks;
     unsigned n_tiles, sort_bits;
     Status *st;
@@ -111,7 +112,7 @@ __global__ void __launch_bounds__(kBinThreads) bin_kernel(const __grid_constant_
                 count = (uint32_t)(w * h);
                 s_rect[tid][0] = (uint32_t)tx0 | ((uint32_t)ty0 << 16);
                 s_rect[tid][1] = (uint32_t)w | ((uint32_t)h << 16);
-                s_q[tid] = depth_q(zmin, depth_bits);
+                s_q[tid] = depth_q(zmin * a.key_scale, depth_bits);
             }
         }
     }
@@ -210,6 +211,7 @@ cudaError_t launch_bin(const RenderArgs &ra, cudaStream_t st) {
     a.tile_shift = 0;
     while ((1 << a.tile_shift) < L.tile) ++a.tile_shift;
     a.depth_bits = L.depth_bits;
+    a.key_scale = ra.key_scale;
     a.cap = L.cap;
     a.nblocks = L.bin_blocks;
     a.fan_blocks = L.bin_fan_blocks;

@@ -40,6 +40,13 @@ struct RenderLayout {
 
 RenderLayout render_layout(int64_t n_fans, int K, const ms_camera *cams, int n_views, const ms_render_params &p);
 
+// Source Gaussians drawn by the splat passes (ms_splat_render); device pointers.
+struct SplatSrc {
+    const float *means, *log_scales, *quats, *opacity, *rgb;
+    int axis_rule;
+    double trunc;
+};
+
 struct RenderArgs {
     const float *xyz, *rgb, *alpha;
     int64_t n_fans;
@@ -49,7 +56,14 @@ struct RenderArgs {
     RenderLayout L;
     char *ws;
     float *d_xyz, *d_rgb, *d_alpha;   // backward outputs
+    bool splat;                // draw the source Gaussians of `spl` over the polygons in xyz
+    float key_scale;           // binning: depth keys from key_scale * min Z (1 for fans)
+    SplatSrc spl;
 };
+
+// Polygons circumscribing the splats' truncation ellipses (K = 8 fans), for binning.
+constexpr int kSplatK = 8;
+cudaError_t launch_splat_polygons(const SplatSrc &s, int64_t N, float *xyz, cudaStream_t st);
 
 cudaError_t launch_bin(const RenderArgs &a, cudaStream_t st);
 cudaError_t launch_sort(const RenderArgs &a, cudaStream_t st);

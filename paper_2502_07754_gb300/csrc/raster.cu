@@ -33,6 +33,7 @@ struct RastArgs {
     float4 *frags;
     int64_t frag_cap;
     Status *st;
+    SplatSrc spl;              // source Gaussians (splat passes only)
 };
 
 constexpr int kRastWarps = 4;   // warps (work items) per block
@@ -41,16 +42,25 @@ constexpr int kRastWarps = 4;   // warps (work items) per block
 // records of the adjoint, which add everything the chain rule to the vertices needs
 // (barycentrics, screen offsets, view coordinates, vertex attributes), so the backward
 // resolve never gathers vertex data from global memory.
-enum RasterMode { kCount = 0, kFill = 1, kFillBwd = 2 };
+// The splat passes draw the source Gaussians themselves (count, then 32-byte records)
+// over the tile lists of their circumscribing polygons.
+enum RasterMode { kCount = 0, kFill = 1, kFillBwd = 2, kSplatCount = 3, kSplatFill = 4 };
+
+__host__ __device__ constexpr bool mode_fills(int m) { return m == kFill || m == kFillBwd || m == kSplatFill; }
+__host__ __device__ constexpr bool mode_splat(int m) { return m >= kSplatCount; }
+__host__ __device__ constexpr int mode_level(int m) { return mode_splat(m) ? (int)kStageDecide : m; }
 
 template <int TILE, int STG, int MODE>
 __host__ __device__ __forceinline__ size_t warp_smem_bytes(int K) {
-    return (size_t)(TILE * TILE * (MODE != kCount ? 2 : 1) + 32) * 4 + stage_bytes(STG, K, MODE);
+    return (size_t)(TILE * TILE * (mode_fills(MODE) ? 2 : 1) + 32) * 4 + stage_bytes(STG, K, mode_level(MODE)) +
+           (mode_splat(MODE) ? (size_t)STG * sizeof(SplatSlot) : 0);
 }
 
 template <int TILE, int STG, int KT, int MODE>
 __global__ void __launch_bounds__(kRastWarps * 32) raster_kernel(const __grid_constant__ RastArgs a) {
-    constexpr bool FILL = MODE != kCount;   // passes that address records
+    constexpr bool FILL = mode_fills(MODE);   // passes that address records
+    constexpr bool SPLAT = mode_splat(MODE);
+    constexpr int LEVEL = mode_level(MODE);
     extern __shared__ __align__(16) char smem[];
     const int K = KT > 0 ? KT : a.K;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -74,7 +84,9 @@ __global__ void __launch_bounds__(kRastWarps * 32) raster_kernel(const __grid_co
     uint32_t *s_cnt = reinterpret_cast<uint32_t *>(mine);   // [TILE*TILE] fragments so far
     uint32_t *s_base = s_cnt + TILE * TILE;                   // [TILE*TILE] record offsets (fill)
     uint32_t *s_nf = s_cnt + TILE * TILE * (FILL ? 2 : 1);    // [32] fragments per lane of a batch
-    const Stage S = stage_ptrs(mine + (size_t)(TILE * TILE * (FILL ? 2 : 1) + 32) * 4, STG, K, MODE);
+    char *stage_base = mine + (size_t)(TILE * TILE * (FILL ? 2 : 1) + 32) * 4;
+    const Stage S = stage_ptrs(stage_base, STG, K, LEVEL);
+    SplatSlot *s_spl = reinterpret_cast<SplatSlot *>(stage_base + stage_bytes(STG, K, LEVEL));
     const int tx0 = (tile % tiles_x) * TILE, ty0 = (tile / tiles_x) * TILE;
     const int tx1 = min(tx0 + TILE, sc.W) - 1, ty1 = min(ty0 + TILE, sc.H) - 1;
     uint32_t *icnt = a.icnt + (size_t)item * TILE * TILE;
@@ -99,7 +111,9 @@ __global__ void __launch_bounds__(kRastWarps * 32) raster_kernel(const __grid_co
         if (lane < cnt) {
             const uint32_t li = cb + lane;
             const uint32_t q = (uint32_t)(__ldg(a.keys + li) & ((1ull << a.depth_bits) - 1ull));
-            stage_fan(sc, S, STG, K, lane, __ldg(a.vals + li), q, MODE);
+            const uint32_t fan = __ldg(a.vals + li);
+            stage_fan(sc, S, STG, K, lane, fan, q, LEVEL);
+            if (SPLAT) s_spl[lane] = splat_setup(a.spl, *sc.cam, fan);
         }
         __syncwarp();
         // The staged fans' rectangles (clipped to the tile) form one packed (fan, pixel)
@@ -129,6 +143,7 @@ __global__ void __launch_bounds__(kRastWarps * 32) raster_kernel(const __grid_co
             const int fexcl = __shfl_sync(0xffffffffu, excl, f);
             uint32_t hits = 0, flags = 0;
             int lp = -1, px = 0, py = 0;
+            float sp_t = 0.0f, sp_a = 0.0f;
             if (idx < total) {
                 ++c_rect;
                 flags = S.flags[f];
@@ -139,7 +154,11 @@ __global__ void __launch_bounds__(kRastWarps * 32) raster_kernel(const __grid_co
                 const int yy = (int)(((float)local + 0.5f) * (1.0f / (float)w));
                 px = rx0 + (local - yy * w);
                 py = ry0 + yy;
-                hits = cover_mask<KT>(S, STG, K, f, flags, (float)px + 0.5f, (float)py + 0.5f);
+                if (SPLAT)
+                    hits = splat_hit(s_spl[f], *sc.cam, a.spl.trunc, (double)px + 0.5, (double)py + 0.5, sp_t, sp_a)
+                               ? 1u : 0u;
+                else
+                    hits = cover_mask<KT>(S, STG, K, f, flags, (float)px + 0.5f, (float)py + 0.5f);
                 if (hits) lp = (py - ty0) * TILE + (px - tx0);
             }
             const int nf = __popc(hits);
@@ -158,7 +177,16 @@ __global__ void __launch_bounds__(kRastWarps * 32) raster_kernel(const __grid_co
             }
             __syncwarp();
             if (nf && (grp >> lane) == 1u) s_cnt[lp] = slot + (uint32_t)nf;   // last lane of its group
-            if (MODE != kCount && nf) {
+            if (SPLAT && FILL && nf) {
+                const uint32_t b = s_base[lp];
+                if (b != 0xffffffffu) {
+                    const SplatSlot &sl = s_spl[f];
+                    float4 *rec = a.frags + (size_t)kRecFwd * ((size_t)b + slot);
+                    rec[0] = make_float4(sp_t, __uint_as_float(S.fan[f]), __uint_as_float(S.q[f]), sp_a);
+                    rec[1] = make_float4(sl.col[0], sl.col[1], sl.col[2], 0.0f);
+                }
+            }
+            if (!SPLAT && FILL && nf) {
                 const uint32_t b = s_base[lp];
                 if (b != 0xffffffffu) {
                     const float pxc = (float)px + 0.5f, pyc = (float)py + 0.5f;
@@ -375,6 +403,10 @@ cudaError_t launch_t(const RastArgs &ra, int64_t max_items, int K, cudaStream_t 
 
 template <int MODE>
 cudaError_t launch_dispatch(const RastArgs &ra, const RenderLayout &L, int K, cudaStream_t st) {
+    if (mode_splat(MODE)) {   // the circumscribing polygons are K = 8 fans
+        if (L.tile == 8) return launch_t<8, kSplatK, MODE>(ra, L.max_items, K, st);
+        return launch_t<16, kSplatK, MODE>(ra, L.max_items, K, st);
+    }
     if (L.tile == 8) {
         if (K == 8) return launch_t<8, 8, MODE>(ra, L.max_items, K, st);
         if (K == 6) return launch_t<8, 6, MODE>(ra, L.max_items, K, st);
@@ -403,6 +435,7 @@ RastArgs make_args(const RenderArgs &ra) {
     a.frags = reinterpret_cast<float4 *>(ra.ws + L.off_frags);
     a.frag_cap = L.frag_cap;
     a.st = reinterpret_cast<Status *>(ra.ws + L.off_status);
+    a.spl = ra.spl;
     return a;
 }
 
@@ -424,7 +457,7 @@ cudaError_t launch_raster_count(const RenderArgs &ra, cudaStream_t st) {
     tile_item_emit_kernel<<<tg, 256, 0, st>>>(ranges, L.n_tiles, nitems, ibase,
                                               reinterpret_cast<uint4 *>(ws + L.off_items), L.max_items, status,
                                               (unsigned long long)L.frag_cap);
-    cudaError_t e = launch_dispatch<kCount>(a, L, ra.K, st);
+    cudaError_t e = ra.splat ? launch_dispatch<kSplatCount>(a, L, ra.K, st) : launch_dispatch<kCount>(a, L, ra.K, st);
     if (e != cudaSuccess) return e;
     if (L.tile == 8)
         item_prefix_kernel<8><<<L.n_tiles, 64, 0, st>>>(nitems, ibase, ra.vt, a.icnt,
@@ -446,7 +479,11 @@ cudaError_t launch_raster(const RenderArgs &ra, bool fill, cudaStream_t st) {
     const RenderLayout &L = ra.L;
     if (L.n_tiles == 0) return cudaSuccess;
     const RastArgs a = make_args(ra);
-    cudaError_t e = fill ? launch_dispatch<kFill>(a, L, ra.K, st) : launch_dispatch<kCount>(a, L, ra.K, st);
+    cudaError_t e;
+    if (ra.splat)
+        e = fill ? launch_dispatch<kSplatFill>(a, L, ra.K, st) : launch_dispatch<kSplatCount>(a, L, ra.K, st);
+    else
+        e = fill ? launch_dispatch<kFill>(a, L, ra.K, st) : launch_dispatch<kCount>(a, L, ra.K, st);
     if (e == cudaSuccess) count_launches(1);
     return e;
 }

@@ -305,4 +305,76 @@ __device__ __forceinline__ void tri_edges(const Stage &S, int CH, int K, int f, 
     E2 = neg ? Sn : Sj;
 }
 
+// ------------------------------------------------------------------------------------
+// Source-Gaussian splats (FP64: the splat image is the reference the fans approximate,
+// drawn once per view, so precision is worth more than speed here)
+// ------------------------------------------------------------------------------------
+
+struct SplatSlot {
+    double mc[3], ua[3], ub[3], n[3];   // camera-space centre, kept unit axes, plane normal
+    double mcn, sa, sb;                 // mc . n, the two kept scales
+    float sigma, col[3];
+};
+
+// The flat Gaussian g in the camera frame: rotation from the normalised quaternion
+// (w, x, y, z), the two kept axes by the same rule as the fan conversion.
+__device__ __forceinline__ SplatSlot splat_setup(const SplatSrc &src, const CamDev &c, uint32_t g) {
+    SplatSlot o;
+    const float4 qf = *reinterpret_cast<const float4 *>(src.quats + 4 * (size_t)g);
+    const double qn = sqrt((double)qf.x * qf.x + (double)qf.y * qf.y + (double)qf.z * qf.z + (double)qf.w * qf.w);
+    const double w = qf.x / qn, x = qf.y / qn, y = qf.z / qn, z = qf.w / qn;
+    const double R[9] = {1 - 2 * (y * y + z * z), 2 * (x * y - w * z),     2 * (x * z + w * y),
+                         2 * (x * y + w * z),     1 - 2 * (x * x + z * z), 2 * (y * z - w * x),
+                         2 * (x * z - w * y),     2 * (y * z + w * x),     1 - 2 * (x * x + y * y)};
+    const float *ls = src.log_scales + 3 * (size_t)g;
+    const float s0 = ls[0], s1 = ls[1], s2 = ls[2];
+    int drop = 0;
+    if (src.axis_rule == 1) {
+        float sm = s0;
+        if (s1 < sm) { drop = 1; sm = s1; }
+        if (s2 < sm) drop = 2;
+    }
+    const int ia = drop == 0 ? 1 : 0, ib = drop == 2 ? 1 : 2;
+    const float *m = src.means + 3 * (size_t)g;
+    const double dm[3] = {(double)m[0] - (double)c.C[0], (double)m[1] - (double)c.C[1], (double)m[2] - (double)c.C[2]};
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        const double R0 = c.R[3 * r], R1 = c.R[3 * r + 1], R2 = c.R[3 * r + 2];
+        o.mc[r] = R0 * dm[0] + R1 * dm[1] + R2 * dm[2];
+        o.ua[r] = R0 * R[ia] + R1 * R[3 + ia] + R2 * R[6 + ia];
+        o.ub[r] = R0 * R[ib] + R1 * R[3 + ib] + R2 * R[6 + ib];
+    }
+    o.n[0] = o.ua[1] * o.ub[2] - o.ua[2] * o.ub[1];
+    o.n[1] = o.ua[2] * o.ub[0] - o.ua[0] * o.ub[2];
+    o.n[2] = o.ua[0] * o.ub[1] - o.ua[1] * o.ub[0];
+    o.mcn = o.mc[0] * o.n[0] + o.mc[1] * o.n[1] + o.mc[2] * o.n[2];
+    o.sa = exp((double)(ia == 0 ? s0 : s1));
+    o.sb = exp((double)(ib == 2 ? s2 : s1));
+    o.sigma = src.opacity[g];
+    o.col[0] = src.rgb[3 * (size_t)g];
+    o.col[1] = src.rgb[3 * (size_t)g + 1];
+    o.col[2] = src.rgb[3 * (size_t)g + 2];
+    return o;
+}
+
+// Ray of pixel centre (px, py) against splat s: kept when the hit lies in front of the
+// near plane and inside the truncation ellipse; t = view depth of the hit (rounded to
+// binary32 as the order key), a = sigma exp(-(u^2/sa^2 + v^2/sb^2)/2).
+__device__ __forceinline__ bool splat_hit(const SplatSlot &s, const CamDev &c, double trunc, double px, double py,
+                                          float &t, float &a) {
+    const double d0 = (px - (double)c.cx) / (double)c.fx, d1 = (py - (double)c.cy) / (double)c.fy;
+    const double den = d0 * s.n[0] + d1 * s.n[1] + s.n[2];
+    if (den == 0.0) return false;
+    const double tt = s.mcn / den;
+    if (!(tt > (double)c.znear)) return false;
+    const double w0 = tt * d0 - s.mc[0], w1 = tt * d1 - s.mc[1], w2 = tt - s.mc[2];
+    const double u = w0 * s.ua[0] + w1 * s.ua[1] + w2 * s.ua[2];
+    const double v = w0 * s.ub[0] + w1 * s.ub[1] + w2 * s.ub[2];
+    const double ru = u / (trunc * s.sa), rv = v / (trunc * s.sb);
+    if (!(ru * ru + rv * rv <= 1.0)) return false;
+    t = (float)tt;
+    a = (float)((double)s.sigma * exp(-0.5 * (u * u / (s.sa * s.sa) + v * v / (s.sb * s.sb))));
+    return true;
+}
+
 }  // namespace ms
