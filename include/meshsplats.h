@@ -243,6 +243,41 @@ MS_API ms_status ms_splat_render(const float *means, const float *log_scales, co
                                  const ms_camera *cams, int32_t n_views, const ms_render_params *params,
                                  float *const *out_rgba, void *workspace, size_t ws_bytes, void *stream);
 
+/*
+ * Learned fan initializer (the project's addition standing in for part of the
+ * fine-tuning of Sec. 3 "Fine-tuning": vertex positions and opacities are optimised
+ * after the conversion).  A perceptron 16 -> 128 -> 128 -> n_out (n_out = 2 (K+1) <= 32)
+ * with exact GELU after the hidden layers, run on the tensor cores (tcgen05.mma, BF16
+ * operands, FP32 accumulation).  Inputs per Gaussian: log-scales (3), normalised
+ * quaternion (4), opacity (1), degree-0 SH (3), scales sorted descending over the largest
+ * (3), log(s_min / s_mid) (1), constant 1.  Outputs: radial corrections dr_0..dr_K then
+ * log-opacity corrections do_0..do_K, the `corr` input of ms_mesh_build.
+ * Weights: FP32 masters W1 (16 x 128), W2 (128 x 128), W3 (128 x n_out), row-major, and a
+ * packed bf16 copy (device, ms_mlp_packed_bytes(), 256-byte aligned, zeroed before first
+ * use: its tail counts expired tensor-core waits, read by ms_mlp_status).
+ */
+MS_API size_t ms_mlp_packed_bytes(void);
+MS_API ms_status ms_mlp_pack(const float *W1, const float *W2, const float *W3, int32_t n_out, void *packed,
+                             void *stream);
+/* X: device N x 16 FP32 inputs. */
+MS_API ms_status ms_mlp_features(const float *log_scales, const float *quats, const float *opacity, const void *sh,
+                                 int32_t sh_dtype, int32_t sh_degree, int64_t N, float *X, void *stream);
+/* corr: device N x n_out FP32 (inputs computed in the kernel from the Gaussians). */
+MS_API ms_status ms_mlp_forward(const float *log_scales, const float *quats, const float *opacity, const void *sh,
+                                int32_t sh_dtype, int32_t sh_degree, int64_t N, const void *packed, int32_t n_out,
+                                float *corr, void *stream);
+/* Training: mean squared error of the outputs for inputs X (n x 16) against targets T
+ * (n x n_out).  ms_mlp_grads overwrites grads (device FP32, the sizes of W1, W2, W3 in that
+ * order) and *loss (device).  ms_mlp_adam updates the masters W (same flat order) with
+ * Adam at step *d_step + 1, advances *d_step and repacks. */
+MS_API size_t ms_mlp_train_workspace_size(int64_t n);
+MS_API ms_status ms_mlp_grads(const float *X, const float *T, int64_t n, int32_t n_out, const void *packed,
+                              float *grads, float *loss, void *workspace, size_t ws_bytes, void *stream);
+MS_API ms_status ms_mlp_adam(float *W, const float *grads, float *m, float *v, int32_t n_out, int32_t *d_step,
+                             float lr, float beta1, float beta2, float eps, void *packed, void *stream);
+/* Synchronises and reads the expired-wait counter: MS_ERR_TIMEOUT if non-zero. */
+MS_API ms_status ms_mlp_status(const void *packed, int32_t *timeouts, void *stream);
+
 /* Candidates the autotuner times: tile in {8, 16, 32} x kbuf in {8, 16}. */
 #define MS_TUNE_CANDIDATES 6
 

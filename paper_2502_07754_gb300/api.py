@@ -360,3 +360,89 @@ class FanAdam:
                                  _ptr(self.m), _ptr(self.v), self.V, self.t, float(self.lr_color),
                                  float(self.lr_color * LR_XYZ_RATIO), float(self.betas[0]), float(self.betas[1]),
                                  float(self.eps), _stream(stream)))
+
+
+class FanMLP:
+    """The learned fan initializer (ms_mlp_*): FP32 master weights, their packed bf16
+    copy, Adam state, and calls for inputs, inference and training steps."""
+
+    N_IN, HIDDEN = 16, 128
+
+    def __init__(self, K=8, weights=None, seed=0, device="cuda"):
+        self.K = int(K)
+        self.n_out = 2 * (self.K + 1)
+        if self.n_out > 32:
+            raise ValueError("K <= 15")
+        self.device = torch.device(device)
+        if weights is None:
+            g = torch.Generator().manual_seed(seed)
+            W1 = torch.randn(self.N_IN, self.HIDDEN, generator=g) * math.sqrt(2.0 / self.N_IN)
+            W2 = torch.randn(self.HIDDEN, self.HIDDEN, generator=g) * math.sqrt(2.0 / self.HIDDEN)
+            W3 = torch.zeros(self.HIDDEN, self.n_out)
+            weights = (W1, W2, W3)
+        flat = torch.cat([torch.as_tensor(w, dtype=torch.float32).reshape(-1) for w in weights])
+        self.W = flat.to(self.device).contiguous()
+        n1, n2 = self.N_IN * self.HIDDEN, self.HIDDEN * self.HIDDEN
+        self.sizes = (n1, n2, self.HIDDEN * self.n_out)
+        self.m = torch.zeros_like(self.W)
+        self.v = torch.zeros_like(self.W)
+        self.step = torch.zeros(1, dtype=torch.int32, device=self.device)
+        self.grads = torch.zeros_like(self.W)
+        self.loss = torch.zeros(1, dtype=torch.float32, device=self.device)
+        self.packed = torch.zeros(int(lib().ms_mlp_packed_bytes()), dtype=torch.uint8, device=self.device)
+        self.ws = None
+        self.pack()
+
+    def weights(self):
+        n1, n2, n3 = self.sizes
+        return (self.W[:n1].view(self.N_IN, self.HIDDEN), self.W[n1:n1 + n2].view(self.HIDDEN, self.HIDDEN),
+                self.W[n1 + n2:].view(self.HIDDEN, self.n_out))
+
+    def pack(self, stream=None):
+        W1, W2, W3 = self.weights()
+        check(lib().ms_mlp_pack(_ptr(W1), _ptr(W2), _ptr(W3), self.n_out, _ptr(self.packed), _stream(stream)))
+
+    @staticmethod
+    def _gauss(log_scales, quats, opacity, sh, sh_degree):
+        sh_dtype = 0 if sh.dtype == torch.float32 else 1
+        return _ptr(log_scales), _ptr(quats), _ptr(opacity), _ptr(sh), sh_dtype, int(sh_degree)
+
+    def features(self, log_scales, quats, opacity, sh, sh_degree, stream=None):
+        N = log_scales.shape[0]
+        X = torch.empty(N, self.N_IN, device=self.device)
+        check(lib().ms_mlp_features(*self._gauss(log_scales, quats, opacity, sh, sh_degree), N, _ptr(X),
+                                    _stream(stream)))
+        return X
+
+    def forward(self, log_scales, quats, opacity, sh, sh_degree, out=None, stream=None):
+        """Corrections N x 2(K+1) for ms_mesh_build."""
+        N = log_scales.shape[0]
+        corr = out if out is not None else torch.empty(N, self.n_out, device=self.device)
+        check(lib().ms_mlp_forward(*self._gauss(log_scales, quats, opacity, sh, sh_degree), N, _ptr(self.packed),
+                                   self.n_out, _ptr(corr), _stream(stream)))
+        return corr
+
+    def compute_grads(self, X, T, stream=None):
+        """Gradients of the mean squared error (into self.grads) and the loss (device)."""
+        n = X.shape[0]
+        need = int(lib().ms_mlp_train_workspace_size(n))
+        if self.ws is None or self.ws.numel() < need:
+            self.ws = torch.empty(max(need, 256), dtype=torch.uint8, device=self.device)
+        check(lib().ms_mlp_grads(_ptr(X), _ptr(T), n, self.n_out, _ptr(self.packed), _ptr(self.grads),
+                                 _ptr(self.loss), _ptr(self.ws), self.ws.numel(), _stream(stream)))
+        return self.grads, self.loss
+
+    def adam(self, lr=1e-3, betas=(0.9, 0.999), eps=1e-8, stream=None):
+        check(lib().ms_mlp_adam(_ptr(self.W), _ptr(self.grads), _ptr(self.m), _ptr(self.v), self.n_out,
+                                _ptr(self.step), float(lr), float(betas[0]), float(betas[1]), float(eps),
+                                _ptr(self.packed), _stream(stream)))
+
+    def train_step(self, X, T, lr=1e-3, stream=None):
+        self.compute_grads(X, T, stream)
+        self.adam(lr, stream=stream)
+        return self.loss
+
+    def status(self, stream=None):
+        t = C.c_int32(0)
+        st = lib().ms_mlp_status(_ptr(self.packed), C.byref(t), _stream(stream))
+        return st, t.value

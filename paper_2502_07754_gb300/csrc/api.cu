@@ -538,6 +538,100 @@ MS_API ms_status ms_adam_step_counted(float *xyz, float *rgb, float *alpha, cons
                        eps, stream);
 }
 
+MS_API size_t ms_mlp_packed_bytes(void) { return mlp_packed_bytes(); }
+
+MS_API ms_status ms_mlp_pack(const float *W1, const float *W2, const float *W3, int32_t n_out, void *packed,
+                             void *stream) {
+    if (!W1 || !W2 || !W3 || !packed) return fail(MS_ERR_INVALID, "NULL pointer");
+    if (n_out < 1 || n_out > 32) return fail(MS_ERR_INVALID, "n_out %d outside 1..32", n_out);
+    if (reinterpret_cast<uintptr_t>(packed) & 255) return fail(MS_ERR_INVALID, "packed weights not 256-byte aligned");
+    cudaError_t e = launch_mlp_pack(W1, W2, W3, n_out, static_cast<char *>(packed), (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "mlp pack launch");
+    count_launches(1);
+    return MS_OK;
+}
+
+static ms_status mlp_src(const float *log_scales, const float *quats, const float *opacity, const void *sh,
+                         int32_t sh_dtype, int32_t sh_degree, int64_t N, MlpSrc &s) {
+    if (N < 0) return fail(MS_ERR_INVALID, "N < 0");
+    if (sh_degree < 0 || sh_degree > 3 || (sh_dtype != 0 && sh_dtype != 1))
+        return fail(MS_ERR_INVALID, "sh_degree %d / sh_dtype %d", sh_degree, sh_dtype);
+    if (N > 0 && (!log_scales || !quats || !opacity || !sh)) return fail(MS_ERR_INVALID, "NULL pointer");
+    if (reinterpret_cast<uintptr_t>(quats) & 15) return fail(MS_ERR_INVALID, "quats must be 16-byte aligned");
+    s.log_scales = log_scales; s.quats = quats; s.opacity = opacity; s.sh = sh;
+    s.sh_dtype = sh_dtype; s.sh_degree = sh_degree;
+    return MS_OK;
+}
+
+MS_API ms_status ms_mlp_features(const float *log_scales, const float *quats, const float *opacity, const void *sh,
+                                 int32_t sh_dtype, int32_t sh_degree, int64_t N, float *X, void *stream) {
+    MlpSrc s;
+    ms_status r = mlp_src(log_scales, quats, opacity, sh, sh_dtype, sh_degree, N, s);
+    if (r != MS_OK) return r;
+    if (N > 0 && !X) return fail(MS_ERR_INVALID, "X is NULL");
+    cudaError_t e = launch_mlp_features(s, N, X, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "mlp features launch");
+    if (N > 0) count_launches(1);
+    return MS_OK;
+}
+
+MS_API ms_status ms_mlp_forward(const float *log_scales, const float *quats, const float *opacity, const void *sh,
+                                int32_t sh_dtype, int32_t sh_degree, int64_t N, const void *packed, int32_t n_out,
+                                float *corr, void *stream) {
+    MlpSrc s;
+    ms_status r = mlp_src(log_scales, quats, opacity, sh, sh_dtype, sh_degree, N, s);
+    if (r != MS_OK) return r;
+    if (!packed || (N > 0 && !corr)) return fail(MS_ERR_INVALID, "NULL pointer");
+    if (n_out < 1 || n_out > 32) return fail(MS_ERR_INVALID, "n_out %d outside 1..32", n_out);
+    if (reinterpret_cast<uintptr_t>(packed) & 255) return fail(MS_ERR_INVALID, "packed weights not 256-byte aligned");
+    cudaError_t e;
+    {
+        StageScope sc(MS_STAGE_MESH_BUILD, (cudaStream_t)stream);
+        e = launch_mlp_forward(s, N, static_cast<const char *>(packed), n_out, corr, (cudaStream_t)stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "mlp forward launch");
+    if (N > 0) count_launches(1);
+    return MS_OK;
+}
+
+MS_API size_t ms_mlp_train_workspace_size(int64_t n) { return n < 0 ? 0 : mlp_act_bytes(n); }
+
+MS_API ms_status ms_mlp_grads(const float *X, const float *T, int64_t n, int32_t n_out, const void *packed,
+                              float *grads, float *loss, void *workspace, size_t ws_bytes, void *stream) {
+    if (n < 0 || n_out < 1 || n_out > 32) return fail(MS_ERR_INVALID, "bad n or n_out");
+    if (!packed || !grads || !loss || (n > 0 && (!X || !T || !workspace))) return fail(MS_ERR_INVALID, "NULL pointer");
+    if (ws_bytes < mlp_act_bytes(n)) return fail(MS_ERR_INVALID, "workspace %zu < %zu", ws_bytes, mlp_act_bytes(n));
+    if ((reinterpret_cast<uintptr_t>(packed) | reinterpret_cast<uintptr_t>(workspace)) & 255)
+        return fail(MS_ERR_INVALID, "packed weights / workspace not 256-byte aligned");
+    cudaError_t e = launch_mlp_grads(X, T, n, n_out, static_cast<const char *>(packed), static_cast<char *>(workspace),
+                                     grads, loss, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "mlp gradient launch");
+    if (n > 0) count_launches(2);
+    return MS_OK;
+}
+
+MS_API ms_status ms_mlp_adam(float *W, const float *grads, float *m, float *v, int32_t n_out, int32_t *d_step,
+                             float lr, float beta1, float beta2, float eps, void *packed, void *stream) {
+    if (!W || !grads || !m || !v || !d_step || !packed) return fail(MS_ERR_INVALID, "NULL pointer");
+    if (n_out < 1 || n_out > 32) return fail(MS_ERR_INVALID, "n_out %d outside 1..32", n_out);
+    cudaError_t e = launch_mlp_adam(W, grads, m, v, n_out, d_step, lr, beta1, beta2, eps, static_cast<char *>(packed),
+                                    (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "mlp adam launch");
+    count_launches(3);
+    return MS_OK;
+}
+
+MS_API ms_status ms_mlp_status(const void *packed, int32_t *timeouts, void *stream) {
+    if (!packed || !timeouts) return fail(MS_ERR_INVALID, "NULL pointer");
+    uint32_t t = 0;
+    cudaError_t e = cudaMemcpyAsync(&t, static_cast<const char *>(packed) + mlp_status_offset(), 4,
+                                    cudaMemcpyDeviceToHost, (cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "mlp status read");
+    *timeouts = (int32_t)t;
+    return t ? fail(MS_ERR_TIMEOUT, "%u bounded tensor-core waits expired", t) : MS_OK;
+}
+
 MS_API void ms_profile_enable(int32_t on) { g_prof = on != 0; }
 
 MS_API ms_status ms_profile_read(double *ms_per_stage, int64_t *launches_per_stage, int32_t n) {

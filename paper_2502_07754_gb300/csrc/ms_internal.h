@@ -61,6 +61,26 @@ struct RenderArgs {
     SplatSrc spl;
 };
 
+// Learned fan initializer (mlp.cu): Gaussian inputs, packed weights, kernels.
+struct MlpSrc {
+    const float *log_scales, *quats, *opacity;
+    const void *sh;
+    int sh_dtype, sh_degree;
+};
+size_t mlp_packed_bytes();
+size_t mlp_act_bytes(int64_t n);
+size_t mlp_param_count(int n_out);
+uint32_t mlp_status_offset();
+cudaError_t launch_mlp_pack(const float *W1, const float *W2, const float *W3, int n_out, char *packed,
+                            cudaStream_t st);
+cudaError_t launch_mlp_features(const MlpSrc &s, int64_t N, float *X, cudaStream_t st);
+cudaError_t launch_mlp_forward(const MlpSrc &s, int64_t N, const char *packed, int n_out, float *corr,
+                               cudaStream_t st);
+cudaError_t launch_mlp_grads(const float *X, const float *T, int64_t n, int n_out, const char *packed, char *act,
+                             float *grads, float *loss, cudaStream_t st);
+cudaError_t launch_mlp_adam(float *W, const float *grads, float *m, float *v, int n_out, int32_t *d_step, float lr,
+                            float b1, float b2, float eps, char *packed, cudaStream_t st);
+
 // Polygons circumscribing the splats' truncation ellipses (K = 8 fans), for binning.
 constexpr int kSplatK = 8;
 cudaError_t launch_splat_polygons(const SplatSrc &s, int64_t N, float *xyz, cudaStream_t st);

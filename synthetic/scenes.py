@@ -182,7 +182,7 @@ def _torus_point(u, v):
 
 
 def _sample_torus(rng, n):
-    out_u, out_v = [], []
+    out_u, out_v = [np.zeros(0)], [np.zeros(0)]
     need = n
     while need > 0:
         u = rng.uniform(0, 2 * np.pi, 2 * need + 16)
