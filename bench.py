@@ -29,8 +29,14 @@ sys.path.insert(0, ROOT)
 
 import numpy as np  # noqa: E402
 
+# multiply-adds x 2 of one row of the initializer: 16x128 + 128x128 + 128x32 (padded outputs)
+MLP_FLOPS_PER_ROW = 2 * (16 * 128 + 128 * 128 + 128 * 32)
+# Gaussian counts of the clustered-surface scenes whose fine-tunes give the initializer's
+# 4 x 125k = 500k training pairs: densities from below to the evaluated scene's
+PAIR_SCENES = (250_000, 500_000, 1_000_000, 3_000_000)
 METRIC = "rendered Mpix/s fwd and fwd+bwd (1080p, 1M fans) vs plain, at 1e-4 image err"
-STAGES = ["mesh_build", "bin", "sort", "raster", "raster_bwd", "loss", "adam"]
+STAGES = ["mesh_build", "bin", "sort", "raster", "raster_bwd", "loss", "adam", "mlp"]
+NSTAGE = len(STAGES)
 # ncu DRAM traffic per launch (bytes) of the kernels, with the source file digest it
 # was captured on; reported only while the digest still matches.
 TRAFFIC = {}
@@ -47,6 +53,9 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-autotune", action="store_true")
+    p.add_argument("--pairs-per-scene", type=int, default=125_000, help="training pairs kept per pair scene")
+    p.add_argument("--finetune-steps", type=int, default=150)
+    p.add_argument("--mlp-steps", type=int, default=400)
     return p.parse_args()
 
 
@@ -215,12 +224,14 @@ def stage_report(stage_ms, stage_n, info, sc, V, K, npx, local):
     except OSError:
         pass
     hbm = float(peaks.get("hbm_gbs", 6800.0))
-    per_launch = {STAGES[i]: stage_ms[i] / max(stage_n[i], 1) for i in range(7)}
+    per_launch = {STAGES[i]: stage_ms[i] / max(stage_n[i], 1) for i in range(NSTAGE)}
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     n_sm = torch.cuda.get_device_properties(local).multi_processor_count
     alu_peak = n_sm * 128 * sm_max * 1e6 / 1e12           # FP32 lane-ops per second, TOP/s
     cov_ops = info.rect_tests * 10 * K + info.fragments * 40
     comp_ops = {"raster": 2 * cov_ops, "raster_bwd": cov_ops + info.commits * 120}
+    tc_flops = {"mlp": sc.n * MLP_FLOPS_PER_ROW}
+    tc_peak = float(peaks.get("bf16_tflops", 1900.0))
     nb = (sc.sh_degree + 1) ** 2 * 3 * (2 if sc.sh_bf16 else 4)
     hbm_bytes = {"mesh_build": sc.n * (44 + nb) + V * 28,
                  "bin": V * 12 + info.pairs * 12,
@@ -235,16 +246,19 @@ def stage_report(stage_ms, stage_n, info, sc, V, K, npx, local):
         if s_ in hbm_bytes:
             ach = hbm_bytes[s_] / (t * 1e-3) / 1e9
             stages[s_] = {"ms": t, "bound": "hbm", "achieved": ach, "unit": "GB/s", "frac": ach / hbm}
+        elif s_ in tc_flops:
+            ach = tc_flops[s_] / (t * 1e-3) / 1e12
+            stages[s_] = {"ms": t, "bound": "tensor", "achieved": ach, "unit": "TFLOP/s", "frac": ach / tc_peak}
         else:
             ach = comp_ops[s_] / (t * 1e-3) / 1e12
             stages[s_] = {"ms": t, "bound": "alu", "achieved": ach, "unit": "TOP/s", "frac": ach / alu_peak}
     dom = max(stages, key=lambda s_: stages[s_]["ms"])
     d = stages[dom]
-    roof = {"kernel": dom, "bound": d["bound"], "achieved": d["achieved"],
-            "peak": hbm if d["bound"] == "hbm" else alu_peak, "unit": d["unit"], "frac": d["frac"],
-            "peak_source": ("measured hbm_gbs (MEASURED_PEAKS.json)" if d["bound"] == "hbm" else
-                            f"{n_sm} SMs x 128 FP32 lanes x {sm_max:.0f} MHz (max SM clock)"),
-            "traffic": TRAFFIC.get(dom)}
+    peak = {"hbm": hbm, "alu": alu_peak, "tensor": tc_peak}[d["bound"]]
+    src = {"hbm": "measured hbm_gbs (MEASURED_PEAKS.json)", "tensor": "measured bf16_tflops (MEASURED_PEAKS.json)",
+           "alu": f"{n_sm} SMs x 128 FP32 lanes x {sm_max:.0f} MHz (max SM clock)"}[d["bound"]]
+    roof = {"kernel": dom, "bound": d["bound"], "achieved": d["achieved"], "peak": peak, "unit": d["unit"],
+            "frac": d["frac"], "peak_source": src, "traffic": TRAFFIC.get(dom)}
     return stages, roof
 
 
@@ -320,9 +334,9 @@ def run_ours(args, ws, rank, local):
     barrier(ws)
     L.ms_profile_enable(0)
     launches = (L.ms_kernel_launches() - launches0) // args.steps
-    stage_ms = (C.c_double * 7)()
-    stage_n = (C.c_int64 * 7)()
-    _lib.check(L.ms_profile_read(stage_ms, stage_n, 7))
+    stage_ms = (C.c_double * NSTAGE)()
+    stage_n = (C.c_int64 * NSTAGE)()
+    _lib.check(L.ms_profile_read(stage_ms, stage_n, NSTAGE))
     step_ms = sum(a_.elapsed_time(b_) for a_, b_ in zip(ev0, ev1)) / args.steps
     step_ms = max_over_ranks(step_ms, ws)
     st, info = rend.info()
@@ -387,6 +401,71 @@ def run_ours(args, ws, rank, local):
     print(json.dumps(line), flush=True)
 
 
+def initializer_experiment(args, w, K, cams, centre, G):
+    """Training pairs from fine-tunes of clustered-surface scenes (the fine-tune workload's
+    generator, other seeds), training of the tensor-core MLP on all of them, then plain
+    vs MLP-initialized conversion + the same fine-tune on the workload's scene, both judged
+    by PSNR against its source-Gaussian render.  Returns (net, report, target)."""
+    import torch
+
+    import synthetic
+    import paper_2502_07754_gb300 as ms
+    from paper_2502_07754_gb300 import initializer as I
+
+    t0 = time.perf_counter()
+    sets = []
+    for i, n in enumerate(PAIR_SCENES):   # every scene gives the same share of the pairs
+        psc = synthetic.surface_scene(n, 3000 + i, degree=3, clustered=True, bf16=True)
+        sets.append(I.make_pairs(I.Gaussians.from_scene(psc), cams, K, args.finetune_steps, centre,
+                                 keep_every=max(1, n // args.pairs_per_scene)))
+    pairs = I.PairSet(torch.cat([p.X for p in sets]).contiguous(), torch.cat([p.T for p in sets]).contiguous())
+    n_pairs = pairs.X.shape[0]
+    t_pairs = time.perf_counter() - t0
+    net = ms.FanMLP(K=K, seed=1)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    l0, l1 = I.train(net, pairs, args.mlp_steps)
+    e1.record()
+    torch.cuda.synchronize()
+    train_ms = e0.elapsed_time(e1) / (args.mlp_steps + 1)      # + the closing gradient pass
+    Gs = I.Gaussians(G[0], G[1], G[2], G[3], G[4], w.scene.sh_degree)
+    corr = torch.empty(Gs.n, 2 * (K + 1), device="cuda")
+    for _ in range(3):
+        net.forward(Gs.log_scales, Gs.quats, Gs.opacity, Gs.sh, Gs.sh_degree, out=corr)
+    f0 = [torch.cuda.Event(enable_timing=True) for _ in range(10)]
+    f1 = [torch.cuda.Event(enable_timing=True) for _ in range(10)]
+    for i in range(10):
+        f0[i].record()
+        net.forward(Gs.log_scales, Gs.quats, Gs.opacity, Gs.sh, Gs.sh_degree, out=corr)
+        f1[i].record()
+    torch.cuda.synchronize()
+    inf_ms = sum(a_.elapsed_time(b_) for a_, b_ in zip(f0, f1)) / 10
+    cmp = I.compare(Gs, cams, K, net, args.finetune_steps, centre, eval_every=10)
+    target = I.source_targets(Gs, cams, centre)
+    st, timeouts = net.status()
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    tc_peak = float(peaks.get("bf16_tflops", 1900.0))
+    inf_tf = Gs.n * MLP_FLOPS_PER_ROW / (inf_ms * 1e-3) / 1e12
+    train_tf = 3 * n_pairs * MLP_FLOPS_PER_ROW / (train_ms * 1e-3) / 1e12
+    report = {
+        "pairs": n_pairs, "pair_scenes": PAIR_SCENES, "finetune_steps": args.finetune_steps,
+        "finetune_lr_color": 5e-4,
+        "pair_generation_s": round(t_pairs, 2),
+        "mlp_train": {"steps": args.mlp_steps, "loss_first": l0, "loss_last": l1, "ms_per_step": train_ms,
+                      "tflops": train_tf, "frac_of_measured_bf16": train_tf / tc_peak},
+        "mlp_inference": {"rows": Gs.n, "ms": inf_ms, "rows_per_s": Gs.n / (inf_ms * 1e-3), "tflops": inf_tf,
+                          "frac_of_measured_bf16": inf_tf / tc_peak},
+        "psnr_db": {"plain": cmp["plain"], "mlp": cmp["mlp"]},
+        "steps_to_plain_final": cmp["steps_to_plain_final"],
+        "tensor_core_timeouts": timeouts,
+    }
+    return net, report, target
+
+
 def run_batch(args, ws, rank, local):
     """The batched multi-view step: 16 cameras of mixed resolution over one fan soup.
     One step = fan conversion, batch render of all views, L1 over all views, batch
@@ -413,12 +492,21 @@ def run_batch(args, ws, rank, local):
     br = ms.BatchRenderer(sc.n, K, cams)
     npx = br.n_pixels
 
-    tg = w.target_scene
-    tG = [dev(tg.means), dev(tg.log_scales), dev(tg.quats), dev(tg.opacity), G[4]]
-    target = br.forward(*ms.mesh_build(*tG, tg.sh_degree, K=K, cam_center=centre)).clone()
-    del tG
+    net, init_report, corr = None, None, None
+    if args.workload == 5:
+        # the learned initializer: trained on pairs from fine-tunes of other scenes, judged
+        # against the plain conversion on this one; its inference is part of every step
+        net, init_report, target = initializer_experiment(args, w, K, cams, centre, G)
+        corr = torch.empty(sc.n, 2 * (K + 1), device="cuda")
+    else:
+        tg = w.target_scene
+        tG = [dev(tg.means), dev(tg.log_scales), dev(tg.quats), dev(tg.opacity), G[4]]
+        target = br.forward(*ms.mesh_build(*tG, tg.sh_degree, K=K, cam_center=centre)).clone()
+        del tG
 
-    xyz, rgb, a = ms.mesh_build(*G, sc.sh_degree, K=K, cam_center=centre)
+    if net is not None:
+        net.forward(G[1], G[2], G[3], G[4], sc.sh_degree, out=corr)
+    xyz, rgb, a = ms.mesh_build(*G, sc.sh_degree, K=K, cam_center=centre, corr=corr)
     br.forward(xyz, rgb, a)
     tune = None
     if not args.no_autotune:
@@ -430,7 +518,9 @@ def run_batch(args, ws, rank, local):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     def step(gs):
-        x, c, al = ms.mesh_build(*gs, sc.sh_degree, K=K, cam_center=centre, out=(xyz, rgb, a))
+        if net is not None:
+            net.forward(gs[1], gs[2], gs[3], gs[4], sc.sh_degree, out=corr)
+        x, c, al = ms.mesh_build(*gs, sc.sh_degree, K=K, cam_center=centre, corr=corr, out=(xyz, rgb, a))
         br.forward(x, c, al, flat, check_status=False)
         loss, dL = ms.l1_loss(flat, target)
         for t in grads:
@@ -492,9 +582,9 @@ def run_batch(args, ws, rank, local):
         step(G)
     torch.cuda.synchronize()
     L.ms_profile_enable(0)
-    stage_ms = (C.c_double * 7)()
-    stage_n = (C.c_int64 * 7)()
-    _lib.check(L.ms_profile_read(stage_ms, stage_n, 7))
+    stage_ms = (C.c_double * NSTAGE)()
+    stage_n = (C.c_int64 * NSTAGE)()
+    _lib.check(L.ms_profile_read(stage_ms, stage_n, NSTAGE))
 
     e2e = None
     if not args.no_e2e:
@@ -533,6 +623,10 @@ def run_batch(args, ws, rank, local):
             "e2e": e2e, "gpu_launches": int(launches), "clocks": clk.summary(), "roofline": roof, "stages": stages,
             "work": {"pairs": info.pairs, "rect_tests": info.rect_tests, "fragments": info.fragments,
                      "commits": info.commits, "extra_passes": info.extra_passes, "sort_bits": info.sort_bits}}
+    if init_report is not None:
+        line["config"]["step"] = ("mlp_forward+mesh_build+batch_render+l1+batch_render_backward+adam "
+                                  "in one CUDA graph")
+        line["initializer"] = init_report
     if tune is not None:
         line["autotune"] = {"cand_ms": [round(x, 3) for x in tune.cand_ms], "best": tune.best,
                             "candidates": "tile 8<<(c//2) x kbuf 8<<(c%2); -1 = not built"}
@@ -550,7 +644,7 @@ def main():
         run_reference(args, ws, rank)
         return
     ws, rank, local = dist_setup()
-    if args.workload == 4:
+    if args.workload in (4, 5):
         run_batch(args, ws, rank, local)
     else:
         run_ours(args, ws, rank, local)

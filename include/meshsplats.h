@@ -121,7 +121,8 @@ typedef enum {
     MS_STAGE_RASTER_BWD = 4,      /* fill, adjoint resolve and gradient scatter */
     MS_STAGE_LOSS = 5,
     MS_STAGE_ADAM = 6,
-    MS_STAGE_COUNT = 7
+    MS_STAGE_MLP = 7,             /* learned initializer inference */
+    MS_STAGE_COUNT = 8
 } ms_stage;
 
 MS_API const char *ms_version(void);
@@ -277,6 +278,18 @@ MS_API ms_status ms_mlp_adam(float *W, const float *grads, float *m, float *v, i
                              float lr, float beta1, float beta2, float eps, void *packed, void *stream);
 /* Synchronises and reads the expired-wait counter: MS_ERR_TIMEOUT if non-zero. */
 MS_API ms_status ms_mlp_status(const void *packed, int32_t *timeouts, void *stream);
+
+/* Mean over n_pixels x RGB of (img - target)^2 into *out (device float, overwritten);
+ * PSNR = -10 log10(*out) for images in [0, 1]. */
+MS_API ms_status ms_mse(const float *img_rgba, const float *target_rgba, int64_t n_pixels, float *out, void *stream);
+
+/* Training targets of the learned initializer from one fine-tune: the corrections (the
+ * corr layout of ms_mesh_build, N x 2(K+1)) that map the converted soup (xyz0, alpha0)
+ * to the fine-tuned one (xyz1, alpha1): dr_i = <o1_i, o0_i> / |o0_i|^2 - 1 with o the
+ * boundary offsets from the original centre (dr_0 = 0), do_k = log(alpha1_k / alpha0_k)
+ * (0 where either is 0).  All device arrays. */
+MS_API ms_status ms_fan_corrections(const float *xyz0, const float *alpha0, const float *xyz1, const float *alpha1,
+                                    int64_t N, int32_t K, float *corr, void *stream);
 
 /* Candidates the autotuner times: tile in {8, 16, 32} x kbuf in {8, 16}. */
 #define MS_TUNE_CANDIDATES 6

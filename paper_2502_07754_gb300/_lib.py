@@ -78,6 +78,8 @@ _SIGS = {
     "ms_splat_workspace_size": (C.c_size_t, [C.c_int64, _P, C.c_int32, _P]),
     "ms_splat_render": (C.c_int, [_P, _P, _P, _P, _P, C.c_int64, C.c_int32, _P, C.c_int32, _P, _P, _P, C.c_size_t,
                                   _P]),
+    "ms_mse": (C.c_int, [_P, _P, C.c_int64, _P, _P]),
+    "ms_fan_corrections": (C.c_int, [_P, _P, _P, _P, C.c_int64, C.c_int32, _P, _P]),
     "ms_mlp_packed_bytes": (C.c_size_t, []),
     "ms_mlp_pack": (C.c_int, [_P, _P, _P, C.c_int32, _P, _P]),
     "ms_mlp_features": (C.c_int, [_P, _P, _P, _P, C.c_int32, C.c_int32, C.c_int64, _P, _P]),

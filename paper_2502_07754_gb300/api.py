@@ -333,6 +333,22 @@ def l1_loss(img_rgba, target_rgba, stream=None):
     return loss, dL
 
 
+def mse(img_rgba, target_rgba, stream=None):
+    """Mean squared RGB error (1-element device tensor)."""
+    out = torch.empty(1, device=img_rgba.device, dtype=torch.float32)
+    check(lib().ms_mse(_ptr(img_rgba), _ptr(target_rgba), img_rgba.numel() // 4, _ptr(out), _stream(stream)))
+    return out
+
+
+def fan_corrections(xyz0, a0, xyz1, a1, K, stream=None):
+    """Corrections (N x 2(K+1)) that turn the converted soup into the fine-tuned one."""
+    N = xyz0.shape[0] // (K + 1)
+    corr = torch.empty(N, 2 * (K + 1), device=xyz0.device, dtype=torch.float32)
+    check(lib().ms_fan_corrections(_ptr(xyz0), _ptr(a0), _ptr(xyz1), _ptr(a1), N, int(K), _ptr(corr),
+                                   _stream(stream)))
+    return corr
+
+
 class FanAdam:
     """Adam over the fan soup: colours/opacities at lr_color, positions at exp(-3) lr_color.
     With device_step=True the step number lives on the device (ms_adam_step_counted), so

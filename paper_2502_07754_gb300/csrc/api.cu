@@ -538,6 +538,26 @@ MS_API ms_status ms_adam_step_counted(float *xyz, float *rgb, float *alpha, cons
                        eps, stream);
 }
 
+MS_API ms_status ms_mse(const float *img_rgba, const float *target_rgba, int64_t n_pixels, float *out, void *stream) {
+    if (n_pixels < 0 || !out || (n_pixels > 0 && (!img_rgba || !target_rgba))) return fail(MS_ERR_INVALID, "bad arguments");
+    if ((reinterpret_cast<uintptr_t>(img_rgba) | reinterpret_cast<uintptr_t>(target_rgba)) & 15)
+        return fail(MS_ERR_INVALID, "images must be 16-byte aligned");
+    cudaError_t e = launch_mse(img_rgba, target_rgba, n_pixels, out, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "mse launch");
+    if (n_pixels > 0) count_launches(1);
+    return MS_OK;
+}
+
+MS_API ms_status ms_fan_corrections(const float *xyz0, const float *alpha0, const float *xyz1, const float *alpha1,
+                                    int64_t N, int32_t K, float *corr, void *stream) {
+    if (N < 0 || K < 3 || K > kMaxK) return fail(MS_ERR_INVALID, "bad N or K");
+    if (N > 0 && (!xyz0 || !alpha0 || !xyz1 || !alpha1 || !corr)) return fail(MS_ERR_INVALID, "NULL pointer");
+    cudaError_t e = launch_fan_corr(xyz0, alpha0, xyz1, alpha1, N, K, corr, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "fan corrections launch");
+    if (N > 0) count_launches(1);
+    return MS_OK;
+}
+
 MS_API size_t ms_mlp_packed_bytes(void) { return mlp_packed_bytes(); }
 
 MS_API ms_status ms_mlp_pack(const float *W1, const float *W2, const float *W3, int32_t n_out, void *packed,
@@ -586,7 +606,7 @@ MS_API ms_status ms_mlp_forward(const float *log_scales, const float *quats, con
     if (reinterpret_cast<uintptr_t>(packed) & 255) return fail(MS_ERR_INVALID, "packed weights not 256-byte aligned");
     cudaError_t e;
     {
-        StageScope sc(MS_STAGE_MESH_BUILD, (cudaStream_t)stream);
+        StageScope sc(MS_STAGE_MLP, (cudaStream_t)stream);
         e = launch_mlp_forward(s, N, static_cast<const char *>(packed), n_out, corr, (cudaStream_t)stream);
     }
     if (e != cudaSuccess) return cuda_fail(e, "mlp forward launch");

@@ -76,7 +76,68 @@ __global__ void adam_kernel(float *__restrict__ xyz, float *__restrict__ rgb, fl
 
 __global__ void step_advance_kernel(int32_t *step) { *step += 1; }
 
+// Mean squared error over the RGB channels of n pixels, accumulated into *out (zeroed by
+// the launcher): the PSNR of a render is -10 log10 of it.
+__global__ void mse_kernel(const float4 *__restrict__ img, const float4 *__restrict__ tgt, int64_t n, float *out) {
+    float acc = 0.0f;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float4 a = img[i], b = tgt[i];
+        const float d0 = a.x - b.x, d1 = a.y - b.y, d2 = a.z - b.z;
+        acc += d0 * d0 + d1 * d1 + d2 * d2;
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    __shared__ float s[32];
+    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        float v = threadIdx.x < (blockDim.x >> 5) ? s[threadIdx.x] : 0.0f;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (threadIdx.x == 0) atomicAdd(out, v / (3.0f * (float)n));
+    }
+}
+
+// Per-fan corrections that turn the conversion (xyz0, a0) into a fine-tuned soup (xyz1,
+// a1): for boundary vertex i the radial component of its new offset from the original
+// centre relative to the original offset, minus 1; for every vertex k the log ratio of
+// the opacities (0 where either is 0).  Row layout as the corr input of mesh_build.
+__global__ void fan_corr_kernel(const float *__restrict__ xyz0, const float *__restrict__ a0,
+                                const float *__restrict__ xyz1, const float *__restrict__ a1, int64_t N, int K,
+                                float *__restrict__ corr) {
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= N) return;
+    const int KV = K + 1;
+    const float *p0 = xyz0 + g * KV * 3, *p1 = xyz1 + g * KV * 3;
+    float *c = corr + g * 2 * KV;
+    c[0] = 0.0f;
+    for (int i = 1; i <= K; ++i) {
+        const float o0x = p0[3 * i] - p0[0], o0y = p0[3 * i + 1] - p0[1], o0z = p0[3 * i + 2] - p0[2];
+        const float o1x = p1[3 * i] - p0[0], o1y = p1[3 * i + 1] - p0[1], o1z = p1[3 * i + 2] - p0[2];
+        const float nn = o0x * o0x + o0y * o0y + o0z * o0z;
+        c[i] = nn > 0.0f ? (o1x * o0x + o1y * o0y + o1z * o0z) / nn - 1.0f : 0.0f;
+    }
+    for (int k = 0; k < KV; ++k) {
+        const float x = a0[g * KV + k], y = a1[g * KV + k];
+        c[KV + k] = (x > 0.0f && y > 0.0f) ? logf(y / x) : 0.0f;
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_mse(const float *img, const float *tgt, int64_t n, float *out, cudaStream_t st) {
+    cudaMemsetAsync(out, 0, sizeof(float), st);
+    if (n == 0) return cudaGetLastError();
+    const int grid = (int)min64((n + 255) / 256, 8 * 152);
+    mse_kernel<<<grid, 256, 0, st>>>(reinterpret_cast<const float4 *>(img), reinterpret_cast<const float4 *>(tgt), n,
+                                     out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fan_corr(const float *xyz0, const float *a0, const float *xyz1, const float *a1, int64_t N, int K,
+                            float *corr, cudaStream_t st) {
+    if (N == 0) return cudaSuccess;
+    fan_corr_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(xyz0, a0, xyz1, a1, N, K, corr);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_l1(const float *img, const float *tgt, int64_t n, float *dL, float *loss, cudaStream_t st) {
     cudaMemsetAsync(loss, 0, sizeof(float), st);
