@@ -140,7 +140,8 @@ RenderLayout render_layout(int64_t n_fans, int K, const ms_camera *cams, int n_v
     L.off_icnt = o;              o = align_up(o + 4 * (size_t)L.max_items * p.tile * p.tile, 256);
     L.off_counts = o;            o = align_up(o + 4 * (size_t)npx, 256);
     L.off_offsets = o;           o = align_up(o + 4 * (size_t)npx, 256);
-    L.off_frags = o;             o = align_up(o + 16 * kRecBwd * (size_t)fcap, 256);
+    L.off_frags = o;             o = align_up(o + 16 * kRecFwd * (size_t)fcap, 256);
+    L.off_fgrad = o;             o = align_up(o + 16 * (size_t)fcap, 256);
     L.off_tfinal = o;            o = align_up(o + 4 * (size_t)npx, 256);
     L.off_ncommit = o;           o = align_up(o + 4 * (size_t)npx, 256);
     L.off_grad = o;              o = align_up(o + 32 * (size_t)L.V, 256);
@@ -260,6 +261,7 @@ static ms_status render_views_backward(const float *xyz, const float *rgb, const
     char *ws = static_cast<char *>(workspace);
     StageScope sc(MS_STAGE_RASTER_BWD, st);
     cudaError_t e = cudaMemsetAsync(ws + L.off_grad, 0, 32 * (size_t)L.V, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ws + L.off_fgrad, 0, 16 * (size_t)L.frag_cap, st);
     if (e != cudaSuccess) return cuda_fail(e, "gradient clear");
     RenderArgs a;
     memset(&a, 0, sizeof(a));
@@ -267,12 +269,12 @@ static ms_status render_views_backward(const float *xyz, const float *rgb, const
     a.d_xyz = d_xyz; a.d_rgb = d_rgb; a.d_alpha = d_alpha;
     a.key_scale = 1.0f;
     a.vt = make_views(cams, n_views, L, nullptr, out_fwd, dL);
-    // the fragment records are regenerated from the sorted tile lists (not kept from the
-    // forward); transmittance is recomputed during the resolve
-    if ((e = launch_raster_fill_bwd(a, st)) != cudaSuccess) return cuda_fail(e, "raster fill launch");
+    // the forward's fragment records are replayed in the same order, recomputing
+    // transmittance; the per-record upstream gradients are then gathered fan by fan
     if ((e = launch_resolve(a, true, st)) != cudaSuccess) return cuda_fail(e, "resolve backward launch");
+    if ((e = launch_raster_grad(a, st)) != cudaSuccess) return cuda_fail(e, "raster gather launch");
     if ((e = launch_grad_scatter(a, st)) != cudaSuccess) return cuda_fail(e, "gradient scatter launch");
-    count_launches(1 + (L.V > 0 ? 1 : 0));   // resolve, scatter (the fill counts itself)
+    count_launches(1 + (L.V > 0 ? 1 : 0));   // resolve, scatter (the gather counts itself)
     return MS_OK;
 }
 

@@ -11,12 +11,13 @@
 // fragments at or before the last committed one.  Order: (depth, triangle id).
 // Compositing stops once the transmittance falls below T_eps.
 //
-// The backward replays the same order, stops after the forward's committed count,
-// and at each committed fragment f forms, from the recomputed transmittance T_f,
-// dC/dc_f = T_f a_f, dC/da_f = T_f c_f - (C_out - C_{<=f}) / (1 - a_f) and
-// dA/da_f = T_out / (1 - a_f), and chains dL/dc_f, dL/da_f to the vertices from the
-// fragment's adjoint record (filled by the rasteriser with everything the chain needs,
-// so no vertex data is gathered here).
+// The backward replays the same order over the forward's records, stops after the
+// forward's committed count, and at each committed fragment f forms, from the
+// recomputed transmittance T_f, dC/dc_f = T_f a_f, dC/da_f = T_f c_f - (C_out -
+// C_{<=f}) / (1 - a_f) and dA/da_f = T_out / (1 - a_f).  It writes dL/dc_f and dL/da_f
+// to the record's gradient slot; the rasteriser's gather pass chains them to the
+// vertices fan by fan (raster.cu), so this pass does no atomics and reads 32 bytes a
+// fragment.
 #include "raster_common.cuh"
 
 namespace ms {
@@ -34,66 +35,9 @@ struct ResolveArgs {
     Status *st;
     float *tfinal;
     uint32_t *ncommit;
-    float4 *grad;
+    float4 *fgrad;             // backward: per record (dL/dc * T a, dL/da)
     ViewTable vt;
 };
-
-// Chain rule from one composited fragment's dL/dc (gc0..2) and dL/da (ga) to its three
-// vertices, using the adjoint record (barycentrics mu and their normaliser W, screen
-// offsets u from the pixel, 1/Z and view X, Y of the vertices, vertex attributes).
-// mu_k = w_k / W with w_k = E_k / Z_k, E_k = cross(u_a, u_b) for the edge opposite k;
-// screen position -> view space -> world space through R_cw^T.  Gradients go to the
-// (xyz, alpha | rgb, 0) scratch with two 16-byte vector atomics per vertex.
-__device__ __forceinline__ void chain_to_vertices(const ResolveArgs &a, const CamDev &c, const float4 *r,
-                                                  uint32_t tri, float gc0, float gc1, float gc2, float ga) {
-    const float4 r2 = r[2], r3 = r[3], r4 = r[4], r5 = r[5], r6 = r[6], r7 = r[7], r8 = r[8], r9 = r[9];
-    const float mu[3] = {r2.x, r2.y, r2.z};
-    const float iW = 1.0f / r2.w;
-    const float ux[3] = {r3.x, r3.z, r4.x}, uy[3] = {r3.y, r3.w, r4.y};
-    const float iz[3] = {r4.z, r4.w, r5.x};
-    const float X[3] = {r5.y, r5.w, r6.y}, Y[3] = {r5.z, r6.x, r6.z};
-    const float al[3] = {r6.w, r7.x, r7.y};
-    const float cr[3] = {r7.z, r8.y, r9.x}, cg[3] = {r7.w, r8.z, r9.y}, cb[3] = {r8.x, r8.w, r9.z};
-    float gmu[3], s = 0.0f;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        gmu[k] = gc0 * cr[k] + gc1 * cg[k] + gc2 * cb[k] + ga * al[k];
-        s += mu[k] * gmu[k];
-    }
-    float gux[3] = {0, 0, 0}, guy[3] = {0, 0, 0}, gZ[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        const int ia = (k + 1) % 3, ib = (k + 2) % 3;
-        const float E = ux[ia] * uy[ib] - uy[ia] * ux[ib];
-        const float gw = (gmu[k] - s) * iW;
-        const float gE = gw * iz[k];
-        gZ[k] = -gw * E * iz[k] * iz[k];
-        gux[ia] += gE * uy[ib];
-        guy[ia] -= gE * ux[ib];
-        guy[ib] += gE * ux[ia];
-        gux[ib] -= gE * uy[ia];
-    }
-    const int K = a.K, KV = K + 1;
-    const uint32_t fan = tri / (uint32_t)K, j = tri - fan * (uint32_t)K;
-    const uint32_t vid[3] = {fan * KV, fan * KV + 1 + j, fan * KV + 1 + (j + 1 == (uint32_t)K ? 0 : j + 1)};
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        const float gX = gux[k] * c.fx * iz[k];
-        const float gY = guy[k] * c.fy * iz[k];
-        const float gZv = gZ[k] - (gux[k] * c.fx * X[k] + guy[k] * c.fy * Y[k]) * iz[k] * iz[k];
-        float4 g0, g1;
-        g0.x = c.R[0] * gX + c.R[3] * gY + c.R[6] * gZv;
-        g0.y = c.R[1] * gX + c.R[4] * gY + c.R[7] * gZv;
-        g0.z = c.R[2] * gX + c.R[5] * gY + c.R[8] * gZv;
-        g0.w = mu[k] * ga;
-        g1.x = mu[k] * gc0;
-        g1.y = mu[k] * gc1;
-        g1.z = mu[k] * gc2;
-        g1.w = 0.0f;
-        atomicAdd(a.grad + 2 * (size_t)vid[k], g0);
-        atomicAdd(a.grad + 2 * (size_t)vid[k] + 1, g1);
-    }
-}
 
 __device__ __forceinline__ bool frag_less(float za, uint32_t ta, float zb, uint32_t tb) {
     return za < zb || (za == zb && ta < tb);
@@ -109,7 +53,7 @@ __global__ void __launch_bounds__(256) resolve_kernel(const __grid_constant__ Re
     int n = valid ? (int)a.counts[pix] : 0;
     const int64_t off = a.offsets[pix];
     if (off + n > a.frag_cap) n = 0;   // the buffer overflowed: reported through the status block
-    constexpr int RS = BWD ? kRecBwd : kRecFwd;   // float4s per record
+    constexpr int RS = kRecFwd;   // float4s per record
     float4 *rec = a.frags + (size_t)RS * off;
 
     float T = 1.0f, C0 = 0.0f, C1 = 0.0f, C2 = 0.0f;
@@ -149,7 +93,7 @@ __global__ void __launch_bounds__(256) resolve_kernel(const __grid_constant__ Re
             const float inv = 1.0f / fmaxf(1.0f - al, 1e-6f);
             const float ga = gR * (T * c0 - (oR - nC0) * inv) + gG * (T * c1 - (oG - nC1) * inv) +
                              gB * (T * c2 - (oB - nC2) * inv) + gA * Tout * inv;
-            chain_to_vertices(a, vw.cam, rc, kt[0], gR * w, gG * w, gB * w, ga);
+            a.fgrad[off + ki[0]] = make_float4(gR * w, gG * w, gB * w, ga);
             C0 = nC0; C1 = nC1; C2 = nC2;
         } else {
             C0 += w * c0;
@@ -282,7 +226,7 @@ cudaError_t launch_resolve(const RenderArgs &ra, bool backward, cudaStream_t st)
     a.st = reinterpret_cast<Status *>(ra.ws + L.off_status);
     a.tfinal = reinterpret_cast<float *>(ra.ws + L.off_tfinal);
     a.ncommit = reinterpret_cast<uint32_t *>(ra.ws + L.off_ncommit);
-    a.grad = reinterpret_cast<float4 *>(ra.ws + L.off_grad);
+    a.fgrad = reinterpret_cast<float4 *>(ra.ws + L.off_fgrad);
     a.vt = ra.vt;
     return backward ? launch_k<true>(a, L.kbuf, L.npx, st) : launch_k<false>(a, L.kbuf, L.npx, st);
 }
