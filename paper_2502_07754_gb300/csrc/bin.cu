@@ -27,6 +27,8 @@ struct BinArgs {
     unsigned long long *state, *keys;
     uint32_t *vals;
     ViewTable vt;
+    float4 *dec;               // [view][vertex] decided (xs, ys, Z, 1/Z), read by the raster passes
+    int64_t V;
 };
 
 // Blocks take virtual ids in start order; id = view * fan_blocks + fan block, so pairs
@@ -83,8 +85,10 @@ __global__ void __launch_bounds__(kBinThreads) bin_kernel(const __grid_constant_
         const uint32_t all = (2u << K) - 1u;   // K+1 vertex bits
         uint32_t vmask = 0;
         float mnx = 3.0e38f, mxx = -3.0e38f, mny = 3.0e38f, mxy = -3.0e38f, zmin = 3.0e38f;
+        float4 *dec = a.dec + (size_t)view * a.V + (size_t)(f0 + tid) * KV;
         for (int k = 0; k < KV; ++k) {
             const DVert d = decide_vertex(cam, p[3 * k], p[3 * k + 1], p[3 * k + 2]);
+            dec[k] = make_float4(d.xs, d.ys, d.Z, d.iz);
             if (d.valid) vmask |= 1u << k;
             mnx = fminf(mnx, d.xs); mxx = fmaxf(mxx, d.xs);
             mny = fminf(mny, d.ys); mxy = fmaxf(mxy, d.ys);
@@ -222,6 +226,8 @@ cudaError_t launch_bin(const RenderArgs &ra, cudaStream_t st) {
     a.keys = reinterpret_cast<unsigned long long *>(ra.ws + L.off_keys0);
     a.vals = reinterpret_cast<uint32_t *>(ra.ws + L.off_vals0);
     a.vt = ra.vt;
+    a.dec = reinterpret_cast<float4 *>(ra.ws + L.off_dec);
+    a.V = L.V;
     bin_kernel<<<(unsigned)L.bin_blocks, kBinThreads, smem, st>>>(a);
     return cudaGetLastError();
 }

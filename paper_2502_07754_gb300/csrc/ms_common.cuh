@@ -117,6 +117,11 @@ __device__ __forceinline__ DVert decide_vertex(const CamDev &c, float px, float 
     return o;
 }
 
+// The validity rule of decide_vertex, from stored decided values.
+__device__ __forceinline__ bool vertex_valid(const CamDev &c, float xs, float ys, float Z) {
+    return (Z > c.znear) && (fabsf(xs) <= kGuardPx) && (fabsf(ys) <= kGuardPx);
+}
+
 __device__ __forceinline__ float dec_area2(float xa, float ya, float xb, float yb, float xc, float yc) {
     return __fsub_rn(__fmul_rn(__fsub_rn(xb, xa), __fsub_rn(yc, ya)),
                      __fmul_rn(__fsub_rn(yb, ya), __fsub_rn(xc, xa)));

@@ -35,6 +35,8 @@ struct RastArgs {
     Status *st;
     SplatSrc spl;              // source Gaussians (splat passes only)
     const float4 *fgrad;       // kGrad: per record (dL/dc * T a, dL/da)
+    const float4 *dec;         // [view][vertex] decided vertices from binning
+    int64_t V;
     float4 *grad;              // kGrad: per vertex (xyz, alpha | rgb, 0) sums
 };
 
@@ -79,6 +81,7 @@ __global__ void __launch_bounds__(kRastWarps * 32) raster_kernel(const __grid_co
     sc.cam = &vw.cam;
     sc.W = vw.cam.width;
     sc.H = vw.cam.height;
+    sc.dec = a.dec + (size_t)view * (size_t)a.V;
     const int tile = (int)(it.x - vw.tile_base);
     const int tiles_x = (int)vw.tiles_x;
     const unsigned long long pix_base = vw.pix_base;
@@ -463,7 +466,10 @@ __global__ void __launch_bounds__(TILE *TILE) item_prefix_kernel(const uint32_t 
 
 template <int TILE, int KT, int MODE>
 cudaError_t launch_t(const RastArgs &ra, int64_t max_items, int K, cudaStream_t st) {
-    constexpr int STG = MODE == kCount ? 32 : 16;
+    // fans staged per chunk: small enough that the shared-memory stage of a warp lets
+    // many warps share an SM (the passes are latency-bound), large enough to keep the
+    // packed (fan, pixel) batches full
+    constexpr int STG = (MODE == kCount || MODE == kSplatCount) ? 16 : 8;
     const size_t smem = kRastWarps * warp_smem_bytes<TILE, STG, MODE>(K);
     auto fn = raster_kernel<TILE, STG, KT, MODE>;
     cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -507,6 +513,8 @@ RastArgs make_args(const RenderArgs &ra) {
     a.st = reinterpret_cast<Status *>(ra.ws + L.off_status);
     a.spl = ra.spl;
     a.fgrad = reinterpret_cast<const float4 *>(ra.ws + L.off_fgrad);
+    a.dec = reinterpret_cast<const float4 *>(ra.ws + L.off_dec);
+    a.V = L.V;
     a.grad = reinterpret_cast<float4 *>(ra.ws + L.off_grad);
     return a;
 }

@@ -13,6 +13,7 @@ struct SceneDev {
     int K;
     const CamDev *cam;   // points into the kernel's __grid_constant__ view table
     int W, H;
+    const float4 *dec;   // this view's decided vertices (xs, ys, Z, 1/Z), written by binning
 };
 
 // ------------------------------------------------------------------------------------
@@ -159,14 +160,15 @@ __device__ __forceinline__ void stage_fan(const SceneDev &a, const Stage &s, int
                                           uint32_t q, int level) {
     const int KV = K + 1;
     const float *p = a.xyz + (size_t)fan * KV * 3;
+    const float4 *dv = a.dec + (size_t)fan * KV;
     uint32_t vmask = 0;
     for (int k = 0; k < KV; ++k) {
-        const DVert d = decide_vertex(*a.cam, __ldg(p + 3 * k), __ldg(p + 3 * k + 1), __ldg(p + 3 * k + 2));
-        s.vx[k * CH + slot] = d.xs;
-        s.vy[k * CH + slot] = d.ys;
-        s.vz[k * CH + slot] = d.Z;
-        s.viz[k * CH + slot] = d.iz;
-        if (d.valid) vmask |= 1u << k;
+        const float4 d = __ldg(dv + k);   // the binning pass's decide_vertex, bit for bit
+        s.vx[k * CH + slot] = d.x;
+        s.vy[k * CH + slot] = d.y;
+        s.vz[k * CH + slot] = d.z;
+        s.viz[k * CH + slot] = d.w;
+        if (vertex_valid(*a.cam, d.x, d.y, d.z)) vmask |= 1u << k;
     }
     const uint32_t tmask = tri_valid_mask(vmask, K);
     float mnx = 3.0e38f, mxx = -3.0e38f, mny = 3.0e38f, mxy = -3.0e38f;
