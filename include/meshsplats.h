@@ -335,8 +335,9 @@ MS_API ms_status ms_l1_loss(const float *img_rgba, const float *target_rgba, int
 /*
  * Adam step on the fan soup (Sec. 3 "Optimization and Pruning": colours and opacities at
  * lr_color, positions at lr_xyz = exp(-3) lr_color).  Parameters and gradients are
- * device SoA arrays of V vertices; m, v: device moments, 7 V floats each (xyz, rgb,
- * alpha), zeroed before step 1.  step counts from 1.  Opacity is clamped to [0, 1].
+ * device SoA arrays of V vertices; m, v: device moments, 7 V floats each laid out like the
+ * parameters ([xyz 3V | rgb 3V | alpha V]), zeroed before step 1.  step counts from 1.
+ * Opacity is clamped to [0, 1].
  */
 MS_API ms_status ms_adam_step(float *xyz, float *rgb, float *alpha, const float *d_xyz, const float *d_rgb,
                               const float *d_alpha, float *m, float *v, int64_t V, int32_t step,

@@ -30,47 +30,71 @@ __global__ void l1_kernel(const float4 *__restrict__ img, const float4 *__restri
     }
 }
 
-__device__ __forceinline__ float adam1(float &p, float g, float &m, float &v, float lr, float b1, float b2, float eps,
+// One Adam update of a flat parameter segment (p, g, m, v of n floats each); clamp01
+// clamps the result to [0, 1] (opacities).  With a device step counter the bias
+// corrections come from *step (already advanced by step_advance).  Moments are laid out
+// like the parameters: [xyz 3V | rgb 3V | alpha V].
+__device__ __forceinline__ float adam1(float p, float g, float &m, float &v, float lr, float b1, float b2, float eps,
                                        float bc1, float bc2) {
     m = b1 * m + (1.0f - b1) * g;
     v = b2 * v + (1.0f - b2) * g * g;
-    p -= lr * (m / bc1) / (sqrtf(v / bc2) + eps);
-    return p;
+    return p - lr * (m / bc1) / (sqrtf(v / bc2) + eps);
 }
 
-// Moments are stored as 7 planes of V floats: x, y, z, r, g, b, alpha.  With a device
-// step counter the bias corrections come from *step (already advanced by step_advance).
-__global__ void adam_kernel(float *__restrict__ xyz, float *__restrict__ rgb, float *__restrict__ alpha,
-                            const float *__restrict__ dx, const float *__restrict__ dc, const float *__restrict__ da,
-                            float *__restrict__ m, float *__restrict__ v, int64_t V, float lr_c, float lr_x, float b1,
-                            float b2, float eps, float bc1, float bc2, const int32_t *step) {
+struct AdamSeg {
+    float *p;
+    const float *g;
+    float *m, *v;
+    int64_t n;
+    float lr;
+    int clamp01;
+};
+
+__global__ void adam_kernel(AdamSeg s0, AdamSeg s1, AdamSeg s2, float b1, float b2, float eps, float bc1, float bc2,
+                            const int32_t *step) {
     if (step) {
         const float t = (float)*step;
         bc1 = 1.0f - powf(b1, t);
         bc2 = 1.0f - powf(b2, t);
     }
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < V; i += (int64_t)gridDim.x * blockDim.x) {
-#pragma unroll
-        for (int r = 0; r < 3; ++r) {
-            float p = xyz[3 * i + r], mm = m[r * V + i], vv = v[r * V + i];
-            adam1(p, dx[3 * i + r], mm, vv, lr_x, b1, b2, eps, bc1, bc2);
-            xyz[3 * i + r] = p;
-            m[r * V + i] = mm;
-            v[r * V + i] = vv;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, nth = (int64_t)gridDim.x * blockDim.x;
+    const AdamSeg segs[3] = {s0, s1, s2};
+#pragma unroll 1
+    for (int k = 0; k < 3; ++k) {
+        const AdamSeg &s = segs[k];
+        const bool vec = ((reinterpret_cast<uintptr_t>(s.p) | reinterpret_cast<uintptr_t>(s.g) |
+                           reinterpret_cast<uintptr_t>(s.m) | reinterpret_cast<uintptr_t>(s.v)) & 15) == 0;
+        int64_t done = 0;
+        if (vec) {   // 16-byte accesses over the aligned body
+            const int64_t n4 = s.n / 4;
+            for (int64_t i = tid; i < n4; i += nth) {
+                float4 p = reinterpret_cast<float4 *>(s.p)[i];
+                const float4 g = reinterpret_cast<const float4 *>(s.g)[i];
+                float4 m = reinterpret_cast<float4 *>(s.m)[i], v = reinterpret_cast<float4 *>(s.v)[i];
+                p.x = adam1(p.x, g.x, m.x, v.x, s.lr, b1, b2, eps, bc1, bc2);
+                p.y = adam1(p.y, g.y, m.y, v.y, s.lr, b1, b2, eps, bc1, bc2);
+                p.z = adam1(p.z, g.z, m.z, v.z, s.lr, b1, b2, eps, bc1, bc2);
+                p.w = adam1(p.w, g.w, m.w, v.w, s.lr, b1, b2, eps, bc1, bc2);
+                if (s.clamp01) {
+                    p.x = fminf(fmaxf(p.x, 0.0f), 1.0f);
+                    p.y = fminf(fmaxf(p.y, 0.0f), 1.0f);
+                    p.z = fminf(fmaxf(p.z, 0.0f), 1.0f);
+                    p.w = fminf(fmaxf(p.w, 0.0f), 1.0f);
+                }
+                reinterpret_cast<float4 *>(s.p)[i] = p;
+                reinterpret_cast<float4 *>(s.m)[i] = m;
+                reinterpret_cast<float4 *>(s.v)[i] = v;
+            }
+            done = n4 * 4;
         }
-#pragma unroll
-        for (int r = 0; r < 3; ++r) {
-            float p = rgb[3 * i + r], mm = m[(3 + r) * V + i], vv = v[(3 + r) * V + i];
-            adam1(p, dc[3 * i + r], mm, vv, lr_c, b1, b2, eps, bc1, bc2);
-            rgb[3 * i + r] = p;
-            m[(3 + r) * V + i] = mm;
-            v[(3 + r) * V + i] = vv;
+        for (int64_t i = done + tid; i < s.n; i += nth) {
+            float m = s.m[i], v = s.v[i];
+            float p = adam1(s.p[i], s.g[i], m, v, s.lr, b1, b2, eps, bc1, bc2);
+            if (s.clamp01) p = fminf(fmaxf(p, 0.0f), 1.0f);
+            s.p[i] = p;
+            s.m[i] = m;
+            s.v[i] = v;
         }
-        float p = alpha[i], mm = m[6 * V + i], vv = v[6 * V + i];
-        adam1(p, da[i], mm, vv, lr_c, b1, b2, eps, bc1, bc2);
-        alpha[i] = fminf(fmaxf(p, 0.0f), 1.0f);
-        m[6 * V + i] = mm;
-        v[6 * V + i] = vv;
     }
 }
 
@@ -158,8 +182,11 @@ cudaError_t launch_adam(float *xyz, float *rgb, float *alpha, const float *dx, c
     }
     if (V == 0) return cudaSuccess;
     const float bc1 = 1.0f - powf(b1, (float)step), bc2 = 1.0f - powf(b2, (float)step);
+    const AdamSeg sx = {xyz, dx, m, v, 3 * V, lr_x, 0};
+    const AdamSeg sc = {rgb, dc, m + 3 * V, v + 3 * V, 3 * V, lr_c, 0};
+    const AdamSeg sa = {alpha, da, m + 6 * V, v + 6 * V, V, lr_c, 1};
     const int grid = (int)min64((V + 255) / 256, 16 * 152);
-    adam_kernel<<<grid, 256, 0, st>>>(xyz, rgb, alpha, dx, dc, da, m, v, V, lr_c, lr_x, b1, b2, eps, bc1, bc2, d_step);
+    adam_kernel<<<grid, 256, 0, st>>>(sx, sc, sa, b1, b2, eps, bc1, bc2, d_step);
     return cudaGetLastError();
 }
 
