@@ -91,7 +91,8 @@ typedef struct {
     float T_eps;            /* early-termination transmittance (default 1e-5) */
     float bg[3];            /* background colour */
     int64_t pair_capacity;  /* (tile, fan) pair capacity of the workspace; 0 = default */
-    int32_t depth_bits;     /* depth bits in the sort key, 8..31 (0 = default 27) */
+    int32_t depth_bits;     /* depth bits in the sort key, 8..31; 0 = automatic: the most (<= 27) that
+                               keep the key within the bytes of tile bits + 20 */
     int64_t frag_capacity;  /* per-pixel fragment records of the workspace; 0 = 8 W H + 65536 */
 } ms_render_params;
 
@@ -128,7 +129,7 @@ typedef enum {
 MS_API const char *ms_version(void);
 /* Message of the last host-side error of this thread (static storage). */
 MS_API const char *ms_last_error(void);
-/* Fills the defaults (tile 16, kbuf 8, T_eps 1e-5, black background, capacity 0, depth bits 27). */
+/* Fills the defaults (tile 16, kbuf 8, T_eps 1e-5, black background, capacities 0, depth bits 0 = automatic). */
 MS_API void ms_render_params_default(ms_render_params *p);
 
 /*

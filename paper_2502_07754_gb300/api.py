@@ -45,7 +45,7 @@ def camera_struct(cam) -> _lib.Camera:
     return c
 
 
-def render_params(tile=16, kbuf=8, T_eps=1e-5, bg=(0.0, 0.0, 0.0), pair_capacity=0, depth_bits=27):
+def render_params(tile=16, kbuf=8, T_eps=1e-5, bg=(0.0, 0.0, 0.0), pair_capacity=0, depth_bits=0):
     p = _lib.RenderParams()
     lib().ms_render_params_default(C.byref(p))
     p.tile, p.kbuf, p.T_eps = int(tile), int(kbuf), float(T_eps)

@@ -3,6 +3,7 @@
 #include <math.h>
 #include <stdarg.h>
 
+#include <algorithm>
 #include <atomic>
 #include <vector>
 #include <stdio.h>
@@ -78,7 +79,7 @@ static void params_or_default(const ms_render_params *p, ms_render_params &out) 
     } else {
         ms_render_params_default(&out);
     }
-    if (out.depth_bits == 0) out.depth_bits = 27;
+    // depth_bits 0: chosen by render_layout
     if (out.T_eps <= 0.0f) out.T_eps = 1e-5f;
 }
 
@@ -100,7 +101,9 @@ RenderLayout render_layout(int64_t n_fans, int K, const ms_camera *cams, int n_v
     L.n_tiles = (int)tiles;
     L.npx = npx;
     L.tile_bits = bits_for(L.n_tiles);
-    L.depth_bits = p.depth_bits;
+    // automatic depth bits: as many as fit (<= 27) without a further byte of sort key
+    // beyond tile bits + 20
+    L.depth_bits = p.depth_bits ? p.depth_bits : std::min(27, 8 * ((L.tile_bits + 20 + 7) / 8) - L.tile_bits);
     L.key_bits = L.tile_bits + L.depth_bits;
     L.passes = (L.key_bits + 7) / 8;
     L.n_fans = n_fans;
@@ -175,7 +178,8 @@ static ms_status check_render_args(const float *xyz, const float *rgb, const flo
     if (p.tile == 32) return fail(MS_ERR_UNSUPPORTED, "tile 32 is not built (one pixel per thread needs 1024 threads)");
     if (p.tile != 8 && p.tile != 16) return fail(MS_ERR_INVALID, "tile %d not in {8,16}", p.tile);
     if (p.kbuf != 8 && p.kbuf != 16) return fail(MS_ERR_INVALID, "kbuf %d not in {8,16}", p.kbuf);
-    if (p.depth_bits < 8 || p.depth_bits > 31) return fail(MS_ERR_INVALID, "depth_bits %d", p.depth_bits);
+    if (p.depth_bits != 0 && (p.depth_bits < 8 || p.depth_bits > 31))
+        return fail(MS_ERR_INVALID, "depth_bits %d", p.depth_bits);
     L = render_layout(n_fans, K, cams, n_views, p);
     if (L.key_bits > 64) return fail(MS_ERR_INVALID, "sort key needs %d bits", L.key_bits);
     if (L.cap >= (1ll << 30)) return fail(MS_ERR_INVALID, "pair capacity %lld >= 2^30", (long long)L.cap);
@@ -344,7 +348,7 @@ MS_API void ms_render_params_default(ms_render_params *p) {
     p->tile = 16;
     p->kbuf = 8;
     p->T_eps = 1e-5f;
-    p->depth_bits = 27;
+    p->depth_bits = 0;
 }
 
 MS_API ms_status ms_mesh_build(const float *means, const float *log_scales, const float *quats, const float *opacity,

@@ -14,17 +14,16 @@ namespace ms {
 namespace {
 
 constexpr int kBinThreads = 256;
-constexpr unsigned long long kFlagAgg = 1ull << 62, kFlagPre = 2ull << 62, kValMask = (1ull << 62) - 1;
 
 struct BinArgs {
     const float *xyz;
     int64_t n_fans;
     int K, tile_shift, depth_bits;
     float key_scale;
-    int64_t cap, nblocks, fan_blocks;
+    int64_t cap, fan_blocks;
     unsigned n_tiles, sort_bits;
     Status *st;
-    unsigned long long *state, *keys;
+    unsigned long long *keys;
     uint32_t *vals;
     ViewTable vt;
     float4 *dec;               // [view][vertex] decided (xs, ys, Z, 1/Z), read by the raster passes
@@ -37,9 +36,8 @@ __global__ void __launch_bounds__(kBinThreads) bin_kernel(const __grid_constant_
     const float *__restrict__ xyz = a.xyz;
     const int64_t n_fans = a.n_fans;
     const int K = a.K, tile_shift = a.tile_shift, depth_bits = a.depth_bits;
-    const int64_t cap = a.cap, nblocks = a.nblocks;
+    const int64_t cap = a.cap;
     Status *st = a.st;
-    unsigned long long *state = a.state;
     unsigned long long *__restrict__ keys = a.keys;
     uint32_t *__restrict__ vals = a.vals;
     extern __shared__ float s_xyz[];   // kBinThreads * (K+1) * 3
@@ -48,17 +46,13 @@ __global__ void __launch_bounds__(kBinThreads) bin_kernel(const __grid_constant_
     __shared__ uint32_t s_q[kBinThreads];
     __shared__ uint32_t s_warp[kBinThreads / 32];
     __shared__ unsigned long long s_excl;
-    __shared__ int s_vid;
     __shared__ unsigned s_culled;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int KV = K + 1;
-    if (tid == 0) {
-        s_vid = (int)atomicAdd(&st->bin_ticket, 1u);
-        s_culled = 0;
-    }
+    if (tid == 0) s_culled = 0;
     __syncthreads();
-    const int64_t vid = s_vid;
+    const int64_t vid = blockIdx.x;
     const int view = (int)(vid / a.fan_blocks);
     const int64_t f0 = (vid - (int64_t)view * a.fan_blocks) * kBinThreads;
     const int nloc = (int)min64(kBinThreads, n_fans - f0);
@@ -144,33 +138,11 @@ __global__ void __launch_bounds__(kBinThreads) bin_kernel(const __grid_constant_
     if (tid == 0) s_off[0] = 0;
     const uint32_t total = s_warp[kBinThreads / 32 - 1];
 
-    // Decoupled look-back over the preceding (already started) blocks.
+    // The block's range of the pair array: one atomic reservation.  Pairs of different
+    // blocks land in an arbitrary order; the sort orders them by key, and fans with equal
+    // keys may then meet a pixel in any order, which the exact-order resolve absorbs.
     if (tid == 0) {
-        unsigned long long excl = 0;
-        if (vid == 0) {
-            st_release_u64(&state[0], kFlagPre | (unsigned long long)total);
-        } else {
-            st_release_u64(&state[vid], kFlagAgg | (unsigned long long)total);
-            int64_t j = vid - 1;
-            uint32_t spins = 0;
-            while (j >= 0) {
-                unsigned long long s = ld_acquire_u64(&state[j]);
-                const unsigned long long flag = s & ~kValMask;
-                if (flag == 0) {
-                    if (++spins > kSpinLimit) {
-                        atomicAdd(&st->timeouts, 1u);
-                        break;
-                    }
-                    continue;
-                }
-                excl += s & kValMask;
-                if (flag == kFlagPre) break;
-                --j;
-            }
-            st_release_u64(&state[vid], kFlagPre | (excl + total));
-        }
-        s_excl = excl;
-        if (vid == nblocks - 1) st->pairs = excl + total;
+        s_excl = total ? atomicAdd(&st->pairs, (unsigned long long)total) : 0ull;
         if (vid == 0) {
             st->cap = (unsigned long long)cap;
             st->n_tiles = a.n_tiles;
@@ -217,12 +189,10 @@ cudaError_t launch_bin(const RenderArgs &ra, cudaStream_t st) {
     a.depth_bits = L.depth_bits;
     a.key_scale = ra.key_scale;
     a.cap = L.cap;
-    a.nblocks = L.bin_blocks;
     a.fan_blocks = L.bin_fan_blocks;
     a.n_tiles = (unsigned)L.n_tiles;
     a.sort_bits = (unsigned)(8 * L.passes);
     a.st = reinterpret_cast<Status *>(ra.ws + L.off_status);
-    a.state = reinterpret_cast<unsigned long long *>(ra.ws + L.off_bin_state);
     a.keys = reinterpret_cast<unsigned long long *>(ra.ws + L.off_keys0);
     a.vals = reinterpret_cast<uint32_t *>(ra.ws + L.off_vals0);
     a.vt = ra.vt;
