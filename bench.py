@@ -53,6 +53,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-autotune", action="store_true")
+    p.add_argument("--tile", type=int, default=16, help="screen tile edge (single-view workloads)")
+    p.add_argument("--kbuf", type=int, default=8, help="per-pixel pending buffer (single-view workloads)")
     p.add_argument("--pairs-per-scene", type=int, default=125_000, help="training pairs kept per pair scene")
     p.add_argument("--finetune-steps", type=int, default=150)
     p.add_argument("--mlp-steps", type=int, default=400)
@@ -287,7 +289,7 @@ def run_ours(args, ws, rank, local):
     # target image: the jittered scene, rendered once (an input of the loss, untimed)
     tg = w.target_scene
     tG = [dev(tg.means), dev(tg.log_scales), dev(tg.quats), dev(tg.opacity), dev(sh_host)]
-    rend = ms.Renderer(sc.n, K, cam)
+    rend = ms.Renderer(sc.n, K, cam, ms.render_params(tile=args.tile, kbuf=args.kbuf))
     txyz, trgb, ta = ms.mesh_build(*tG, tg.sh_degree, K=K, cam_center=cam.C)
     target = rend.forward(txyz, trgb, ta).clone()
     del txyz, trgb, ta, tG
@@ -390,7 +392,7 @@ def run_ours(args, ws, rank, local):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": w.name, "gaussians": sc.n, "K": K, "resolution": f"{W}x{H}",
                        "sh": f"degree {sc.sh_degree} {'bf16' if sc.sh_bf16 else 'f32'}",
-                       "step": "mesh_build+render+l1+render_backward+adam",
+                       "step": "mesh_build+render+l1+render_backward+adam", "tile": args.tile, "kbuf": args.kbuf,
                        "l2": "flushed before every timed step (256 MB write)", "parallelism": "replicas"},
             "fwd_mpix_s": ws * mpix(W, H, fwd_ms), "fwd_ms": fwd_ms,
             "e2e": e2e, "gpu_launches": int(launches), "clocks": clk.summary(), "roofline": roof, "stages": stages,

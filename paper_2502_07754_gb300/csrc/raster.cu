@@ -168,6 +168,10 @@ __global__ void __launch_bounds__(kRastWarps * 32) raster_kernel(const __grid_co
             }
             const int nf = __popc(hits);
             c_frag += nf;
+            if (!FILL) {   // counting: the order of a pixel's slots does not matter yet
+                if (nf) atomicAdd(&s_cnt[lp], (uint32_t)nf);
+                continue;
+            }
             // Lanes that hit the same pixel take consecutive slots in lane order, which is
             // fan order, so a pixel's records keep the depth-key order of the tile list.
             const unsigned grp = __match_any_sync(0xffffffffu, lp);
