@@ -128,20 +128,6 @@ __device__ __forceinline__ bool wait_mma(TcState *S, uint32_t &phase, uint32_t *
     return ok;
 }
 
-// GELU epilogue of a 128-column accumulator into a K-major bf16 tile (this thread's row);
-// also returns nothing else: pre-activations stay in tensor memory.
-__device__ __forceinline__ void gelu_rows(uint32_t tz, char *H, int r) {
-#pragma unroll 1
-    for (int c0 = 0; c0 < kHid; c0 += 16) {
-        float v[16];
-        tc::tmem_ld16(tz + c0, v);
-#pragma unroll
-        for (int i = 0; i < 16; ++i) v[i] = gelu(v[i]);
-        put8(H, kHid, r, c0, v);
-        put8(H, kHid, r, c0 + 8, v + 8);
-    }
-}
-
 // Shared prologue: weights into shared memory, barrier, tensor memory.
 __device__ __forceinline__ void setup(char *smem, const char *packed, uint32_t wbytes_lo, uint32_t wbytes_hi,
                                       char *wdst, TcState *S, uint32_t ncols) {
@@ -175,49 +161,73 @@ constexpr uint32_t kFH2 = kFH1 + kRows * kHid * 2;       // H2
 constexpr uint32_t kFState = kFH2 + kRows * kHid * 2;
 constexpr uint32_t kFwdSmem = kFState + 64;
 
-__global__ void __launch_bounds__(128, 1) mlp_fwd_kernel(const MlpSrc s, int64_t N, const char *__restrict__ packed,
-                                                         int n_out, float *__restrict__ corr) {
+// 16 warps: warp w reads tensor-memory lanes 32 (w % 4) .. + 31 (rows of the tile) and
+// handles accumulator columns 32 (w / 4) .. + 31, so four warps share each row's GELU
+// epilogue; warps 0-3 also compute the inputs and write the outputs.
+constexpr int kFwdThreads = 512;
+
+__device__ __forceinline__ void gelu_cols(uint32_t tz, char *H, int r, int c0) {
+#pragma unroll
+    for (int h = 0; h < 32; h += 16) {
+        float v[16];
+        tc::tmem_ld16(tz + c0 + h, v);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[i] = gelu(v[i]);
+        put8(H, kHid, r, c0 + h, v);
+        put8(H, kHid, r, c0 + h + 8, v + 8);
+    }
+}
+
+__global__ void __launch_bounds__(kFwdThreads, 1) mlp_fwd_kernel(const MlpSrc s, int64_t N,
+                                                                 const char *__restrict__ packed, int n_out,
+                                                                 float *__restrict__ corr) {
     extern __shared__ __align__(1024) char smem[];
     TcState *S = reinterpret_cast<TcState *>(smem + kFState);
     uint32_t *timeouts = reinterpret_cast<uint32_t *>(const_cast<char *>(packed) + kStatusOff);
     setup(smem, packed, kFwdW, kFwdWEnd, smem, S, 256);
     const char *W1 = smem + (kW1f - kFwdW), *W2 = smem + (kW2f - kFwdW), *W3 = smem + (kW3f - kFwdW);
     char *X = smem + kFX, *H1 = smem + kFH1, *H2 = smem + kFH2;
-    const int r = threadIdx.x, warp = r >> 5;
-    const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int r = 32 * (warp & 3) + lane;   // the row (tensor-memory lane) this thread reads
+    const int c0 = 32 * (warp >> 2);        // its accumulator column group
+    const bool row_owner = warp < 4;
+    const uint32_t lane_off = (uint32_t)(32 * (warp & 3)) << 16;
     const uint32_t tZ1 = S->tmem, tZ2 = S->tmem + 128, tZ3 = S->tmem;
     const int64_t tiles = (N + kRows - 1) / kRows;
     uint32_t phase = 0;
     bool ok = true;
     for (int64_t t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
         const int64_t g = t * kRows + r;
-        float f[kIn];
-        if (g < N) {
-            gaussian_features(s, g, f);
-        } else {
+        if (row_owner) {
+            float f[kIn];
+            if (g < N) {
+                gaussian_features(s, g, f);
+            } else {
 #pragma unroll
-            for (int i = 0; i < kIn; ++i) f[i] = 0.0f;
+                for (int i = 0; i < kIn; ++i) f[i] = 0.0f;
+            }
+            put8(X, kIn, r, 0, f);
+            put8(X, kIn, r, 8, f + 8);
         }
-        put8(X, kIn, r, 0, f);
-        put8(X, kIn, r, 8, f + 8);
-        sync_then(r == 0);
-        if (r == 0) issue(tZ1, X, W1, kIn, kHid, false, &S->mbar);
+        sync_then(tid == 0);
+        if (tid == 0) issue(tZ1, X, W1, kIn, kHid, false, &S->mbar);
         ok = wait_mma(S, phase, timeouts);
-        gelu_rows(tZ1 + lane_off, H1, r);
-        sync_then(r == 0);
-        if (r == 0) issue(tZ2, H1, W2, kHid, kHid, false, &S->mbar);
+        gelu_cols(tZ1 + lane_off, H1, r, c0);
+        sync_then(tid == 0);
+        if (tid == 0) issue(tZ2, H1, W2, kHid, kHid, false, &S->mbar);
         ok = wait_mma(S, phase, timeouts) && ok;
-        gelu_rows(tZ2 + lane_off, H2, r);
-        sync_then(r == 0);
-        if (r == 0) issue(tZ3, H2, W3, kHid, kOutPad, false, &S->mbar);
+        gelu_cols(tZ2 + lane_off, H2, r, c0);
+        sync_then(tid == 0);
+        if (tid == 0) issue(tZ3, H2, W3, kHid, kOutPad, false, &S->mbar);
         ok = wait_mma(S, phase, timeouts) && ok;
-        float y[32];
-        tc::tmem_ld16(tZ3 + lane_off, *reinterpret_cast<float(*)[16]>(y));
-        tc::tmem_ld16(tZ3 + lane_off + 16, *reinterpret_cast<float(*)[16]>(y + 16));
-        if (g < N)
-            for (int o = 0; o < n_out; ++o) corr[g * n_out + o] = y[o];
+        if (row_owner) {
+            float y[32];
+            tc::tmem_ld16(tZ3 + lane_off, *reinterpret_cast<float(*)[16]>(y));
+            tc::tmem_ld16(tZ3 + lane_off + 16, *reinterpret_cast<float(*)[16]>(y + 16));
+            if (g < N)
+                for (int o = 0; o < n_out; ++o) corr[g * n_out + o] = y[o];
+        }
         tc::fence_before_sync();
-        __syncthreads();
         ok = __syncthreads_and(ok);
     }
     if (!ok) tc::mbar_wait(&S->mbar, phase, kTcWaitLimit);   // let an unfinished product drain
@@ -517,7 +527,7 @@ cudaError_t launch_mlp_forward(const MlpSrc &s, int64_t N, const char *packed, i
     cudaFuncSetAttribute(mlp_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFwdSmem);
     const int64_t tiles = (N + kRows - 1) / kRows;
     const int grid = (int)min64(tiles, sm_count());
-    mlp_fwd_kernel<<<grid, 128, kFwdSmem, st>>>(s, N, packed, n_out, corr);
+    mlp_fwd_kernel<<<grid, kFwdThreads, kFwdSmem, st>>>(s, N, packed, n_out, corr);
     return cudaGetLastError();
 }
 
