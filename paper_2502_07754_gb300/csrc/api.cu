@@ -145,6 +145,7 @@ RenderLayout render_layout(int64_t n_fans, int K, const ms_camera *cams, int n_v
     L.off_offsets = o;           o = align_up(o + 4 * (size_t)npx, 256);
     L.off_frags = o;             o = align_up(o + 16 * kRecFwd * (size_t)fcap, 256);
     L.off_fgrad = o;             o = align_up(o + 16 * (size_t)fcap, 256);
+    L.off_corder = o;            o = align_up(o + 4 * (size_t)fcap, 256);
     L.off_tfinal = o;            o = align_up(o + 4 * (size_t)npx, 256);
     L.off_ncommit = o;           o = align_up(o + 4 * (size_t)npx, 256);
     L.off_grad = o;              o = align_up(o + 32 * (size_t)L.V, 256);

@@ -11,13 +11,13 @@
 // fragments at or before the last committed one.  Order: (depth, triangle id).
 // Compositing stops once the transmittance falls below T_eps.
 //
-// The backward replays the same order over the forward's records, stops after the
-// forward's committed count, and at each committed fragment f forms, from the
-// recomputed transmittance T_f, dC/dc_f = T_f a_f, dC/da_f = T_f c_f - (C_out -
-// C_{<=f}) / (1 - a_f) and dA/da_f = T_out / (1 - a_f).  It writes dL/dc_f and dL/da_f
-// to the record's gradient slot; the rasteriser's gather pass chains them to the
-// vertices fan by fan (raster.cu), so this pass does no atomics and reads 32 bytes a
-// fragment.
+// The forward also records, per pixel, the record index of each committed fragment in
+// commit order.  The backward walks that list (no pending buffer, no re-reads), and at
+// each committed fragment f forms, from the recomputed transmittance T_f,
+// dC/dc_f = T_f a_f, dC/da_f = T_f c_f - (C_out - C_{<=f}) / (1 - a_f) and
+// dA/da_f = T_out / (1 - a_f).  It writes dL/dc_f and dL/da_f to the record's gradient
+// slot; the rasteriser's gather pass chains them to the vertices fan by fan
+// (raster.cu), so this pass does no atomics.
 #include "raster_common.cuh"
 
 namespace ms {
@@ -36,6 +36,7 @@ struct ResolveArgs {
     float *tfinal;
     uint32_t *ncommit;
     float4 *fgrad;             // backward: per record (dL/dc * T a, dL/da)
+    uint32_t *corder;          // per pixel: record indices in commit order (same offsets as records)
     ViewTable vt;
 };
 
@@ -43,7 +44,7 @@ __device__ __forceinline__ bool frag_less(float za, uint32_t ta, float zb, uint3
     return za < zb || (za == zb && ta < tb);
 }
 
-template <int KB, bool BWD>
+template <int KB>
 __global__ void __launch_bounds__(256) resolve_kernel(const __grid_constant__ ResolveArgs a) {
     const int64_t pix0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool valid = pix0 < a.npx;
@@ -68,17 +69,7 @@ __global__ void __launch_bounds__(256) resolve_kernel(const __grid_constant__ Re
     bool dropped = false;
     int restart = 0x7fffffff;
     bool done = !valid;
-    uint32_t ncom = 0, ncom_limit = 0xffffffffu;
-    float gR = 0, gG = 0, gB = 0, gA = 0, oR = 0, oG = 0, oB = 0, Tout = 0;
-    if (BWD && valid) {
-        ncom_limit = a.ncommit[pix];
-        Tout = a.tfinal[pix];
-        const float4 g = reinterpret_cast<const float4 *>(vw.dL)[lpix];
-        const float4 ov = reinterpret_cast<const float4 *>(vw.out_fwd)[lpix];
-        gR = g.x; gG = g.y; gB = g.z; gA = g.w;
-        oR = ov.x; oG = ov.y; oB = ov.z;
-        if (ncom_limit == 0) done = true;
-    }
+    uint32_t ncom = 0;
 
     auto commit_front = [&]() {
         // colour and opacity are re-read from the record (an L1 / L2 hit) rather than
@@ -88,19 +79,11 @@ __global__ void __launch_bounds__(256) resolve_kernel(const __grid_constant__ Re
         const float4 col = rc[1];
         const float c0 = col.x, c1 = col.y, c2 = col.z;
         const float w = T * al;
-        if (BWD) {
-            const float nC0 = C0 + w * c0, nC1 = C1 + w * c1, nC2 = C2 + w * c2;
-            const float inv = 1.0f / fmaxf(1.0f - al, 1e-6f);
-            const float ga = gR * (T * c0 - (oR - nC0) * inv) + gG * (T * c1 - (oG - nC1) * inv) +
-                             gB * (T * c2 - (oB - nC2) * inv) + gA * Tout * inv;
-            a.fgrad[off + ki[0]] = make_float4(gR * w, gG * w, gB * w, ga);
-            C0 = nC0; C1 = nC1; C2 = nC2;
-        } else {
-            C0 += w * c0;
-            C1 += w * c1;
-            C2 += w * c2;
-        }
+        C0 += w * c0;
+        C1 += w * c1;
+        C2 += w * c2;
         T *= (1.0f - al);
+        a.corder[off + ncom] = ki[0];
         ++ncom;
         fz = kz[0];
         ft = kt[0];
@@ -110,7 +93,7 @@ __global__ void __launch_bounds__(256) resolve_kernel(const __grid_constant__ Re
             kz[i] = kz[i + 1]; kt[i] = kt[i + 1]; ki[i] = ki[i + 1];
         }
         --nb;
-        if (BWD ? (ncom >= ncom_limit) : (T < a.T_eps)) {
+        if (T < a.T_eps) {
             done = true;
             nb = 0;
         }
@@ -171,7 +154,7 @@ __global__ void __launch_bounds__(256) resolve_kernel(const __grid_constant__ Re
         dropped = false;
         restart = 0x7fffffff;
     }
-    if (!BWD) {
+    {
         if (valid) {
             reinterpret_cast<float4 *>(vw.out)[lpix] =
                 make_float4(C0 + T * a.bg0, C1 + T * a.bg1, C2 + T * a.bg2, 1.0f - T);
@@ -183,13 +166,48 @@ __global__ void __launch_bounds__(256) resolve_kernel(const __grid_constant__ Re
     }
 }
 
-template <bool BWD>
-cudaError_t launch_k(const ResolveArgs &ra, int kbuf, int64_t npx, cudaStream_t st) {
+// Backward: replay the forward's committed fragments in their recorded order.
+__global__ void __launch_bounds__(256) resolve_bwd_kernel(const __grid_constant__ ResolveArgs a) {
+    const int64_t pix = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (pix >= a.npx) return;
+    const ViewDev &vw = a.vt.v[view_of_pixel(a.vt, (unsigned long long)pix)];
+    const int64_t lpix = pix - (int64_t)vw.pix_base;
+    const uint32_t n = a.ncommit[pix];
+    if (n == 0) return;
+    const int64_t off = a.offsets[pix];
+    const float4 *rec = a.frags + (size_t)kRecFwd * off;
+    const uint32_t *ord = a.corder + off;
+    const float4 g = reinterpret_cast<const float4 *>(vw.dL)[lpix];
+    const float4 ov = reinterpret_cast<const float4 *>(vw.out_fwd)[lpix];
+    const float Tout = a.tfinal[pix];
+    float T = 1.0f, C0 = 0.0f, C1 = 0.0f, C2 = 0.0f;
+    uint32_t idx = ord[0];
+    for (uint32_t c = 0; c < n; ++c) {
+        const uint32_t nidx = c + 1 < n ? ord[c + 1] : 0u;   // the next index loads early
+        const float4 *rc = rec + (size_t)kRecFwd * idx;
+        const float al = rc[0].w;
+        const float4 col = rc[1];
+        const float w = T * al;
+        const float nC0 = C0 + w * col.x, nC1 = C1 + w * col.y, nC2 = C2 + w * col.z;
+        const float inv = 1.0f / fmaxf(1.0f - al, 1e-6f);
+        const float ga = g.x * (T * col.x - (ov.x - nC0) * inv) + g.y * (T * col.y - (ov.y - nC1) * inv) +
+                         g.z * (T * col.z - (ov.z - nC2) * inv) + g.w * Tout * inv;
+        a.fgrad[off + idx] = make_float4(g.x * w, g.y * w, g.z * w, ga);
+        C0 = nC0; C1 = nC1; C2 = nC2;
+        T *= (1.0f - al);
+        idx = nidx;
+    }
+}
+
+cudaError_t launch_k(const ResolveArgs &ra, bool backward, int kbuf, int64_t npx, cudaStream_t st) {
     const unsigned grid = (unsigned)((npx + 255) / 256);
-    if (kbuf == 16)
-        resolve_kernel<16, BWD><<<grid, 256, 0, st>>>(ra);
+    if (npx == 0) return cudaSuccess;
+    if (backward)
+        resolve_bwd_kernel<<<grid, 256, 0, st>>>(ra);
+    else if (kbuf == 16)
+        resolve_kernel<16><<<grid, 256, 0, st>>>(ra);
     else
-        resolve_kernel<8, BWD><<<grid, 256, 0, st>>>(ra);
+        resolve_kernel<8><<<grid, 256, 0, st>>>(ra);
     return cudaGetLastError();
 }
 
@@ -227,8 +245,9 @@ cudaError_t launch_resolve(const RenderArgs &ra, bool backward, cudaStream_t st)
     a.tfinal = reinterpret_cast<float *>(ra.ws + L.off_tfinal);
     a.ncommit = reinterpret_cast<uint32_t *>(ra.ws + L.off_ncommit);
     a.fgrad = reinterpret_cast<float4 *>(ra.ws + L.off_fgrad);
+    a.corder = reinterpret_cast<uint32_t *>(ra.ws + L.off_corder);
     a.vt = ra.vt;
-    return backward ? launch_k<true>(a, L.kbuf, L.npx, st) : launch_k<false>(a, L.kbuf, L.npx, st);
+    return launch_k(a, backward, L.kbuf, L.npx, st);
 }
 
 cudaError_t launch_grad_scatter(const RenderArgs &ra, cudaStream_t st) {
