@@ -42,17 +42,16 @@ NSTAGE = len(STAGES)
 # on; reported only while the digest still matches.  Taken on the 200k-Gaussian case of
 # the same generator (10.86M fragments) and scaled by fragments to 10.12M (the stage's
 # traffic is per fragment: records written and re-read).
-TRAFFIC = {"raster": {"bytes": 970e6, "digest": "c526186ce11d91df"}}
+TRAFFIC = {"raster": {"bytes": 970e6, "digest": "2d631735de3c35b0"}}
 
 
 def kernel_digest():
+    """Digest of the sources of the rasterisation stage's kernels."""
     import hashlib
-    import glob
     h = hashlib.sha256()
-    for p in sorted(glob.glob(os.path.join(ROOT, "paper_2502_07754_gb300", "csrc", "*"))):
-        if p.endswith((".cu", ".cuh", ".h")):
-            h.update(os.path.basename(p).encode())
-            h.update(open(p, "rb").read())
+    for f in ("raster.cu", "resolve.cu", "raster_common.cuh", "fan_geom.cuh"):
+        h.update(f.encode())
+        h.update(open(os.path.join(ROOT, "paper_2502_07754_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -314,7 +313,6 @@ def run_ours(args, ws, rank, local):
     xyz, rgb, a = convert(G)
     rend.forward(xyz, rgb, a)           # sizes the pair capacity (host check, untimed)
     V = xyz.shape[0]
-    d_xyz, d_rgb, d_a = torch.zeros_like(xyz), torch.zeros_like(rgb), torch.zeros_like(a)
     adam = ms.FanAdam(xyz, rgb, a)
     out = torch.empty(H, W, 4, device="cuda")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
@@ -324,9 +322,8 @@ def run_ours(args, ws, rank, local):
         x, c, al = convert(gs)
         rend.forward(x, c, al, out=out, check_status=False)
         loss, dL = ms.l1_loss(out, target)
-        d_xyz.zero_(); d_rgb.zero_(); d_a.zero_()
-        rend.backward(x, c, al, out, dL, d_xyz, d_rgb, d_a)
-        adam.step(x, c, al, d_xyz, d_rgb, d_a)
+        rend.backward(x, c, al, out, dL, into_workspace=True)   # gradients stay in the workspace
+        adam.step_ws(x, c, al, rend)
         return loss
 
     for _ in range(args.warmup):
@@ -532,7 +529,6 @@ def run_batch(args, ws, rank, local):
         tune = br.autotune(xyz, rgb, a, reps=2, headroom=0.05)
     V = xyz.shape[0]
     flat = br.new_flat()
-    grads = [torch.zeros_like(xyz), torch.zeros_like(rgb), torch.zeros_like(a)]
     adam = ms.FanAdam(xyz, rgb, a, device_step=True)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
@@ -542,10 +538,8 @@ def run_batch(args, ws, rank, local):
         x, c, al = ms.mesh_build(*gs, sc.sh_degree, K=K, cam_center=centre, corr=corr, out=(xyz, rgb, a))
         br.forward(x, c, al, flat, check_status=False)
         loss, dL = ms.l1_loss(flat, target)
-        for t in grads:
-            t.zero_()
-        br.backward(x, c, al, flat, dL, *grads)
-        adam.step(x, c, al, *grads)
+        br.backward(x, c, al, flat, dL, into_workspace=True)   # gradients stay in the workspace
+        adam.step_ws(x, c, al, br)
         return loss
 
     # capture one step in a CUDA graph (after an eager warm-up on a side stream)

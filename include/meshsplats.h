@@ -175,12 +175,23 @@ MS_API ms_status ms_render(const float *xyz, const float *rgb, const float *alph
  * scene must not have changed).  Replays the front-to-back traversal, recomputing
  * transmittance, and accumulates dL/dxyz, dL/drgb, dL/dalpha (device, +=) from dL/drgba
  * (device H x W x 4) and the forward output out_rgba.  Visibility (coverage and order)
- * is held fixed.
+ * is held fixed.  With d_xyz, d_rgb and d_alpha all NULL the gradients are left in the
+ * workspace instead (see ms_render_grad_offset).
  */
 MS_API ms_status ms_render_backward(const float *xyz, const float *rgb, const float *alpha, int64_t n_fans,
                                     int32_t K, const ms_camera *cam, const ms_render_params *params,
                                     const float *out_rgba, const float *dL_drgba, float *d_xyz, float *d_rgb,
                                     float *d_alpha, void *workspace, size_t ws_bytes, void *stream);
+
+/*
+ * Byte offset, within a render workspace, of the gradient sums that ms_render_backward /
+ * ms_batch_render_backward leave there when called with d_xyz = d_rgb = d_alpha = NULL:
+ * per vertex two float4s, (dL/dxyz, dL/dalpha) and (dL/drgb, 0), overwritten by each call.
+ * ms_adam_step_ws consumes them without a separate gradient array.  0 for an invalid
+ * request.
+ */
+MS_API size_t ms_render_grad_offset(int64_t n_fans, int32_t K, const ms_camera *cams, int32_t n_views,
+                                    const ms_render_params *params);
 
 /* Synchronises the stream and reads the device-side outcome recorded in the workspace.
  * Returns MS_ERR_CAPACITY or MS_ERR_TIMEOUT when the last render (single or batch) on it
@@ -343,6 +354,16 @@ MS_API ms_status ms_l1_loss(const float *img_rgba, const float *target_rgba, int
 MS_API ms_status ms_adam_step(float *xyz, float *rgb, float *alpha, const float *d_xyz, const float *d_rgb,
                               const float *d_alpha, float *m, float *v, int64_t V, int32_t step,
                               float lr_color, float lr_xyz, float beta1, float beta2, float eps, void *stream);
+
+/*
+ * ms_adam_step reading the gradients from a render workspace (grad = workspace +
+ * ms_render_grad_offset(...), device, 16-byte aligned; layout as stated there).  With
+ * d_step non-NULL the step number is kept on the device as in ms_adam_step_counted and
+ * `step` is ignored.
+ */
+MS_API ms_status ms_adam_step_ws(float *xyz, float *rgb, float *alpha, const void *grad, float *m, float *v,
+                                 int64_t V, int32_t step, int32_t *d_step, float lr_color, float lr_xyz, float beta1,
+                                 float beta2, float eps, void *stream);
 
 /*
  * ms_adam_step with the step number kept on the device: *d_step (device int32, 0 before

@@ -88,6 +88,9 @@ _SIGS = {
     "ms_mlp_grads": (C.c_int, [_P, _P, C.c_int64, C.c_int32, _P, _P, _P, _P, C.c_size_t, _P]),
     "ms_mlp_adam": (C.c_int, [_P, _P, _P, _P, C.c_int32, _P, C.c_float, C.c_float, C.c_float, C.c_float, _P, _P]),
     "ms_mlp_status": (C.c_int, [_P, _P, _P]),
+    "ms_render_grad_offset": (C.c_size_t, [C.c_int64, C.c_int32, _P, C.c_int32, _P]),
+    "ms_adam_step_ws": (C.c_int, [_P, _P, _P, _P, _P, _P, C.c_int64, C.c_int32, _P, C.c_float, C.c_float, C.c_float,
+                                  C.c_float, C.c_float, _P]),
     "ms_render_noalloc": (C.c_int, [_P, _P, _P, C.c_int64, C.c_int32, _P, _P, _P, _P, _P]),
     "ms_profile_enable": (None, [C.c_int32]),
     "ms_profile_read": (C.c_int, [_P, _P, C.c_int32]),

@@ -128,7 +128,16 @@ class Renderer:
             return out
         raise _lib.MSError(_lib.MS_ERR_CAPACITY, "pair capacity did not converge")
 
-    def backward(self, xyz, rgb, alpha, out_rgba, dL, d_xyz=None, d_rgb=None, d_alpha=None, stream=None):
+    def backward(self, xyz, rgb, alpha, out_rgba, dL, d_xyz=None, d_rgb=None, d_alpha=None, stream=None,
+                 into_workspace=False):
+        """Accumulates the adjoint into (d_xyz, d_rgb, d_alpha); with into_workspace the
+        gradients stay in the workspace for FanAdam.step_ws and None is returned."""
+        if into_workspace:
+            check(lib().ms_render_backward(_ptr(xyz), _ptr(rgb), _ptr(alpha), self.n_fans, self.K,
+                                           C.byref(self.cam), C.byref(self.params), _ptr(out_rgba),
+                                           _ptr(dL.contiguous()), None, None, None, _ptr(self.ws), self.ws.numel(),
+                                           _stream(stream)))
+            return None
         if d_xyz is None:
             d_xyz = torch.zeros_like(xyz)
             d_rgb = torch.zeros_like(rgb)
@@ -137,6 +146,11 @@ class Renderer:
                                        C.byref(self.params), _ptr(out_rgba), _ptr(dL.contiguous()), _ptr(d_xyz),
                                        _ptr(d_rgb), _ptr(d_alpha), _ptr(self.ws), self.ws.numel(), _stream(stream)))
         return d_xyz, d_rgb, d_alpha
+
+    def grad_ptr(self):
+        """Device address of the gradients a backward with into_workspace left behind."""
+        off = lib().ms_render_grad_offset(self.n_fans, self.K, C.byref(self.cam), 1, C.byref(self.params))
+        return C.c_void_p(self.ws.data_ptr() + int(off))
 
 
 class BatchRenderer:
@@ -245,7 +259,18 @@ class BatchRenderer:
         self._alloc()
         return res
 
-    def backward(self, xyz, rgb, alpha, flat, dL_flat, d_xyz=None, d_rgb=None, d_alpha=None, stream=None):
+    def grad_ptr(self):
+        off = lib().ms_render_grad_offset(self.n_fans, self.K, self.cams, self.n_views, C.byref(self.params))
+        return C.c_void_p(self.ws.data_ptr() + int(off))
+
+    def backward(self, xyz, rgb, alpha, flat, dL_flat, d_xyz=None, d_rgb=None, d_alpha=None, stream=None,
+                 into_workspace=False):
+        if into_workspace:
+            check(lib().ms_batch_render_backward(_ptr(xyz), _ptr(rgb), _ptr(alpha), self.n_fans, self.K, self.cams,
+                                                 self.n_views, C.byref(self.params), self._ptrs(flat),
+                                                 self._ptrs(dL_flat), None, None, None, _ptr(self.ws),
+                                                 self.ws.numel(), _stream(stream)))
+            return None
         if d_xyz is None:
             d_xyz = torch.zeros_like(xyz)
             d_rgb = torch.zeros_like(rgb)
@@ -362,6 +387,16 @@ class FanAdam:
         self.v = torch.zeros(7 * self.V, device=xyz.device)
         self.t = 0
         self.d_step = torch.zeros(1, dtype=torch.int32, device=xyz.device) if device_step else None
+
+    def step_ws(self, xyz, rgb, alpha, renderer, stream=None):
+        """One step from the gradients a renderer's backward left in its workspace."""
+        if self.d_step is None:
+            self.t += 1
+        check(lib().ms_adam_step_ws(_ptr(xyz), _ptr(rgb), _ptr(alpha), renderer.grad_ptr(), _ptr(self.m),
+                                    _ptr(self.v), self.V, self.t if self.d_step is None else 0,
+                                    _ptr(self.d_step) if self.d_step is not None else None,
+                                    float(self.lr_color), float(self.lr_color * LR_XYZ_RATIO),
+                                    float(self.betas[0]), float(self.betas[1]), float(self.eps), _stream(stream)))
 
     def step(self, xyz, rgb, alpha, d_xyz, d_rgb, d_alpha, stream=None):
         if self.d_step is not None:

@@ -263,7 +263,9 @@ static ms_status render_views_backward(const float *xyz, const float *rgb, const
     for (int v = 0; v < n_views; ++v)
         if (!out_fwd[v] || !dL[v] || !aligned16(out_fwd[v]) || !aligned16(dL[v]))
             return fail(MS_ERR_INVALID, "view %d: image NULL or not 16-byte aligned", v);
-    if (n_fans > 0 && (!d_xyz || !d_rgb || !d_alpha)) return fail(MS_ERR_INVALID, "gradient pointer is NULL");
+    const bool keep_in_ws = !d_xyz && !d_rgb && !d_alpha;   // gradients stay in the workspace
+    if (n_fans > 0 && !keep_in_ws && (!d_xyz || !d_rgb || !d_alpha))
+        return fail(MS_ERR_INVALID, "gradient pointers must be all set or all NULL");
     char *ws = static_cast<char *>(workspace);
     StageScope sc(MS_STAGE_RASTER_BWD, st);
     cudaError_t e = cudaMemsetAsync(ws + L.off_grad, 0, 32 * (size_t)L.V, st);
@@ -279,8 +281,9 @@ static ms_status render_views_backward(const float *xyz, const float *rgb, const
     // transmittance; the per-record upstream gradients are then gathered fan by fan
     if ((e = launch_resolve(a, true, st)) != cudaSuccess) return cuda_fail(e, "resolve backward launch");
     if ((e = launch_raster_grad(a, st)) != cudaSuccess) return cuda_fail(e, "raster gather launch");
-    if ((e = launch_grad_scatter(a, st)) != cudaSuccess) return cuda_fail(e, "gradient scatter launch");
-    count_launches(1 + (L.V > 0 ? 1 : 0));   // resolve, scatter (the gather counts itself)
+    if (!keep_in_ws && (e = launch_grad_scatter(a, st)) != cudaSuccess)
+        return cuda_fail(e, "gradient scatter launch");
+    count_launches(1 + (L.V > 0 && !keep_in_ws ? 1 : 0));   // resolve, scatter (the gather counts itself)
     return MS_OK;
 }
 
@@ -465,6 +468,14 @@ MS_API ms_status ms_splat_render(const float *means, const float *log_scales, co
                        workspace, ws_bytes, (cudaStream_t)stream);
 }
 
+MS_API size_t ms_render_grad_offset(int64_t n_fans, int32_t K, const ms_camera *cams, int32_t n_views,
+                                    const ms_render_params *params) {
+    if (!cams || K < 3 || K > kMaxK || n_fans < 0 || n_views < 1 || n_views > kMaxViews) return 0;
+    ms_render_params p;
+    params_or_default(params, p);
+    return render_layout(n_fans, K, cams, n_views, p).off_grad;
+}
+
 MS_API ms_status ms_render_get_info(const void *workspace, ms_render_info *info, void *stream) {
     if (!workspace || !info) return fail(MS_ERR_INVALID, "NULL argument");
     Status st;
@@ -535,6 +546,23 @@ MS_API ms_status ms_adam_step(float *xyz, float *rgb, float *alpha, const float 
     if (V < 0 || step < 1) return fail(MS_ERR_INVALID, "bad V or step");
     return adam_common(xyz, rgb, alpha, d_xyz, d_rgb, d_alpha, m, v, V, step, nullptr, lr_color, lr_xyz, beta1, beta2,
                        eps, stream);
+}
+
+MS_API ms_status ms_adam_step_ws(float *xyz, float *rgb, float *alpha, const void *grad, float *m, float *v,
+                                 int64_t V, int32_t step, int32_t *d_step, float lr_color, float lr_xyz, float beta1,
+                                 float beta2, float eps, void *stream) {
+    if (V < 0 || (!d_step && step < 1)) return fail(MS_ERR_INVALID, "bad V or step");
+    if (V > 0 && (!xyz || !rgb || !alpha || !grad || !m || !v)) return fail(MS_ERR_INVALID, "NULL pointer");
+    if (reinterpret_cast<uintptr_t>(grad) & 15) return fail(MS_ERR_INVALID, "gradients not 16-byte aligned");
+    cudaError_t e;
+    {
+        StageScope sc(MS_STAGE_ADAM, (cudaStream_t)stream);
+        e = launch_adam_ws(xyz, rgb, alpha, static_cast<const float4 *>(grad), m, v, V, d_step ? 1 : step, d_step,
+                           lr_color, lr_xyz, beta1, beta2, eps, (cudaStream_t)stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "adam launch");
+    count_launches((V > 0 ? 1 : 0) + (d_step ? 1 : 0));
+    return MS_OK;
 }
 
 MS_API ms_status ms_adam_step_counted(float *xyz, float *rgb, float *alpha, const float *d_xyz, const float *d_rgb,

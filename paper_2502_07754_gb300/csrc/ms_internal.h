@@ -110,6 +110,9 @@ struct StageScope {
 };
 
 cudaError_t launch_l1(const float *img, const float *tgt, int64_t n_pixels, float *dL, float *loss, cudaStream_t st);
+cudaError_t launch_adam_ws(float *xyz, float *rgb, float *alpha, const float4 *grad, float *m, float *v, int64_t V,
+                           int step, int32_t *d_step, float lr_c, float lr_x, float b1, float b2, float eps,
+                           cudaStream_t st);
 cudaError_t launch_mse(const float *img, const float *tgt, int64_t n_pixels, float *out, cudaStream_t st);
 cudaError_t launch_fan_corr(const float *xyz0, const float *a0, const float *xyz1, const float *a1, int64_t N, int K,
                             float *corr, cudaStream_t st);

@@ -100,6 +100,43 @@ __global__ void adam_kernel(AdamSeg s0, AdamSeg s1, AdamSeg s2, float b1, float 
 
 __global__ void step_advance_kernel(int32_t *step) { *step += 1; }
 
+// Adam straight from a render workspace's gradient sums: per vertex (dxyz, dalpha) and
+// (drgb, 0) as two float4s; parameters and moments as in adam_kernel.
+__global__ void adam_ws_kernel(float *__restrict__ xyz, float *__restrict__ rgb, float *__restrict__ alpha,
+                               const float4 *__restrict__ grad, float *__restrict__ m, float *__restrict__ v,
+                               int64_t V, float lr_c, float lr_x, float b1, float b2, float eps, float bc1, float bc2,
+                               const int32_t *step) {
+    if (step) {
+        const float t = (float)*step;
+        bc1 = 1.0f - powf(b1, t);
+        bc2 = 1.0f - powf(b2, t);
+    }
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < V; i += (int64_t)gridDim.x * blockDim.x) {
+        const float4 g0 = grad[2 * i], g1 = grad[2 * i + 1];
+        const float gx[3] = {g0.x, g0.y, g0.z}, gc[3] = {g1.x, g1.y, g1.z};
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            float mm = m[3 * i + r], vv = v[3 * i + r];
+            xyz[3 * i + r] = adam1(xyz[3 * i + r], gx[r], mm, vv, lr_x, b1, b2, eps, bc1, bc2);
+            m[3 * i + r] = mm;
+            v[3 * i + r] = vv;
+        }
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            const int64_t k = 3 * V + 3 * i + r;
+            float mm = m[k], vv = v[k];
+            rgb[3 * i + r] = adam1(rgb[3 * i + r], gc[r], mm, vv, lr_c, b1, b2, eps, bc1, bc2);
+            m[k] = mm;
+            v[k] = vv;
+        }
+        const int64_t k = 6 * V + i;
+        float mm = m[k], vv = v[k];
+        alpha[i] = fminf(fmaxf(adam1(alpha[i], g0.w, mm, vv, lr_c, b1, b2, eps, bc1, bc2), 0.0f), 1.0f);
+        m[k] = mm;
+        v[k] = vv;
+    }
+}
+
 // Mean squared error over the RGB channels of n pixels, accumulated into *out (zeroed by
 // the launcher): the PSNR of a render is -10 log10 of it.
 __global__ void mse_kernel(const float4 *__restrict__ img, const float4 *__restrict__ tgt, int64_t n, float *out) {
@@ -146,6 +183,21 @@ __global__ void fan_corr_kernel(const float *__restrict__ xyz0, const float *__r
 }
 
 }  // namespace
+
+cudaError_t launch_adam_ws(float *xyz, float *rgb, float *alpha, const float4 *grad, float *m, float *v, int64_t V,
+                           int step, int32_t *d_step, float lr_c, float lr_x, float b1, float b2, float eps,
+                           cudaStream_t st) {
+    if (d_step) {
+        step_advance_kernel<<<1, 1, 0, st>>>(d_step);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    if (V == 0) return cudaSuccess;
+    const float bc1 = 1.0f - powf(b1, (float)step), bc2 = 1.0f - powf(b2, (float)step);
+    const int grid = (int)min64((V + 255) / 256, 16 * 152);
+    adam_ws_kernel<<<grid, 256, 0, st>>>(xyz, rgb, alpha, grad, m, v, V, lr_c, lr_x, b1, b2, eps, bc1, bc2, d_step);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_mse(const float *img, const float *tgt, int64_t n, float *out, cudaStream_t st) {
     cudaMemsetAsync(out, 0, sizeof(float), st);
