@@ -642,7 +642,7 @@ def run_batch(args, ws, rank, local):
         line["initializer"] = init_report
     if tune is not None:
         line["autotune"] = {"cand_ms": [round(x, 3) for x in tune.cand_ms], "best": tune.best,
-                            "candidates": "tile 8<<(c//2) x kbuf 8<<(c%2); -1 = not built"}
+                            "candidates": "tile 8<<(c//2) x kbuf 8<<(c%2); negative = skipped"}
     if not args.no_cpu_baseline and ws == 1:
         line["cpu_baseline"] = cpu_baseline(w, K)
     print(json.dumps(line), flush=True)

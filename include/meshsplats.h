@@ -86,7 +86,7 @@ typedef struct {
 } ms_camera;
 
 typedef struct {
-    int32_t tile;           /* screen tile edge in pixels: 8 or 16 (32: MS_ERR_UNSUPPORTED) */
+    int32_t tile;           /* screen tile edge in pixels: 8, 16 or 32 */
     int32_t kbuf;           /* per-pixel pending-fragment buffer: 8 or 16 */
     float T_eps;            /* early-termination transmittance (default 1e-5) */
     float bg[3];            /* background colour */
@@ -308,7 +308,7 @@ MS_API ms_status ms_fan_corrections(const float *xyz0, const float *alpha0, cons
 
 typedef struct {
     /* per candidate c (tile = 8 << (c / 2), kbuf = 8 << (c % 2)): median milliseconds of one
-     * forward+backward batch step, or -1 unsupported (tile 32), -2 workspace too small,
+     * forward+backward batch step, or -2 workspace too small,
      * -3 capacity did not settle */
     float cand_ms[MS_TUNE_CANDIDATES];
     size_t cand_ws_bytes[MS_TUNE_CANDIDATES];   /* workspace each candidate needs (0 if unknown) */

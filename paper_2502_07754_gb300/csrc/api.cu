@@ -176,8 +176,7 @@ static ms_status check_render_args(const float *xyz, const float *rgb, const flo
     if (n_fans < 0) return fail(MS_ERR_INVALID, "n_fans < 0");
     if (n_fans > 0 && (!xyz || !rgb || !alpha)) return fail(MS_ERR_INVALID, "scene pointer is NULL");
     if (n_fans * (int64_t)(K + 1) >= (1ll << 32)) return fail(MS_ERR_INVALID, "too many vertices");
-    if (p.tile == 32) return fail(MS_ERR_UNSUPPORTED, "tile 32 is not built (one pixel per thread needs 1024 threads)");
-    if (p.tile != 8 && p.tile != 16) return fail(MS_ERR_INVALID, "tile %d not in {8,16}", p.tile);
+    if (p.tile != 8 && p.tile != 16 && p.tile != 32) return fail(MS_ERR_INVALID, "tile %d not in {8,16,32}", p.tile);
     if (p.kbuf != 8 && p.kbuf != 16) return fail(MS_ERR_INVALID, "kbuf %d not in {8,16}", p.kbuf);
     if (p.depth_bits != 0 && (p.depth_bits < 8 || p.depth_bits > 31))
         return fail(MS_ERR_INVALID, "depth_bits %d", p.depth_bits);

@@ -2,7 +2,7 @@
 // capacities (tile-pair list, fragment-record list) of the batch render by measurement.
 //
 // Host code only.  Every candidate goes through the public batch entry points, so what
-// is timed is exactly what a caller runs; the tile-32 candidate is reported unsupported.
+// is timed is exactly what a caller runs.
 #include <algorithm>
 #include <string.h>
 #include <vector>
@@ -58,7 +58,6 @@ extern "C" MS_API ms_status ms_batch_autotune(const float *xyz, const float *rgb
         p.tile = 8 << (c / 2);
         p.kbuf = 8 << (c % 2);
         res->cand_ms[c] = -1.0f;
-        if (p.tile == 32) continue;   // not built (MS_ERR_UNSUPPORTED from the render)
         // measure the two list lengths; grow the capacities until a render fits
         bool settled = false;
         for (int attempt = 0; attempt < 4 && !settled; ++attempt) {

@@ -485,12 +485,18 @@ template <int MODE>
 cudaError_t launch_dispatch(const RastArgs &ra, const RenderLayout &L, int K, cudaStream_t st) {
     if (mode_splat(MODE)) {   // the circumscribing polygons are K = 8 fans
         if (L.tile == 8) return launch_t<8, kSplatK, MODE>(ra, L.max_items, K, st);
+        if (L.tile == 32) return launch_t<32, kSplatK, MODE>(ra, L.max_items, K, st);
         return launch_t<16, kSplatK, MODE>(ra, L.max_items, K, st);
     }
     if (L.tile == 8) {
         if (K == 8) return launch_t<8, 8, MODE>(ra, L.max_items, K, st);
         if (K == 6) return launch_t<8, 6, MODE>(ra, L.max_items, K, st);
         return launch_t<8, 0, MODE>(ra, L.max_items, K, st);
+    }
+    if (L.tile == 32) {
+        if (K == 8) return launch_t<32, 8, MODE>(ra, L.max_items, K, st);
+        if (K == 6) return launch_t<32, 6, MODE>(ra, L.max_items, K, st);
+        return launch_t<32, 0, MODE>(ra, L.max_items, K, st);
     }
     if (K == 8) return launch_t<16, 8, MODE>(ra, L.max_items, K, st);
     if (K == 6) return launch_t<16, 6, MODE>(ra, L.max_items, K, st);
@@ -546,6 +552,9 @@ cudaError_t launch_raster_count(const RenderArgs &ra, cudaStream_t st) {
     if (L.tile == 8)
         item_prefix_kernel<8><<<L.n_tiles, 64, 0, st>>>(nitems, ibase, ra.vt, a.icnt,
                                                         reinterpret_cast<uint32_t *>(ws + L.off_counts));
+    else if (L.tile == 32)
+        item_prefix_kernel<32><<<L.n_tiles, 1024, 0, st>>>(nitems, ibase, ra.vt, a.icnt,
+                                                           reinterpret_cast<uint32_t *>(ws + L.off_counts));
     else
         item_prefix_kernel<16><<<L.n_tiles, 256, 0, st>>>(nitems, ibase, ra.vt, a.icnt,
                                                           reinterpret_cast<uint32_t *>(ws + L.off_counts));

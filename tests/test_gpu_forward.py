@@ -62,7 +62,7 @@ def test_render_workload1_all_variants_identical():
     orc, nf, culled = oracle_render(xyz, rgb, a, 8, cam)
     assert culled == 0
     base = None
-    for tile, kb in [(16, 16), (16, 8), (8, 16), (8, 8)]:
+    for tile, kb in [(16, 16), (16, 8), (8, 16), (8, 8), (32, 8), (32, 16)]:
         img, r, _ = gpu_render(xyz, rgb, a, 8, cam, tile=tile, kbuf=kb)
         rep = err_report(img, orc)
         print(json.dumps({"workload": "random-1k", "tile": tile, "kbuf": kb, **rep}))
