@@ -93,11 +93,13 @@ def barrier(ws):
 
 
 def max_over_ranks(x, ws):
+    """The slowest rank's value (every rank gets it); NCCL on GPUs, gloo on the host."""
     if ws == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
