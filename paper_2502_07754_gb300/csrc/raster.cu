@@ -40,7 +40,7 @@ struct RastArgs {
     float4 *grad;              // kGrad: per vertex (xyz, alpha | rgb, 0) sums
 };
 
-constexpr int kRastWarps = 4;   // warps (work items) per block
+constexpr int kRastWarps = 2;   // warps (work items) per block: items differ widely in cost
 
 // Pass kinds: count fragments; fill their 32-byte forward records; gather the adjoint
 // (each fragment's record slot is found exactly as the fill found it; the per-record

@@ -24,6 +24,10 @@ namespace ms {
 
 namespace {
 
+// Pixels differ widely in their fragment counts: small blocks let an SM refill the slots
+// of warps that finished early instead of holding them until the block's slowest warp.
+constexpr int kResolveThreads = 64;
+
 struct ResolveArgs {
     int K;
     int64_t npx;
@@ -45,7 +49,7 @@ __device__ __forceinline__ bool frag_less(float za, uint32_t ta, float zb, uint3
 }
 
 template <int KB>
-__global__ void __launch_bounds__(256) resolve_kernel(const __grid_constant__ ResolveArgs a) {
+__global__ void __launch_bounds__(kResolveThreads) resolve_kernel(const __grid_constant__ ResolveArgs a) {
     const int64_t pix0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool valid = pix0 < a.npx;
     const int64_t pix = valid ? pix0 : 0;
@@ -167,7 +171,7 @@ __global__ void __launch_bounds__(256) resolve_kernel(const __grid_constant__ Re
 }
 
 // Backward: replay the forward's committed fragments in their recorded order.
-__global__ void __launch_bounds__(256) resolve_bwd_kernel(const __grid_constant__ ResolveArgs a) {
+__global__ void __launch_bounds__(kResolveThreads) resolve_bwd_kernel(const __grid_constant__ ResolveArgs a) {
     const int64_t pix = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (pix >= a.npx) return;
     const ViewDev &vw = a.vt.v[view_of_pixel(a.vt, (unsigned long long)pix)];
@@ -200,14 +204,14 @@ __global__ void __launch_bounds__(256) resolve_bwd_kernel(const __grid_constant_
 }
 
 cudaError_t launch_k(const ResolveArgs &ra, bool backward, int kbuf, int64_t npx, cudaStream_t st) {
-    const unsigned grid = (unsigned)((npx + 255) / 256);
+    const unsigned grid = (unsigned)((npx + kResolveThreads - 1) / kResolveThreads);
     if (npx == 0) return cudaSuccess;
     if (backward)
-        resolve_bwd_kernel<<<grid, 256, 0, st>>>(ra);
+        resolve_bwd_kernel<<<grid, kResolveThreads, 0, st>>>(ra);
     else if (kbuf == 16)
-        resolve_kernel<16><<<grid, 256, 0, st>>>(ra);
+        resolve_kernel<16><<<grid, kResolveThreads, 0, st>>>(ra);
     else
-        resolve_kernel<8><<<grid, 256, 0, st>>>(ra);
+        resolve_kernel<8><<<grid, kResolveThreads, 0, st>>>(ra);
     return cudaGetLastError();
 }
 
