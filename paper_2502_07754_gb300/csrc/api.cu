@@ -133,6 +133,7 @@ RenderLayout render_layout(int64_t n_fans, int K, const ms_camera *cams, int n_v
     L.off_ranges = o;            o = align_up(o + 8 * (size_t)L.n_tiles, 256);
     L.off_scan_state = o;        o = align_up(o + 8 * (size_t)L.scan_blocks, 256);
     L.off_tscan_state = o;       o = align_up(o + 8 * (size_t)L.tscan_blocks, 256);
+    L.off_pbucket = o;           o = align_up(o + 2 * 256 * 4, 256);   // pixel-count histogram, fill cursors
     L.off_keys0 = o;             o = align_up(o + 8 * (size_t)cap, 256);   // (zeroed prefix ends here)
     L.off_keys1 = o;             o = align_up(o + 8 * (size_t)cap, 256);
     L.off_vals0 = o;             o = align_up(o + 4 * (size_t)cap, 256);
@@ -143,6 +144,7 @@ RenderLayout render_layout(int64_t n_fans, int K, const ms_camera *cams, int n_v
     L.off_icnt = o;              o = align_up(o + 4 * (size_t)L.max_items * p.tile * p.tile, 256);
     L.off_counts = o;            o = align_up(o + 4 * (size_t)npx, 256);
     L.off_offsets = o;           o = align_up(o + 4 * (size_t)npx, 256);
+    L.off_perm = o;              o = align_up(o + 8 * (size_t)npx, 256);   // forward, backward pixel orders
     L.off_frags = o;             o = align_up(o + 16 * kRecFwd * (size_t)fcap, 256);
     L.off_fgrad = o;             o = align_up(o + 16 * (size_t)fcap, 256);
     L.off_corder = o;            o = align_up(o + 4 * (size_t)fcap, 256);
@@ -267,8 +269,9 @@ static ms_status render_views_backward(const float *xyz, const float *rgb, const
         return fail(MS_ERR_INVALID, "gradient pointers must be all set or all NULL");
     char *ws = static_cast<char *>(workspace);
     StageScope sc(MS_STAGE_RASTER_BWD, st);
+    // (the backward resolve writes every record's upstream gradient, zero where a record
+    // was not composited, so only the vertex sums are cleared here)
     cudaError_t e = cudaMemsetAsync(ws + L.off_grad, 0, 32 * (size_t)L.V, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(ws + L.off_fgrad, 0, 16 * (size_t)L.frag_cap, st);
     if (e != cudaSuccess) return cuda_fail(e, "gradient clear");
     RenderArgs a;
     memset(&a, 0, sizeof(a));

@@ -34,7 +34,7 @@ struct RenderLayout {
     int64_t npx, n_fans, V, cap, frag_cap;
     int64_t bin_fan_blocks, bin_blocks, sort_blocks, scan_blocks, tscan_blocks, max_items;
     size_t off_status, off_bin_state, off_keys0, off_keys1, off_vals0, off_vals1, off_hist, off_lookback,
-        off_ranges, off_scan_state, off_tscan_state, off_tile_nitems, off_tile_ibase, off_items, off_icnt,
+        off_ranges, off_scan_state, off_tscan_state, off_pbucket, off_perm, off_tile_nitems, off_tile_ibase, off_items, off_icnt,
         off_counts, off_offsets, off_frags, off_fgrad, off_corder, off_tfinal, off_ncommit, off_grad, off_dec, total;
 };
 
@@ -93,6 +93,7 @@ cudaError_t launch_raster(const RenderArgs &a, bool fill, cudaStream_t st);
 cudaError_t launch_raster_count(const RenderArgs &a, cudaStream_t st);   // items, count, prefix, pixel scan
 cudaError_t launch_raster_grad(const RenderArgs &a, cudaStream_t st);   // adjoint gather to the vertices
 constexpr int kRecFwd = 2;   // float4s per fragment record
+cudaError_t launch_pixel_order(const RenderArgs &a, cudaStream_t st);   // resolve order of the pixels
 cudaError_t launch_resolve(const RenderArgs &a, bool backward, cudaStream_t st);
 cudaError_t launch_grad_scatter(const RenderArgs &a, cudaStream_t st);
 

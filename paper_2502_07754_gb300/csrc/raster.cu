@@ -434,16 +434,19 @@ __global__ void tile_item_emit_kernel(const uint2 *__restrict__ ranges, int n_ti
             items[b + k] = make_uint4((uint32_t)t, r.x + k * kItemFans, min(r.y, r.x + (k + 1) * kItemFans), k);
 }
 
-// Per tile: exclusive prefix of the (item, pixel) counts over the tile's items, and the
-// pixel totals.  One block per tile, one thread per pixel; loads are issued four items
+// Per tile: exclusive prefix of the (item, pixel) counts over the tile's items, the
+// pixel totals, and their histogram by count_bucket (for the resolve's pixel order).  One block per tile, one thread per pixel; loads are issued four items
 // at a time so a tile with many items is not latency-bound.
 template <int TILE>
 __global__ void __launch_bounds__(TILE *TILE) item_prefix_kernel(const uint32_t *__restrict__ nitems,
                                                                  const uint32_t *__restrict__ ibase,
                                                                  const __grid_constant__ ViewTable vt,
                                                                  uint32_t *__restrict__ icnt,
-                                                                 uint32_t *__restrict__ counts) {
+                                                                 uint32_t *__restrict__ counts,
+                                                                 uint32_t *__restrict__ hist) {
+    __shared__ uint32_t s_hist[kCountBuckets];
     const int t = blockIdx.x, i = threadIdx.x;
+    for (int b = i; b < kCountBuckets; b += TILE * TILE) s_hist[b] = 0;
     const uint32_t n = nitems[t], b = ibase[t];
     uint32_t *c = icnt + (size_t)b * TILE * TILE + i;
     uint32_t run = 0;
@@ -465,7 +468,14 @@ __global__ void __launch_bounds__(TILE *TILE) item_prefix_kernel(const uint32_t 
     const ViewDev &vw = vt.v[view_of_tile(vt, (uint32_t)t)];
     const int lt = t - (int)vw.tile_base, tiles_x = (int)vw.tiles_x;
     const int x = (lt % tiles_x) * TILE + (i % TILE), y = (lt / tiles_x) * TILE + (i / TILE);
-    if (x < vw.cam.width && y < vw.cam.height) counts[vw.pix_base + (size_t)y * vw.cam.width + x] = run;
+    __syncthreads();
+    if (x < vw.cam.width && y < vw.cam.height) {
+        counts[vw.pix_base + (size_t)y * vw.cam.width + x] = run;
+        atomicAdd(&s_hist[count_bucket(run)], 1u);
+    }
+    __syncthreads();
+    for (int b = i; b < kCountBuckets; b += TILE * TILE)
+        if (s_hist[b]) atomicAdd(&hist[b], s_hist[b]);
 }
 
 template <int TILE, int KT, int MODE>
@@ -549,15 +559,14 @@ cudaError_t launch_raster_count(const RenderArgs &ra, cudaStream_t st) {
                                               (unsigned long long)L.frag_cap);
     cudaError_t e = ra.splat ? launch_dispatch<kSplatCount>(a, L, ra.K, st) : launch_dispatch<kCount>(a, L, ra.K, st);
     if (e != cudaSuccess) return e;
+    uint32_t *cnts = reinterpret_cast<uint32_t *>(ws + L.off_counts);
+    uint32_t *hist = reinterpret_cast<uint32_t *>(ws + L.off_pbucket);
     if (L.tile == 8)
-        item_prefix_kernel<8><<<L.n_tiles, 64, 0, st>>>(nitems, ibase, ra.vt, a.icnt,
-                                                        reinterpret_cast<uint32_t *>(ws + L.off_counts));
+        item_prefix_kernel<8><<<L.n_tiles, 64, 0, st>>>(nitems, ibase, ra.vt, a.icnt, cnts, hist);
     else if (L.tile == 32)
-        item_prefix_kernel<32><<<L.n_tiles, 1024, 0, st>>>(nitems, ibase, ra.vt, a.icnt,
-                                                           reinterpret_cast<uint32_t *>(ws + L.off_counts));
+        item_prefix_kernel<32><<<L.n_tiles, 1024, 0, st>>>(nitems, ibase, ra.vt, a.icnt, cnts, hist);
     else
-        item_prefix_kernel<16><<<L.n_tiles, 256, 0, st>>>(nitems, ibase, ra.vt, a.icnt,
-                                                          reinterpret_cast<uint32_t *>(ws + L.off_counts));
+        item_prefix_kernel<16><<<L.n_tiles, 256, 0, st>>>(nitems, ibase, ra.vt, a.icnt, cnts, hist);
     const int64_t n = L.npx;
     scan_u32_kernel<<<(unsigned)L.scan_blocks, kScanThreads, 0, st>>>(
         reinterpret_cast<const uint32_t *>(ws + L.off_counts), reinterpret_cast<uint32_t *>(ws + L.off_offsets), n,
@@ -565,6 +574,7 @@ cudaError_t launch_raster_count(const RenderArgs &ra, cudaStream_t st) {
         &status->frags, status);
     e = cudaGetLastError();
     if (e == cudaSuccess) count_launches(6);
+    if (e == cudaSuccess) e = launch_pixel_order(ra, st);
     return e;
 }
 

@@ -8,6 +8,12 @@
 
 namespace ms {
 
+// Pixels are resolved in descending order of their fragment counts, clamped here.
+constexpr int kCountBuckets = 256;
+__device__ __forceinline__ int count_bucket(uint32_t n) {
+    return n < (uint32_t)kCountBuckets ? (int)n : kCountBuckets - 1;
+}
+
 struct SceneDev {
     const float *xyz, *rgb, *alpha;
     int K;

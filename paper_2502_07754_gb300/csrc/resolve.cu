@@ -11,6 +11,10 @@
 // fragments at or before the last committed one.  Order: (depth, triangle id).
 // Compositing stops once the transmittance falls below T_eps.
 //
+// Both passes visit the pixels in orders that pixel_order_kernel builds after the pixel
+// scan (by fragment count), so a warp's lanes run loops of about the same length instead
+// of all waiting for the deepest pixel among 32 neighbours.
+//
 // The forward also records, per pixel, the record index of each committed fragment in
 // commit order.  The backward walks that list (no pending buffer, no re-reads), and at
 // each committed fragment f forms, from the recomputed transmittance T_f,
@@ -41,8 +45,77 @@ struct ResolveArgs {
     uint32_t *ncommit;
     float4 *fgrad;             // backward: per record (dL/dc * T a, dL/da)
     uint32_t *corder;          // per pixel: record indices in commit order (same offsets as records)
+    const uint32_t *perm;      // visiting order of the pixels
     ViewTable vt;
 };
+
+// Resolve orders, built after the pixel scan.  Forward: all pixels in descending order of
+// their fragment counts (a counting sort over the histogram the tile prefix gathered), so
+// the 32 lanes of a warp walk lists of about the same length and the deepest pixels
+// start first instead of trailing at the end of the grid.  Backward: the same sort within
+// spans of kOrderSpan consecutive pixels only: that pass does little arithmetic per
+// record and is bound by memory latency, and pixels of one span have their records in
+// one small region of the buffer.  The order within one count varies from run to run;
+// no pixel's result depends on it.
+constexpr int kOrderThreads = 256, kOrderItems = 4, kOrderSpan = kOrderThreads * kOrderItems;
+
+// Exclusive prefix of v over the buckets in descending order (thread t holds bucket 255 - t).
+__device__ __forceinline__ uint32_t desc_prefix(uint32_t v, uint32_t *s_warp) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    __syncthreads();   // s_warp may still be read by an earlier call
+    if (lane == 31) s_warp[warp] = x;
+    __syncthreads();
+    uint32_t before = 0;
+    for (int w = 0; w < warp; ++w) before += s_warp[w];
+    return before + x - v;
+}
+
+__global__ void __launch_bounds__(kOrderThreads) pixel_order_kernel(const uint32_t *__restrict__ counts, int64_t npx,
+                                                                    const uint32_t *__restrict__ hist,
+                                                                    uint32_t *__restrict__ fill,
+                                                                    uint32_t *__restrict__ perm_fwd,
+                                                                    uint32_t *__restrict__ perm_bwd) {
+    __shared__ uint32_t s_cnt[kCountBuckets], s_span[kCountBuckets], s_glob[kCountBuckets], s_warp[kOrderThreads / 32];
+    static_assert(kOrderThreads == kCountBuckets, "one thread per bucket");
+    const int tid = threadIdx.x;
+    const int64_t base = (int64_t)blockIdx.x * kOrderSpan;
+    const int mb = kCountBuckets - 1 - tid;   // this thread's bucket in the scans
+    s_cnt[tid] = 0;
+    const uint32_t g0 = desc_prefix(hist[mb], s_warp);   // (its barriers also order the clear)
+    int bk[kOrderItems];
+    uint32_t rk[kOrderItems];
+#pragma unroll
+    for (int i = 0; i < kOrderItems; ++i) {
+        const int64_t p = base + i * kOrderThreads + tid;
+        bk[i] = -1;
+        rk[i] = 0;
+        if (p < npx) {
+            bk[i] = count_bucket(counts[p]);
+            rk[i] = atomicAdd(&s_cnt[bk[i]], 1u);
+        }
+    }
+    __syncthreads();
+    const uint32_t h = s_cnt[mb];
+    s_span[mb] = desc_prefix(h, s_warp);
+    s_glob[mb] = h ? g0 + atomicAdd(&fill[mb], h) : 0u;
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < kOrderItems; ++i)
+        if (bk[i] >= 0) {
+            const uint32_t p = (uint32_t)(base + i * kOrderThreads + tid);
+            // both positions are < npx: the span and the histogram count each pixel once
+            const int64_t ps = base + s_span[bk[i]] + rk[i];
+            const int64_t pg = (int64_t)s_glob[bk[i]] + rk[i];
+            if (ps < npx) perm_bwd[ps] = p;
+            if (pg < npx) perm_fwd[pg] = p;
+        }
+}
 
 __device__ __forceinline__ bool frag_less(float za, uint32_t ta, float zb, uint32_t tb) {
     return za < zb || (za == zb && ta < tb);
@@ -50,9 +123,10 @@ __device__ __forceinline__ bool frag_less(float za, uint32_t ta, float zb, uint3
 
 template <int KB>
 __global__ void __launch_bounds__(kResolveThreads) resolve_kernel(const __grid_constant__ ResolveArgs a) {
-    const int64_t pix0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool valid = pix0 < a.npx;
-    const int64_t pix = valid ? pix0 : 0;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t pt = t < a.npx ? (int64_t)a.perm[t] : a.npx;
+    const bool valid = pt < a.npx;
+    const int64_t pix = valid ? pt : 0;
     const ViewDev &vw = a.vt.v[view_of_pixel(a.vt, (unsigned long long)pix)];
     const int64_t lpix = pix - (int64_t)vw.pix_base;   // index within the view's image
     int n = valid ? (int)a.counts[pix] : 0;
@@ -172,13 +246,21 @@ __global__ void __launch_bounds__(kResolveThreads) resolve_kernel(const __grid_c
 
 // Backward: replay the forward's committed fragments in their recorded order.
 __global__ void __launch_bounds__(kResolveThreads) resolve_bwd_kernel(const __grid_constant__ ResolveArgs a) {
-    const int64_t pix = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= a.npx) return;
+    const int64_t pix = a.perm[t];
     if (pix >= a.npx) return;
     const ViewDev &vw = a.vt.v[view_of_pixel(a.vt, (unsigned long long)pix)];
     const int64_t lpix = pix - (int64_t)vw.pix_base;
     const uint32_t n = a.ncommit[pix];
-    if (n == 0) return;
     const int64_t off = a.offsets[pix];
+    const uint32_t nrec = a.counts[pix];
+    if (n < nrec && off + nrec <= a.frag_cap) {
+        // records that were never composited get a zero upstream gradient (the gather
+        // pass reads every record of the pixel)
+        for (uint32_t i = 0; i < nrec; ++i) a.fgrad[off + i] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    }
+    if (n == 0) return;
     const float4 *rec = a.frags + (size_t)kRecFwd * off;
     const uint32_t *ord = a.corder + off;
     const float4 g = reinterpret_cast<const float4 *>(vw.dL)[lpix];
@@ -250,8 +332,22 @@ cudaError_t launch_resolve(const RenderArgs &ra, bool backward, cudaStream_t st)
     a.ncommit = reinterpret_cast<uint32_t *>(ra.ws + L.off_ncommit);
     a.fgrad = reinterpret_cast<float4 *>(ra.ws + L.off_fgrad);
     a.corder = reinterpret_cast<uint32_t *>(ra.ws + L.off_corder);
+    a.perm = reinterpret_cast<const uint32_t *>(ra.ws + L.off_perm) + (backward ? L.npx : 0);
     a.vt = ra.vt;
     return launch_k(a, backward, L.kbuf, L.npx, st);
+}
+
+cudaError_t launch_pixel_order(const RenderArgs &ra, cudaStream_t st) {
+    const RenderLayout &L = ra.L;
+    if (L.npx == 0) return cudaSuccess;
+    const uint32_t *hist = reinterpret_cast<const uint32_t *>(ra.ws + L.off_pbucket);
+    uint32_t *fill = reinterpret_cast<uint32_t *>(ra.ws + L.off_pbucket) + kCountBuckets;
+    uint32_t *perm = reinterpret_cast<uint32_t *>(ra.ws + L.off_perm);
+    pixel_order_kernel<<<(unsigned)((L.npx + kOrderSpan - 1) / kOrderSpan), kOrderThreads, 0, st>>>(
+        reinterpret_cast<const uint32_t *>(ra.ws + L.off_counts), L.npx, hist, fill, perm, perm + L.npx);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) count_launches(1);
+    return e;
 }
 
 cudaError_t launch_grad_scatter(const RenderArgs &ra, cudaStream_t st) {
