@@ -146,7 +146,7 @@ RenderLayout render_layout(int64_t n_fans, int K, const ms_camera *cams, int n_v
     L.off_offsets = o;           o = align_up(o + 4 * (size_t)npx, 256);
     L.off_perm = o;              o = align_up(o + 8 * (size_t)npx, 256);   // forward, backward pixel orders
     L.off_frags = o;             o = align_up(o + 16 * kRecFwd * (size_t)fcap, 256);
-    L.off_fgrad = o;             o = align_up(o + 16 * (size_t)fcap, 256);
+    L.off_adj = o;               o = align_up(o + 32 * (size_t)fcap, 256);   // adjoint records
     L.off_corder = o;            o = align_up(o + 4 * (size_t)fcap, 256);
     L.off_tfinal = o;            o = align_up(o + 4 * (size_t)npx, 256);
     L.off_ncommit = o;           o = align_up(o + 4 * (size_t)npx, 256);
@@ -186,6 +186,7 @@ static ms_status check_render_args(const float *xyz, const float *rgb, const flo
     if (L.key_bits > 64) return fail(MS_ERR_INVALID, "sort key needs %d bits", L.key_bits);
     if (L.cap >= (1ll << 30)) return fail(MS_ERR_INVALID, "pair capacity %lld >= 2^30", (long long)L.cap);
     if (L.frag_cap >= (1ll << 32)) return fail(MS_ERR_INVALID, "fragment capacity %lld >= 2^32", (long long)L.frag_cap);
+    if (L.npx >= (1ll << 32)) return fail(MS_ERR_INVALID, "%lld pixels over all views >= 2^32", (long long)L.npx);
     if (!ws) return fail(MS_ERR_INVALID, "workspace is NULL");
     if (reinterpret_cast<uintptr_t>(ws) & 255) return fail(MS_ERR_INVALID, "workspace not 256-byte aligned");
     if (ws_bytes < L.total) return fail(MS_ERR_INVALID, "workspace %zu bytes < %zu needed", ws_bytes, L.total);
@@ -279,13 +280,14 @@ static ms_status render_views_backward(const float *xyz, const float *rgb, const
     a.d_xyz = d_xyz; a.d_rgb = d_rgb; a.d_alpha = d_alpha;
     a.key_scale = 1.0f;
     a.vt = make_views(cams, n_views, L, nullptr, out_fwd, dL);
-    // the forward's fragment records are replayed in the same order, recomputing
-    // transmittance; the per-record upstream gradients are then gathered fan by fan
+    // the forward's composited fragments are replayed in commit order, recomputing
+    // transmittance; the per-record upstream gradients are then chained to the vertices
+    // record by record
     if ((e = launch_resolve(a, true, st)) != cudaSuccess) return cuda_fail(e, "resolve backward launch");
-    if ((e = launch_raster_grad(a, st)) != cudaSuccess) return cuda_fail(e, "raster gather launch");
+    if ((e = launch_record_chain(a, st)) != cudaSuccess) return cuda_fail(e, "record chain launch");
     if (!keep_in_ws && (e = launch_grad_scatter(a, st)) != cudaSuccess)
         return cuda_fail(e, "gradient scatter launch");
-    count_launches(1 + (L.V > 0 && !keep_in_ws ? 1 : 0));   // resolve, scatter (the gather counts itself)
+    count_launches(1 + (L.V > 0 && !keep_in_ws ? 1 : 0));   // resolve, scatter (the chain counts itself)
     return MS_OK;
 }
 

@@ -35,7 +35,7 @@ struct RenderLayout {
     int64_t bin_fan_blocks, bin_blocks, sort_blocks, scan_blocks, tscan_blocks, max_items;
     size_t off_status, off_bin_state, off_keys0, off_keys1, off_vals0, off_vals1, off_hist, off_lookback,
         off_ranges, off_scan_state, off_tscan_state, off_pbucket, off_perm, off_tile_nitems, off_tile_ibase, off_items, off_icnt,
-        off_counts, off_offsets, off_frags, off_fgrad, off_corder, off_tfinal, off_ncommit, off_grad, off_dec, total;
+        off_counts, off_offsets, off_frags, off_adj, off_corder, off_tfinal, off_ncommit, off_grad, off_dec, total;
 };
 
 RenderLayout render_layout(int64_t n_fans, int K, const ms_camera *cams, int n_views, const ms_render_params &p);
@@ -91,7 +91,7 @@ constexpr int kItemFans = 64;   // fans per raster work item
 
 cudaError_t launch_raster(const RenderArgs &a, bool fill, cudaStream_t st);
 cudaError_t launch_raster_count(const RenderArgs &a, cudaStream_t st);   // items, count, prefix, pixel scan
-cudaError_t launch_raster_grad(const RenderArgs &a, cudaStream_t st);   // adjoint gather to the vertices
+cudaError_t launch_record_chain(const RenderArgs &a, cudaStream_t st);   // adjoint: records -> fan vertices
 constexpr int kRecFwd = 2;   // float4s per fragment record
 cudaError_t launch_pixel_order(const RenderArgs &a, cudaStream_t st);   // resolve order of the pixels
 cudaError_t launch_resolve(const RenderArgs &a, bool backward, cudaStream_t st);

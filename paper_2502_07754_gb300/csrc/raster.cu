@@ -12,8 +12,8 @@
 // items turns them into each item's starting slot within the pixel and gives the
 // pixel totals; an exclusive scan over pixels gives record offsets.  Fill pass: the
 // same walk writes one 32-byte record per fragment at offset + item slot + running
-// index -- depth, triangle id, the fan's depth bound, opacity, colour -- so a pixel's
-// records come out in tile-list order, which the resolve relies on.
+// index -- depth, triangle id, the fan's depth bound, opacity, colour, pixel -- so a
+// pixel's records come out in tile-list order, which the resolve relies on.
 #include "raster_common.cuh"
 
 namespace ms {
@@ -34,23 +34,18 @@ struct RastArgs {
     int64_t frag_cap;
     Status *st;
     SplatSrc spl;              // source Gaussians (splat passes only)
-    const float4 *fgrad;       // kGrad: per record (dL/dc * T a, dL/da)
     const float4 *dec;         // [view][vertex] decided vertices from binning
     int64_t V;
-    float4 *grad;              // kGrad: per vertex (xyz, alpha | rgb, 0) sums
 };
 
 constexpr int kRastWarps = 2;   // warps (work items) per block: items differ widely in cost
 
-// Pass kinds: count fragments; fill their 32-byte forward records; gather the adjoint
-// (each fragment's record slot is found exactly as the fill found it; the per-record
-// upstream gradients that the backward resolve wrote are chained to the fan's vertices
-// and summed per fan in shared memory, then added to the gradient scratch once per
-// (fan, work item)).  The splat passes draw the source Gaussians themselves (count, then
-// 32-byte records) over the tile lists of their circumscribing polygons.
-enum RasterMode { kCount = 0, kFill = 1, kGrad = 2, kSplatCount = 3, kSplatFill = 4 };
+// Pass kinds: count fragments; fill their 32-byte forward records.  The splat passes draw
+// the source Gaussians themselves (count, then 32-byte records) over the tile lists of
+// their circumscribing polygons.
+enum RasterMode { kCount = 0, kFill = 1, kSplatCount = 3, kSplatFill = 4 };
 
-__host__ __device__ constexpr bool mode_fills(int m) { return m == kFill || m == kGrad || m == kSplatFill; }
+__host__ __device__ constexpr bool mode_fills(int m) { return m == kFill || m == kSplatFill; }
 __host__ __device__ constexpr bool mode_splat(int m) { return m >= kSplatCount; }
 __host__ __device__ constexpr int mode_level(int m) { return mode_splat(m) ? (int)kStageDecide : m; }
 
@@ -199,6 +194,7 @@ __global__ void __launch_bounds__(kRastWarps * 32) raster_kernel(const __grid_co
                 const uint32_t b = s_base[lp];
                 if (b != 0xffffffffu) {
                     const float pxc = (float)px + 0.5f, pyc = (float)py + 0.5f;
+                    const uint32_t pix = (uint32_t)(pix_base + (unsigned long long)py * (unsigned)sc.W + (unsigned)px);
                     for (uint32_t hm = hits; hm; hm &= hm - 1, ++slot) {
                         const int j = __ffs(hm) - 1;
                         const int jn = (j + 1 == K) ? 0 : j + 1;
@@ -229,87 +225,8 @@ __global__ void __launch_bounds__(kRastWarps * 32) raster_kernel(const __grid_co
                         const uint32_t tri = S.fan[f] * (uint32_t)K + (uint32_t)j;
                         float4 *rec = a.frags + (size_t)kRecFwd * ((size_t)b + slot);
                         rec[0] = make_float4(zf, __uint_as_float(tri), __uint_as_float(S.q[f]), al);
-                        rec[1] = make_float4(c0, c1, c2, 0.0f);
+                        rec[1] = make_float4(c0, c1, c2, __uint_as_float(pix));
                     }
-                }
-            }
-            if (MODE == kGrad) {
-                uint32_t hm = 0;
-                uint32_t base_rec = 0;
-                if (nf) {
-                    base_rec = s_base[lp];
-                    if (base_rec != 0xffffffffu) hm = hits;
-                }
-                const int rounds = __reduce_max_sync(0xffffffffu, (unsigned)__popc(hm));
-                const float pxc = (float)px + 0.5f, pyc = (float)py + 0.5f;
-                uint32_t sl = slot;
-                for (int h = 0; h < rounds; ++h) {
-                    bool have = false;
-                    if (hm) {
-                        const int j = __ffs(hm) - 1;
-                        // upstream gradients of this fragment (zero if it was not composited)
-                        const float4 gr = a.fgrad[(size_t)base_rec + sl];
-                        have = gr.x != 0.0f || gr.y != 0.0f || gr.z != 0.0f || gr.w != 0.0f;
-                        if (have) {
-                            const int jn = (j + 1 == K) ? 0 : j + 1;
-                            const int vc = f, vj = (1 + j) * STG + f, vn = (1 + jn) * STG + f;
-                            const float izc = S.viz[f];
-                            const float izj = S.viz[vj], izn = S.viz[vn];
-                            const float ox = __fsub_rn(S.cxh[f], pxc) + S.cxl[f];
-                            const float oy = __fsub_rn(S.cyh[f], pyc) + S.cyl[f];
-                            const float ujx = ox + S.du[j * STG + f], ujy = oy + S.dv[j * STG + f];
-                            const float unx = ox + S.du[jn * STG + f], uny = oy + S.dv[jn * STG + f];
-                            const float w0 = (ujx * uny - ujy * unx) * izc;
-                            const float w1 = (unx * oy - uny * ox) * izj;
-                            const float w2 = (ox * ujy - oy * ujx) * izn;
-                            const float iW = 1.0f / (w0 + w1 + w2);
-                            const float mu[3] = {w0 * iW, w1 * iW, w2 * iW};
-                            const float ux[3] = {ox, ujx, unx}, uy[3] = {oy, ujy, uny};
-                            const float iz[3] = {1.0f / S.vZ[vc], 1.0f / S.vZ[vj], 1.0f / S.vZ[vn]};
-                            const int vv[3] = {vc, vj, vn};
-                            // dL/dmu_k, then through mu_k = w_k / W, w_k = E_k / Z_k with E_k the cross
-                            // product of the other two offsets, to screen offsets and Z
-                            float gmu[3], sdot = 0.0f;
-#pragma unroll
-                            for (int k = 0; k < 3; ++k) {
-                                gmu[k] = gr.x * S.cr[vv[k]] + gr.y * S.cg[vv[k]] + gr.z * S.cb[vv[k]] +
-                                         gr.w * S.ca[vv[k]];
-                                sdot += mu[k] * gmu[k];
-                            }
-                            float gux[3] = {0.0f, 0.0f, 0.0f}, guy[3] = {0.0f, 0.0f, 0.0f}, gZ[3];
-#pragma unroll
-                            for (int k = 0; k < 3; ++k) {
-                                const int ia = (k + 1) % 3, ib = (k + 2) % 3;
-                                const float E = ux[ia] * uy[ib] - uy[ia] * ux[ib];
-                                const float gw = (gmu[k] - sdot) * iW;
-                                const float gE = gw * iz[k];
-                                gZ[k] = -gw * E * iz[k] * iz[k];
-                                gux[ia] += gE * uy[ib];
-                                guy[ia] -= gE * ux[ib];
-                                guy[ib] += gE * ux[ia];
-                                gux[ib] -= gE * uy[ia];
-                            }
-                            const CamDev &c = *sc.cam;
-                            const size_t v0 = (size_t)S.fan[f] * (K + 1);
-                            const size_t vid[3] = {v0, v0 + 1 + j, v0 + 1 + jn};
-#pragma unroll
-                            for (int k = 0; k < 3; ++k) {
-                                const float gX = gux[k] * c.fx * iz[k];
-                                const float gY = guy[k] * c.fy * iz[k];
-                                const float gZv =
-                                    gZ[k] - (gux[k] * c.fx * S.vX[vv[k]] + guy[k] * c.fy * S.vY[vv[k]]) * iz[k] * iz[k];
-                                atomicAdd(a.grad + 2 * vid[k],
-                                          make_float4(c.R[0] * gX + c.R[3] * gY + c.R[6] * gZv,
-                                                      c.R[1] * gX + c.R[4] * gY + c.R[7] * gZv,
-                                                      c.R[2] * gX + c.R[5] * gY + c.R[8] * gZv, mu[k] * gr.w));
-                                atomicAdd(a.grad + 2 * vid[k] + 1,
-                                          make_float4(mu[k] * gr.x, mu[k] * gr.y, mu[k] * gr.z, 0.0f));
-                            }
-                        }
-                        hm &= hm - 1;
-                        ++sl;
-                    }
-                    __syncwarp();
                 }
             }
             __syncwarp();   // the next batch may append to the same pixels
@@ -532,10 +449,8 @@ RastArgs make_args(const RenderArgs &ra) {
     a.frag_cap = L.frag_cap;
     a.st = reinterpret_cast<Status *>(ra.ws + L.off_status);
     a.spl = ra.spl;
-    a.fgrad = reinterpret_cast<const float4 *>(ra.ws + L.off_fgrad);
     a.dec = reinterpret_cast<const float4 *>(ra.ws + L.off_dec);
     a.V = L.V;
-    a.grad = reinterpret_cast<float4 *>(ra.ws + L.off_grad);
     return a;
 }
 
@@ -591,13 +506,5 @@ cudaError_t launch_raster(const RenderArgs &ra, bool fill, cudaStream_t st) {
     return e;
 }
 
-cudaError_t launch_raster_grad(const RenderArgs &ra, cudaStream_t st) {
-    const RenderLayout &L = ra.L;
-    if (L.n_tiles == 0) return cudaSuccess;
-    const RastArgs a = make_args(ra);
-    cudaError_t e = launch_dispatch<kGrad>(a, L, ra.K, st);
-    if (e == cudaSuccess) count_launches(1);
-    return e;
-}
 
 }  // namespace ms

@@ -109,18 +109,15 @@ struct Stage {
     float *cxh, *cxl, *cyh, *cyl; // [CH] double-float screen position of the centre (values)
     float *du, *dv;               // [K][CH] screen offsets of the boundary vertices (values)
     float *cr, *cg, *cb, *ca;     // [KV][CH] vertex colour and opacity (values)
-    float *vX, *vY, *vZ;          // [KV][CH] view-space vertices (adjoint records)
 };
 
-// What a stage holds: decisions only, + values (fill), + view coordinates (fill of the
-// adjoint's records).
-enum StageLevel { kStageDecide = 0, kStageValues = 1, kStageGrad = 2 };
+// What a stage holds: decisions only (count), or decisions and values (fill).
+enum StageLevel { kStageDecide = 0, kStageValues = 1 };
 
 __host__ __device__ __forceinline__ size_t stage_bytes(int CH, int K, int level) {
     const int dec = 4 * (K + 1) + 5 * K;
     const int val = level >= kStageValues ? 4 + 2 * K + 4 * (K + 1) : 0;
-    const int grd = level >= kStageGrad ? 3 * (K + 1) : 0;
-    return (size_t)CH * (16 + 20 + 4 * (dec + val + grd));
+    return (size_t)CH * (16 + 20 + 4 * (dec + val));
 }
 
 __device__ __forceinline__ Stage stage_ptrs(char *base, int CH, int K, int level) {
@@ -152,12 +149,7 @@ __device__ __forceinline__ Stage stage_ptrs(char *base, int CH, int K, int level
         s.cr = f; f += KV * CH;
         s.cg = f; f += KV * CH;
         s.cb = f; f += KV * CH;
-        s.ca = f; f += KV * CH;
-    }
-    if (level >= kStageGrad) {
-        s.vX = f; f += KV * CH;
-        s.vY = f; f += KV * CH;
-        s.vZ = f;
+        s.ca = f;
     }
     return s;
 }
@@ -232,16 +224,6 @@ __device__ __forceinline__ void stage_fan(const SceneDev &a, const Stage &s, int
         vertex_offset(*a.cam, cp, d, du, dv, X, Y, Z);
         s.du[i * CH + slot] = du;
         s.dv[i * CH + slot] = dv;
-        if (level >= kStageGrad) {
-            s.vX[(1 + i) * CH + slot] = X;
-            s.vY[(1 + i) * CH + slot] = Y;
-            s.vZ[(1 + i) * CH + slot] = Z;
-        }
-    }
-    if (level >= kStageGrad) {
-        s.vX[slot] = cp.Xh;
-        s.vY[slot] = cp.Yh;
-        s.vZ[slot] = cp.Zh;
     }
     const float *col = a.rgb + (size_t)fan * KV * 3;
     const float *al = a.alpha + (size_t)fan * KV;

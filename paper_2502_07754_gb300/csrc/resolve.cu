@@ -19,9 +19,10 @@
 // commit order.  The backward walks that list (no pending buffer, no re-reads), and at
 // each committed fragment f forms, from the recomputed transmittance T_f,
 // dC/dc_f = T_f a_f, dC/da_f = T_f c_f - (C_out - C_{<=f}) / (1 - a_f) and
-// dA/da_f = T_out / (1 - a_f).  It writes dL/dc_f and dL/da_f to the record's gradient
-// slot; the rasteriser's gather pass chains them to the vertices fan by fan
-// (raster.cu), so this pass does no atomics.
+// dA/da_f = T_out / (1 - a_f).  It writes dL/dc_f and dL/da_f, with the fragment's
+// triangle and pixel, as an adjoint record (the pixel's c-th composited fragment in slot
+// c of its record range); the chain pass (chain.cu) takes them to the vertices record by
+// record, so this pass does no atomics.
 #include "raster_common.cuh"
 
 namespace ms {
@@ -43,7 +44,8 @@ struct ResolveArgs {
     Status *st;
     float *tfinal;
     uint32_t *ncommit;
-    float4 *fgrad;             // backward: per record (dL/dc * T a, dL/da)
+    float4 *adj;               // backward: per composited fragment, in commit order within the
+                               // pixel's record range: (dL/dc * T a, dL/da), (triangle, pixel, 0, 0)
     uint32_t *corder;          // per pixel: record indices in commit order (same offsets as records)
     const uint32_t *perm;      // visiting order of the pixels
     ViewTable vt;
@@ -256,9 +258,12 @@ __global__ void __launch_bounds__(kResolveThreads) resolve_bwd_kernel(const __gr
     const int64_t off = a.offsets[pix];
     const uint32_t nrec = a.counts[pix];
     if (n < nrec && off + nrec <= a.frag_cap) {
-        // records that were never composited get a zero upstream gradient (the gather
-        // pass reads every record of the pixel)
-        for (uint32_t i = 0; i < nrec; ++i) a.fgrad[off + i] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        // slots past the composited fragments carry a zero gradient (the chain pass reads
+        // every slot of the pixel's range)
+        for (uint32_t i = n; i < nrec; ++i) {
+            a.adj[2 * (off + i)] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            a.adj[2 * (off + i) + 1] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        }
     }
     if (n == 0) return;
     const float4 *rec = a.frags + (size_t)kRecFwd * off;
@@ -271,14 +276,16 @@ __global__ void __launch_bounds__(kResolveThreads) resolve_bwd_kernel(const __gr
     for (uint32_t c = 0; c < n; ++c) {
         const uint32_t nidx = c + 1 < n ? ord[c + 1] : 0u;   // the next index loads early
         const float4 *rc = rec + (size_t)kRecFwd * idx;
-        const float al = rc[0].w;
+        const float4 r0 = rc[0];
+        const float al = r0.w;
         const float4 col = rc[1];
         const float w = T * al;
         const float nC0 = C0 + w * col.x, nC1 = C1 + w * col.y, nC2 = C2 + w * col.z;
         const float inv = 1.0f / fmaxf(1.0f - al, 1e-6f);
         const float ga = g.x * (T * col.x - (ov.x - nC0) * inv) + g.y * (T * col.y - (ov.y - nC1) * inv) +
                          g.z * (T * col.z - (ov.z - nC2) * inv) + g.w * Tout * inv;
-        a.fgrad[off + idx] = make_float4(g.x * w, g.y * w, g.z * w, ga);
+        a.adj[2 * (off + c)] = make_float4(g.x * w, g.y * w, g.z * w, ga);
+        a.adj[2 * (off + c) + 1] = make_float4(r0.y, __uint_as_float((uint32_t)pix), 0.0f, 0.0f);
         C0 = nC0; C1 = nC1; C2 = nC2;
         T *= (1.0f - al);
         idx = nidx;
@@ -330,7 +337,7 @@ cudaError_t launch_resolve(const RenderArgs &ra, bool backward, cudaStream_t st)
     a.st = reinterpret_cast<Status *>(ra.ws + L.off_status);
     a.tfinal = reinterpret_cast<float *>(ra.ws + L.off_tfinal);
     a.ncommit = reinterpret_cast<uint32_t *>(ra.ws + L.off_ncommit);
-    a.fgrad = reinterpret_cast<float4 *>(ra.ws + L.off_fgrad);
+    a.adj = reinterpret_cast<float4 *>(ra.ws + L.off_adj);
     a.corder = reinterpret_cast<uint32_t *>(ra.ws + L.off_corder);
     a.perm = reinterpret_cast<const uint32_t *>(ra.ws + L.off_perm) + (backward ? L.npx : 0);
     a.vt = ra.vt;
