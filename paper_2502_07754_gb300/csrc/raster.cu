@@ -3,8 +3,8 @@
 // Every tile's fan list (sorted by the fans' depth bounds) is cut into work items of
 // at most kItemFans fans; one warp rasterises one item, so a hot tile with thousands
 // of fans spreads over many warps instead of serialising on one.  A warp projects
-// the item's fans in parallel (one fan per lane) into its own shared-memory stage,
-// then walks them in list order: for each fan its lanes enumerate exactly the pixels
+// a chunk of the item's fans into its own shared-memory stage (32 / chunk lanes per fan,
+// sharing its vertices and triangles), then walks them in list order: for each fan its lanes enumerate exactly the pixels
 // of the fan's pixel rectangle inside the tile and test the fan's K triangles at each
 // with the binary32 decision formulas.  No block barriers are used.
 //
@@ -108,12 +108,17 @@ __global__ void __launch_bounds__(kRastWarps * 32) raster_kernel(const __grid_co
     __syncwarp();
     for (uint32_t cb = it.y; cb < it.z; cb += STG) {
         const int cnt = (int)min((uint32_t)STG, it.z - cb);
-        if (lane < cnt) {
-            const uint32_t li = cb + lane;
-            const uint32_t q = (uint32_t)(__ldg(a.keys + li) & ((1ull << a.depth_bits) - 1ull));
-            const uint32_t fan = __ldg(a.vals + li);
-            stage_fan(sc, S, STG, K, lane, fan, q, LEVEL);
-            if (SPLAT) s_spl[lane] = splat_setup(a.spl, *sc.cam, fan);
+        {
+            constexpr int LPF = 32 / STG;   // lanes staging one fan
+            const int slot = lane / LPF;
+            uint32_t q = 0, fan = 0;
+            if (slot < cnt) {
+                const uint32_t li = cb + slot;
+                q = (uint32_t)(__ldg(a.keys + li) & ((1ull << a.depth_bits) - 1ull));
+                fan = __ldg(a.vals + li);
+            }
+            stage_fans<LPF>(sc, S, K, lane, slot < cnt, fan, q, LEVEL);
+            if (SPLAT && lane < cnt) s_spl[lane] = splat_setup(a.spl, *sc.cam, __ldg(a.vals + cb + lane));
         }
         __syncwarp();
         // The staged fans' rectangles (clipped to the tile) form one packed (fan, pixel)

@@ -154,70 +154,115 @@ __device__ __forceinline__ Stage stage_ptrs(char *base, int CH, int K, int level
     return s;
 }
 
-__device__ __forceinline__ void stage_fan(const SceneDev &a, const Stage &s, int CH, int K, int slot, uint32_t fan,
-                                          uint32_t q, int level) {
+// OR / min / max over the LPF lanes of a fan's group (lanes lane & ~(LPF-1) .. + LPF-1).
+template <int LPF>
+__device__ __forceinline__ uint32_t group_or(uint32_t x) {
+#pragma unroll
+    for (int o = LPF / 2; o > 0; o >>= 1) x |= __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+template <int LPF>
+__device__ __forceinline__ float group_min(float x) {
+#pragma unroll
+    for (int o = LPF / 2; o > 0; o >>= 1) x = fminf(x, __shfl_xor_sync(0xffffffffu, x, o));
+    return x;
+}
+template <int LPF>
+__device__ __forceinline__ float group_max(float x) {
+#pragma unroll
+    for (int o = LPF / 2; o > 0; o >>= 1) x = fmaxf(x, __shfl_xor_sync(0xffffffffu, x, o));
+    return x;
+}
+
+// Stages CH = 32 / LPF fans into slots 0..CH-1 with the whole warp: the LPF lanes of slot
+// lane / LPF share the fan's vertices, triangles and colours (every lane of the warp
+// calls this; a lane whose slot is not active does no loads or stores but takes part in
+// the shuffles).  The staged words are the same as one lane per fan would write.
+template <int LPF>
+__device__ __forceinline__ void stage_fans(const SceneDev &a, const Stage &s, int K, int lane, bool active,
+                                           uint32_t fan, uint32_t q, int level) {
+    constexpr int CH = 32 / LPF;
     const int KV = K + 1;
+    const int slot = lane / LPF, sub = lane % LPF;
     const float *p = a.xyz + (size_t)fan * KV * 3;
     const float4 *dv = a.dec + (size_t)fan * KV;
     uint32_t vmask = 0;
-    for (int k = 0; k < KV; ++k) {
-        const float4 d = __ldg(dv + k);   // the binning pass's decide_vertex, bit for bit
-        s.vx[k * CH + slot] = d.x;
-        s.vy[k * CH + slot] = d.y;
-        s.vz[k * CH + slot] = d.z;
-        s.viz[k * CH + slot] = d.w;
-        if (vertex_valid(*a.cam, d.x, d.y, d.z)) vmask |= 1u << k;
-    }
+    if (active)
+        for (int k = sub; k < KV; k += LPF) {
+            const float4 d = __ldg(dv + k);   // the binning pass's decide_vertex, bit for bit
+            s.vx[k * CH + slot] = d.x;
+            s.vy[k * CH + slot] = d.y;
+            s.vz[k * CH + slot] = d.z;
+            s.viz[k * CH + slot] = d.w;
+            if (vertex_valid(*a.cam, d.x, d.y, d.z)) vmask |= 1u << k;
+        }
+    vmask = group_or<LPF>(vmask);
+    __syncwarp();   // the group's vertex rows are complete
     const uint32_t tmask = tri_valid_mask(vmask, K);
     float mnx = 3.0e38f, mxx = -3.0e38f, mny = 3.0e38f, mxy = -3.0e38f;
-    for (int k = 0; k < KV; ++k) {
-        if (!vertex_used(tmask, k, K)) continue;
-        const float x = s.vx[k * CH + slot], y = s.vy[k * CH + slot];
-        mnx = fminf(mnx, x); mxx = fmaxf(mxx, x);
-        mny = fminf(mny, y); mxy = fmaxf(mxy, y);
-    }
-    const FanRect r = rect_from_bounds(mnx, mxx, mny, mxy, a.W, a.H);
-    const float xc = s.vx[slot], yc = s.vy[slot];
     uint32_t flags = 0, stie = 0, rtie = 0;
-    for (int j = 0; j < K; ++j) {
-        const int b = 1 + j, c = 1 + (j + 1 == K ? 0 : j + 1);
-        const float xb = s.vx[b * CH + slot], yb = s.vy[b * CH + slot];
-        const float xn = s.vx[c * CH + slot], yn = s.vy[c * CH + slot];
-        s.sdx[j * CH + slot] = __fsub_rn(xb, xc);
-        s.sdy[j * CH + slot] = __fsub_rn(yb, yc);
-        if (j + 1 == K) {   // rim (b_{K-1}, b_0): the lower index is b_0
-            s.rdx[j * CH + slot] = __fsub_rn(xb, xn);
-            s.rdy[j * CH + slot] = __fsub_rn(yb, yn);
-        } else {
-            s.rdx[j * CH + slot] = __fsub_rn(xn, xb);
-            s.rdy[j * CH + slot] = __fsub_rn(yn, yb);
+    if (active) {
+        for (int k = sub; k < KV; k += LPF) {
+            if (!vertex_used(tmask, k, K)) continue;
+            const float x = s.vx[k * CH + slot], y = s.vy[k * CH + slot];
+            mnx = fminf(mnx, x); mxx = fmaxf(mxx, x);
+            mny = fminf(mny, y); mxy = fmaxf(mxy, y);
         }
-        const float ar = dec_area2(xc, yc, xb, yb, xn, yn);
-        s.area[j * CH + slot] = fabsf(ar);
-        if (((tmask >> j) & 1u) && ar != 0.0f) flags |= 1u << j;
-        if (ar < 0.0f) flags |= 1u << (16 + j);
-        // tie acceptance (E == 0) of each direction and of its reverse
-        const float sx = s.sdx[j * CH + slot], sy = s.sdy[j * CH + slot];
-        const float rx = s.rdx[j * CH + slot], ry = s.rdy[j * CH + slot];
-        if (sy < 0.0f || (sy == 0.0f && sx > 0.0f)) stie |= 1u << j;
-        if (sy > 0.0f || (sy == 0.0f && sx < 0.0f)) stie |= 1u << (16 + j);
-        if (ry < 0.0f || (ry == 0.0f && rx > 0.0f)) rtie |= 1u << j;
-        if (ry > 0.0f || (ry == 0.0f && rx < 0.0f)) rtie |= 1u << (16 + j);
+        const float xc = s.vx[slot], yc = s.vy[slot];
+        for (int j = sub; j < K; j += LPF) {
+            const int b = 1 + j, c = 1 + (j + 1 == K ? 0 : j + 1);
+            const float xb = s.vx[b * CH + slot], yb = s.vy[b * CH + slot];
+            const float xn = s.vx[c * CH + slot], yn = s.vy[c * CH + slot];
+            const float sx = __fsub_rn(xb, xc), sy = __fsub_rn(yb, yc);
+            float rx, ry;
+            if (j + 1 == K) {   // rim (b_{K-1}, b_0): the lower index is b_0
+                rx = __fsub_rn(xb, xn);
+                ry = __fsub_rn(yb, yn);
+            } else {
+                rx = __fsub_rn(xn, xb);
+                ry = __fsub_rn(yn, yb);
+            }
+            s.sdx[j * CH + slot] = sx;
+            s.sdy[j * CH + slot] = sy;
+            s.rdx[j * CH + slot] = rx;
+            s.rdy[j * CH + slot] = ry;
+            const float ar = dec_area2(xc, yc, xb, yb, xn, yn);
+            s.area[j * CH + slot] = fabsf(ar);
+            if (((tmask >> j) & 1u) && ar != 0.0f) flags |= 1u << j;
+            if (ar < 0.0f) flags |= 1u << (16 + j);
+            // tie acceptance (E == 0) of each direction and of its reverse
+            if (sy < 0.0f || (sy == 0.0f && sx > 0.0f)) stie |= 1u << j;
+            if (sy > 0.0f || (sy == 0.0f && sx < 0.0f)) stie |= 1u << (16 + j);
+            if (ry < 0.0f || (ry == 0.0f && rx > 0.0f)) rtie |= 1u << j;
+            if (ry > 0.0f || (ry == 0.0f && rx < 0.0f)) rtie |= 1u << (16 + j);
+        }
     }
-    s.stie[slot] = stie;
-    s.rtie[slot] = rtie;
-    s.flags[slot] = (tmask == 0 || r.empty) ? 0u : flags;
-    s.q[slot] = q;
-    s.fan[slot] = fan;
-    s.rect[slot] = make_int4(r.i0, r.i1, r.j0, r.j1);
-    if (level < kStageValues) return;
+    mnx = group_min<LPF>(mnx);
+    mxx = group_max<LPF>(mxx);
+    mny = group_min<LPF>(mny);
+    mxy = group_max<LPF>(mxy);
+    flags = group_or<LPF>(flags);
+    stie = group_or<LPF>(stie);
+    rtie = group_or<LPF>(rtie);
+    if (active && sub == 0) {
+        const FanRect r = rect_from_bounds(mnx, mxx, mny, mxy, a.W, a.H);
+        s.stie[slot] = stie;
+        s.rtie[slot] = rtie;
+        s.flags[slot] = (tmask == 0 || r.empty) ? 0u : flags;
+        s.q[slot] = q;
+        s.fan[slot] = fan;
+        s.rect[slot] = make_int4(r.i0, r.i1, r.j0, r.j1);
+    }
+    if (level < kStageValues || !active) return;
     const float m[3] = {__ldg(p), __ldg(p + 1), __ldg(p + 2)};
     const CentreProj cp = project_centre(*a.cam, m);
-    s.cxh[slot] = cp.xh;
-    s.cxl[slot] = cp.xl;
-    s.cyh[slot] = cp.yh;
-    s.cyl[slot] = cp.yl;
-    for (int i = 0; i < K; ++i) {
+    if (sub == 0) {
+        s.cxh[slot] = cp.xh;
+        s.cxl[slot] = cp.xl;
+        s.cyh[slot] = cp.yh;
+        s.cyl[slot] = cp.yl;
+    }
+    for (int i = sub; i < K; i += LPF) {
         const float d[3] = {__ldg(p + 3 * (1 + i)) - m[0], __ldg(p + 3 * (1 + i) + 1) - m[1],
                             __ldg(p + 3 * (1 + i) + 2) - m[2]};
         float du, dv, X, Y, Z;
@@ -227,7 +272,7 @@ __device__ __forceinline__ void stage_fan(const SceneDev &a, const Stage &s, int
     }
     const float *col = a.rgb + (size_t)fan * KV * 3;
     const float *al = a.alpha + (size_t)fan * KV;
-    for (int k = 0; k < KV; ++k) {
+    for (int k = sub; k < KV; k += LPF) {
         s.cr[k * CH + slot] = __ldg(col + 3 * k);
         s.cg[k * CH + slot] = __ldg(col + 3 * k + 1);
         s.cb[k * CH + slot] = __ldg(col + 3 * k + 2);
