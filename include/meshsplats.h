@@ -164,6 +164,8 @@ MS_API size_t ms_render_workspace_size(int64_t n_fans, int32_t K, const ms_camer
  *   out_rgba: device H x W x 4.
  *   workspace: device, >= ms_render_workspace_size bytes, 256-byte aligned; it keeps
  *   the sorted tile lists and per-pixel transmittance that ms_render_backward reuses.
+ * MS_ERR_INVALID for bad sizes or pointers, including 2^32 or more pixels over all views
+ * of a call (pixel indices are 32-bit in the fragment records).
  * Returns once the work is queued; call ms_render_get_info for device-side errors.
  */
 MS_API ms_status ms_render(const float *xyz, const float *rgb, const float *alpha, int64_t n_fans, int32_t K,
