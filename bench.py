@@ -40,9 +40,10 @@ NSTAGE = len(STAGES)
 # ncu DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of a stage's
 # kernels on the 1M-fan 1080p workload, with the digest of the kernel sources it was taken
 # on; reported only while the digest still matches.  Taken on the 200k-Gaussian case of
-# the same generator (10.86M fragments) and scaled by fragments to 10.12M (the stage's
-# traffic is per fragment: records written and re-read).
-TRAFFIC = {"raster": {"bytes": 970e6, "digest": "2d631735de3c35b0"}}
+# the same generator (10.86M fragments: count 34 MB, tile prefix 9, pixel scan 8, pixel
+# order 8, fill 545, resolve 984) and scaled by fragments to 10.12M (the stage's traffic is
+# per fragment: records written and re-read).
+TRAFFIC = {"raster": {"bytes": 1.48e9, "digest": "1b710aacb3a4ab02"}}
 
 
 def kernel_digest():

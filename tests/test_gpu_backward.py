@@ -236,3 +236,45 @@ def test_gradients_left_in_workspace_drive_adam_like_explicit_arrays():
         assert torch.allclose(p_ref, p_ws, rtol=3e-7, atol=1e-9), (p_ref - p_ws).abs().max().item()   # <= 2 ulp
     moved = (params[1][0] != xyz0).float().mean().item()
     assert moved > 0.01   # the step did something
+
+
+def test_backward_after_fragment_overflow_stays_in_bounds():
+    """A forward whose fragment buffer is too small reports MS_ERR_CAPACITY; the backward
+    on that workspace (whose record ranges beyond the capacity and adjoint slots hold
+    whatever the memory held before) must still finish without a CUDA error."""
+    import ctypes as C
+    import paper_2502_07754_gb300 as ms
+    from paper_2502_07754_gb300 import _lib
+    L = _lib.lib()
+    w = synthetic.workload(1)
+    cam = w.cameras[0]
+    xyz, rgb, a = oracle_mesh_f32(w.scene, 8, cam.C)
+    X, Cc, A = dev(xyz), dev(rgb), dev(a)
+    full = ms.Renderer(w.scene.n, 8, cam)
+    full.forward(X, Cc, A)
+    frags = full.last_info.frags
+    cs = ms.camera_struct(cam)
+    p = ms.render_params()
+    p.frag_capacity = max(1, frags // 2)
+    nbytes = L.ms_render_workspace_size(w.scene.n, 8, C.byref(cs), C.byref(p))
+    g = torch.Generator(device="cuda").manual_seed(9)
+    ws = torch.randint(0, 256, (nbytes + 256,), dtype=torch.uint8, device="cuda", generator=g)
+    base = (256 - ws.data_ptr() % 256) % 256
+    wsp = C.c_void_p(ws.data_ptr() + base)
+    out = torch.zeros(cam.height, cam.width, 4, device="cuda")
+    stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    ptr = lambda t: C.c_void_p(t.data_ptr())
+    assert L.ms_render(ptr(X), ptr(Cc), ptr(A), w.scene.n, 8, C.byref(cs), C.byref(p), ptr(out), wsp, nbytes,
+                       stream) == _lib.MS_OK
+    info = _lib.RenderInfo()
+    assert L.ms_render_get_info(wsp, C.byref(info), stream) == _lib.MS_ERR_CAPACITY
+    assert info.overflow == 1 and info.frags > info.frag_capacity
+    dL = torch.randn(out.shape, device="cuda", generator=g)
+    grads = [torch.zeros_like(X), torch.zeros_like(Cc), torch.zeros_like(A)]
+    assert L.ms_render_backward(ptr(X), ptr(Cc), ptr(A), w.scene.n, 8, C.byref(cs), C.byref(p), ptr(out), ptr(dL),
+                                *[ptr(t) for t in grads], wsp, nbytes, stream) == _lib.MS_OK
+    torch.cuda.synchronize()   # raises if a kernel faulted
+    # the renderer's own workspace still renders and differentiates normally afterwards
+    gx, gc, ga = full.backward(X, Cc, A, full.forward(X, Cc, A), dL)
+    torch.cuda.synchronize()
+    assert torch.isfinite(gx).all() and torch.isfinite(gc).all() and torch.isfinite(ga).all()
