@@ -286,6 +286,21 @@ def stage_report(stage_ms, stage_n, info, sc, V, K, npx, local):
     return stages, roof
 
 
+def loss_report(ms_, npx):
+    """Roofline entry of the full fine-tuning loss: two stencil passes over the image,
+    algorithmic 152 B per pixel (image and target 32 B in each pass, nine gradient factor
+    planes 36 B written and read, the gradient image 16 B written)."""
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    ach = npx * 152 / (ms_ * 1e-3) / 1e9
+    return {"ms": ms_, "bound": "hbm", "achieved": ach, "unit": "GB/s", "frac": ach / hbm,
+            "bytes_per_pixel": 152, "loss": "0.6 L1 + 0.4 (1 - SSIM), 11x11 Gaussian window"}
+
+
 def run_ours(args, ws, rank, local):
     import torch
 
@@ -376,6 +391,22 @@ def run_ours(args, ws, rank, local):
     torch.cuda.synchronize()
     fwd_ms = max_over_ranks(sum(a_.elapsed_time(b_) for a_, b_ in zip(f0, f1)) / args.steps, ws)
 
+    # ---- the full fine-tuning loss of Eq. 3 (lambda L1 + (1 - lambda)(1 - SSIM)) on the same
+    # render and target, timed alone: not part of the step above, whose configuration names
+    # the L1 loss
+    lws = torch.empty(L.ms_fine_tune_loss_workspace_size(H, W), dtype=torch.uint8, device="cuda")
+    for _ in range(3):
+        ms.fine_tune_loss(out, target, workspace=lws)
+    s0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    s1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    for i in range(args.steps):
+        flush.zero_()
+        s0[i].record(stream)
+        ms.fine_tune_loss(out, target, workspace=lws)
+        s1[i].record(stream)
+    torch.cuda.synchronize()
+    ssim_ms = max_over_ranks(sum(a_.elapsed_time(b_) for a_, b_ in zip(s0, s1)) / args.steps, ws)
+
     # ---- end to end through the public API from pinned host memory
     e2e = None
     if not args.no_e2e:
@@ -417,7 +448,8 @@ def run_ours(args, ws, rank, local):
             "fwd_mpix_s": ws * mpix(W, H, fwd_ms), "fwd_ms": fwd_ms,
             "e2e": e2e, "gpu_launches": int(launches), "clocks": clk.summary(), "roofline": roof, "stages": stages,
             "work": {"pairs": info.pairs, "rect_tests": info.rect_tests, "fragments": info.fragments,
-                     "commits": info.commits, "extra_passes": info.extra_passes, "sort_bits": info.sort_bits}}
+                     "commits": info.commits, "extra_passes": info.extra_passes, "sort_bits": info.sort_bits},
+            "extra_stages": {"fine_tune_loss": loss_report(ssim_ms, W * H)}}
     if not args.no_cpu_baseline and ws == 1:
         line["cpu_baseline"] = cpu_baseline(w, K)
     print(json.dumps(line), flush=True)

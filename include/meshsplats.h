@@ -12,7 +12,8 @@
  *                       MeshSplats in Nvdiffrast")
  *   ms_render_backward  adjoint of ms_render for vertex positions, colours and opacities
  *                       (Sec. 3 "Fine-tuning", "Optimization and Pruning")
- *   ms_l1_loss, ms_adam_step   the L1 term of Eq. 3 and the two-learning-rate update
+ *   ms_l1_loss, ms_fine_tune_loss, ms_adam_step   the L1 term and the full loss of Eq. 3,
+ *                       and the two-learning-rate update
  *
  * Conventions (all entry points):
  *   - Every pointer named d_* or documented as "device" is caller-owned device memory;
@@ -345,6 +346,27 @@ MS_API ms_status ms_batch_autotune(const float *xyz, const float *rgb, const flo
  */
 MS_API ms_status ms_l1_loss(const float *img_rgba, const float *target_rgba, int64_t n_pixels,
                             float *dL_drgba, float *loss, void *stream);
+
+/*
+ * Full fine-tuning loss of Eq. 3 (Sec. 3 "Loss Function"), read as
+ *   loss = lambda L1 + (1 - lambda)(1 - SSIM),  lambda = 0.6 in the paper,
+ * with L1 = mean |C - C*| and SSIM the mean over the pixels and the three colour channels
+ * of the local structural similarity under an 11 x 11 Gaussian window (sigma 1.5, zero
+ * padding outside the image, C1 = 0.01^2, C2 = 0.03^2).  (The equation as printed adds
+ * SSIM itself; the text says the loss follows 3DGS, whose SSIM term is 1 - SSIM.)
+ *   img_rgba, target_rgba: device height x width x 4 floats, 16-byte aligned (alpha
+ *     ignored).
+ *   dL_drgba: device height x width x 4, written (alpha gradient 0).
+ *   loss: device, 1 float, overwritten.
+ *   workspace: device scratch of ms_fine_tune_loss_workspace_size bytes (any alignment);
+ *     its contents need not be initialised and are not kept.
+ * MS_ERR_INVALID for a size outside 0..32768, lambda outside [0, 1], NULL or misaligned
+ * pointers or a short workspace.  Two kernel launches on `stream`.
+ */
+MS_API size_t ms_fine_tune_loss_workspace_size(int32_t height, int32_t width);
+MS_API ms_status ms_fine_tune_loss(const float *img_rgba, const float *target_rgba, int32_t height, int32_t width,
+                                   float lambda, float *dL_drgba, float *loss, void *workspace, size_t ws_bytes,
+                                   void *stream);
 
 /*
  * Adam step on the fan soup (Sec. 3 "Optimization and Pruning": colours and opacities at

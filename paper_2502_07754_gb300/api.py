@@ -358,6 +358,21 @@ def l1_loss(img_rgba, target_rgba, stream=None):
     return loss, dL
 
 
+def fine_tune_loss(img_rgba, target_rgba, lam=0.6, workspace=None, stream=None):
+    """Eq. 3 read as lam * L1 + (1 - lam)(1 - SSIM) of H x W x 4 images: returns (loss as a
+    1-element device tensor, dL/d img_rgba).  `workspace` (a uint8 device tensor of
+    ms_fine_tune_loss_workspace_size bytes) may be passed to avoid an allocation per call."""
+    H, W = int(img_rgba.shape[0]), int(img_rgba.shape[1])
+    need = lib().ms_fine_tune_loss_workspace_size(H, W)
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(max(need, 1), dtype=torch.uint8, device=img_rgba.device)
+    dL = torch.empty_like(img_rgba)
+    loss = torch.empty(1, device=img_rgba.device, dtype=torch.float32)
+    check(lib().ms_fine_tune_loss(_ptr(img_rgba), _ptr(target_rgba), H, W, float(lam), _ptr(dL), _ptr(loss),
+                                  _ptr(workspace), workspace.numel(), _stream(stream)))
+    return loss, dL
+
+
 def mse(img_rgba, target_rgba, stream=None):
     """Mean squared RGB error (1-element device tensor)."""
     out = torch.empty(1, device=img_rgba.device, dtype=torch.float32)

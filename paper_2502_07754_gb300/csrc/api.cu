@@ -528,6 +528,38 @@ MS_API ms_status ms_l1_loss(const float *img_rgba, const float *target_rgba, int
     return MS_OK;
 }
 
+MS_API size_t ms_fine_tune_loss_workspace_size(int32_t height, int32_t width) {
+    if (height < 0 || width < 0) return 0;
+    return align_up(ssim_scratch_bytes(height, width), 256) + 256;
+}
+
+MS_API ms_status ms_fine_tune_loss(const float *img_rgba, const float *target_rgba, int32_t height, int32_t width,
+                                   float lambda, float *dL_drgba, float *loss, void *workspace, size_t ws_bytes,
+                                   void *stream) {
+    if (height < 0 || width < 0 || height > 32768 || width > 32768 || !loss)
+        return fail(MS_ERR_INVALID, "bad image size %dx%d or NULL loss", width, height);
+    if (!(lambda >= 0.0f && lambda <= 1.0f)) return fail(MS_ERR_INVALID, "lambda %g outside [0, 1]", (double)lambda);
+    const bool empty = height == 0 || width == 0;
+    if (!empty && (!img_rgba || !target_rgba || !dL_drgba || !workspace)) return fail(MS_ERR_INVALID, "NULL pointer");
+    if ((reinterpret_cast<uintptr_t>(img_rgba) | reinterpret_cast<uintptr_t>(target_rgba) |
+         reinterpret_cast<uintptr_t>(dL_drgba)) & 15)
+        return fail(MS_ERR_INVALID, "images must be 16-byte aligned");
+    if (!empty && ws_bytes < ms_fine_tune_loss_workspace_size(height, width))
+        return fail(MS_ERR_INVALID, "workspace %zu bytes < %zu needed", ws_bytes,
+                    ms_fine_tune_loss_workspace_size(height, width));
+    char *ws = static_cast<char *>(workspace);
+    float *scratch = reinterpret_cast<float *>(ws + ((256 - (reinterpret_cast<uintptr_t>(ws) & 255)) & 255));
+    cudaError_t e;
+    {
+        StageScope sc(MS_STAGE_LOSS, (cudaStream_t)stream);
+        e = launch_ssim_loss(img_rgba, target_rgba, height, width, lambda, dL_drgba, loss, empty ? nullptr : scratch,
+                             (cudaStream_t)stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "fine-tune loss launch");
+    if (!empty) count_launches(2);
+    return MS_OK;
+}
+
 static ms_status adam_common(float *xyz, float *rgb, float *alpha, const float *d_xyz, const float *d_rgb,
                              const float *d_alpha, float *m, float *v, int64_t V, int32_t step, int32_t *d_step,
                              float lr_color, float lr_xyz, float beta1, float beta2, float eps, void *stream) {

@@ -111,6 +111,10 @@ struct StageScope {
 };
 
 cudaError_t launch_l1(const float *img, const float *tgt, int64_t n_pixels, float *dL, float *loss, cudaStream_t st);
+// Fine-tuning loss lambda L1 + (1 - lambda)(1 - SSIM) of one H x W RGBA image (ssim.cu).
+size_t ssim_scratch_bytes(int H, int W);
+cudaError_t launch_ssim_loss(const float *img, const float *tgt, int H, int W, float lam, float *dL, float *loss,
+                             float *scratch, cudaStream_t st);
 cudaError_t launch_adam_ws(float *xyz, float *rgb, float *alpha, const float4 *grad, float *m, float *v, int64_t V,
                            int step, int32_t *d_step, float lr_c, float lr_x, float b1, float b2, float eps,
                            cudaStream_t st);
