@@ -3,7 +3,8 @@
 // the image, C1 = 0.01^2, C2 = 0.03^2) averaged over the pixels and the three channels.
 //
 // Two launches over 16 x 16 output tiles, each staging a 26 x 26 window of its inputs in
-// shared memory and applying the separable window as a row pass then a column pass:
+// shared memory (the forward stages the three channels of image and target in one pass)
+// and applying the separable window as a row pass then a column pass:
 //
 // ssim_fwd_kernel: per channel the raw local moments (x, y, x^2, y^2, xy), the SSIM map,
 //   and the three per-pixel factors of its gradient (with A = 2 mu_x mu_y + C1,
@@ -55,7 +56,7 @@ __device__ __forceinline__ float block_sum(float v, float *s_red) {
 __global__ void __launch_bounds__(kT *kT) ssim_fwd_kernel(const float4 *__restrict__ img, const float4 *__restrict__ tgt,
                                                           int H, int W, float lam, float inv_n, Window win,
                                                           float *__restrict__ G, float *__restrict__ loss) {
-    __shared__ float sx[kIn][kIn + 1], sy[kIn][kIn + 1];
+    __shared__ float sx[3][kIn][kIn + 1], sy[3][kIn][kIn + 1];   // the three channels, shifted
     __shared__ float sh[5][kIn][kT + 1];
     __shared__ float s_red[(kT * kT) / 32];
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kT + tx;
@@ -72,26 +73,30 @@ __global__ void __launch_bounds__(kT *kT) ssim_fwd_kernel(const float4 *__restri
     }
     const size_t ref = (size_t)min(y0 + kT / 2, H - 1) * W + min(x0 + kT / 2, W - 1);
     const float4 rxv = img[ref], ryv = tgt[ref];
+    // one pass over the window stages all three channels (each RGBA pixel loaded once)
+    for (int i = tid; i < kIn * kIn; i += kT * kT) {
+        const int lx = i % kIn, ly = i / kIn;
+        const int gx = x0 - kR + lx, gy = y0 - kR + ly;
+        float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
+        if (gx >= 0 && gx < W && gy >= 0 && gy < H) {
+            a = img[(size_t)gy * W + gx];
+            b = tgt[(size_t)gy * W + gx];
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            sx[c][ly][lx] = chan(a, c) - chan(rxv, c);
+            sy[c][ly][lx] = chan(b, c) - chan(ryv, c);
+        }
+    }
+    __syncthreads();
     for (int c = 0; c < 3; ++c) {
         const float rx = chan(rxv, c), ry = chan(ryv, c);
-        for (int i = tid; i < kIn * kIn; i += kT * kT) {
-            const int lx = i % kIn, ly = i / kIn;
-            const int gx = x0 - kR + lx, gy = y0 - kR + ly;
-            float a = 0.0f, b = 0.0f;
-            if (gx >= 0 && gx < W && gy >= 0 && gy < H) {
-                a = chan(img[(size_t)gy * W + gx], c);
-                b = chan(tgt[(size_t)gy * W + gx], c);
-            }
-            sx[ly][lx] = a - rx;
-            sy[ly][lx] = b - ry;
-        }
-        __syncthreads();
         for (int i = tid; i < kIn * kT; i += kT * kT) {
             const int r = i / kT, q = i % kT;
             float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f, s4 = 0.f;
 #pragma unroll
             for (int t = 0; t <= 2 * kR; ++t) {
-                const float a = sx[r][q + t], b = sy[r][q + t], wt = win.w[t];
+                const float a = sx[c][r][q + t], b = sy[c][r][q + t], wt = win.w[t];
                 s0 += wt * a;
                 s1 += wt * b;
                 s2 += wt * a * a;
@@ -128,7 +133,7 @@ __global__ void __launch_bounds__(kT *kT) ssim_fwd_kernel(const float4 *__restri
             G[(3 * c + 2) * plane + o] = g3;
             acc += (1.0f - lam) * (1.0f - S);
         }
-        __syncthreads();   // the next channel restages the tiles
+        __syncthreads();   // the next channel's row pass overwrites sh
     }
     const float t = block_sum(acc, s_red);
     if (tid == 0) atomicAdd(loss, t * inv_n);
