@@ -209,3 +209,28 @@ def adam_step(params, grads, m, v, step, lrs, betas=(0.9, 0.999), eps=1e-15):
         vh = v[i] / (1 - b2 ** step)
         p -= lrs[i] * mh / (np.sqrt(vh) + eps)
     np.clip(params[-1], 0.0, 1.0, out=params[-1])
+
+
+PRUNE_THRESHOLD = float(np.exp(-4.0))
+
+
+def prune_fans(xyz, rgb, alpha, K, threshold=PRUNE_THRESHOLD, moments=()):
+    """Pruning step of Sec. 3 ("Optimization and Pruning") at fan granularity: a face goes
+    when all three of its vertices have opacity below the threshold (exp(-4)); a fan whose
+    faces all go is removed with its K + 1 vertices, the other fans are kept whole and in
+    order.  (All of a fan's faces qualify exactly when all of its vertices are below the
+    threshold, since every face holds the centre and each boundary vertex is in a face.)
+    moments: arrays in the optimiser layout [xyz 3V | rgb 3V | alpha V], compacted alike.
+    Returns (xyz, rgb, alpha, [moments...], kept fan indices)."""
+    a = np.asarray(alpha).reshape(-1, K + 1)
+    keep = ~np.all(a < threshold, axis=1)
+    fans = np.nonzero(keep)[0]
+    vsel = (fans[:, None] * (K + 1) + np.arange(K + 1)).reshape(-1)
+    V = a.size
+    out_m = []
+    for m in moments:
+        m = np.asarray(m)
+        out_m.append(np.concatenate([m[:3 * V].reshape(V, 3)[vsel].reshape(-1),
+                                     m[3 * V:6 * V].reshape(V, 3)[vsel].reshape(-1), m[6 * V:7 * V][vsel]]))
+    return (np.asarray(xyz).reshape(V, 3)[vsel], np.asarray(rgb).reshape(V, 3)[vsel], np.asarray(alpha).reshape(V)[vsel],
+            out_m, fans)
