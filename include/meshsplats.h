@@ -369,6 +369,29 @@ MS_API ms_status ms_fine_tune_loss(const float *img_rgba, const float *target_rg
                                    void *stream);
 
 /*
+ * Pruning step of Sec. 3 ("Optimization and Pruning"): a face goes when all three of its
+ * vertex opacities are below `threshold` (exp(-4) in the paper), and vertices no face
+ * uses any more go with it.  With the implicit fan layout this is applied per fan: a fan
+ * whose faces all go -- exactly when all K + 1 of its vertex opacities are below the
+ * threshold -- is removed; every other fan is kept whole.  (A fan whose centre is below
+ * the threshold but some boundary vertex is not keeps the faces that Sec. 3 would drop
+ * between two dim boundary vertices.)  Kept fans are compacted in their order.
+ *   xyz, rgb, alpha: device soup of n_fans fans of K triangles (read only).
+ *   m, v: optional device Adam moments in the ms_adam_step layout [xyz 3V | rgb 3V |
+ *     alpha V], compacted with the soup; NULL together with m_out / v_out to skip.
+ *   *_out: device arrays of the input sizes (the kept soup fills their front); they must
+ *     not overlap the inputs.
+ *   n_kept: device int64, written with the number of kept fans.
+ *   workspace: device scratch of ms_prune_workspace_size bytes (any alignment).
+ * Three kernel launches on `stream`.
+ */
+MS_API size_t ms_prune_workspace_size(int64_t n_fans);
+MS_API ms_status ms_prune_fans(const float *xyz, const float *rgb, const float *alpha, const float *m, const float *v,
+                               int64_t n_fans, int32_t K, float threshold, float *xyz_out, float *rgb_out,
+                               float *alpha_out, float *m_out, float *v_out, int64_t *n_kept, void *workspace,
+                               size_t ws_bytes, void *stream);
+
+/*
  * Adam step on the fan soup (Sec. 3 "Optimization and Pruning": colours and opacities at
  * lr_color, positions at lr_xyz = exp(-3) lr_color).  Parameters and gradients are
  * device SoA arrays of V vertices; m, v: device moments, 7 V floats each laid out like the

@@ -67,6 +67,9 @@ _SIGS = {
     "ms_l1_loss": (C.c_int, [_P, _P, C.c_int64, _P, _P, _P]),
     "ms_fine_tune_loss_workspace_size": (C.c_size_t, [C.c_int32, C.c_int32]),
     "ms_fine_tune_loss": (C.c_int, [_P, _P, C.c_int32, C.c_int32, C.c_float, _P, _P, _P, C.c_size_t, _P]),
+    "ms_prune_workspace_size": (C.c_size_t, [C.c_int64]),
+    "ms_prune_fans": (C.c_int, [_P, _P, _P, _P, _P, C.c_int64, C.c_int32, C.c_float, _P, _P, _P, _P, _P, _P, _P,
+                                C.c_size_t, _P]),
     "ms_adam_step": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, C.c_int64, C.c_int32, C.c_float, C.c_float, C.c_float,
                                C.c_float, C.c_float, _P]),
     "ms_batch_workspace_size": (C.c_size_t, [C.c_int64, C.c_int32, _P, C.c_int32, _P]),

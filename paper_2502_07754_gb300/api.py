@@ -373,6 +373,29 @@ def fine_tune_loss(img_rgba, target_rgba, lam=0.6, workspace=None, stream=None):
     return loss, dL
 
 
+def prune_fans(xyz, rgb, alpha, K, threshold=math.exp(-4.0), m=None, v=None, stream=None):
+    """Pruning step (ms_prune_fans): removes the fans whose K + 1 vertex opacities are all
+    below `threshold` and compacts the rest (and, if given, their Adam moments m, v in the
+    FanAdam layout).  Returns (xyz, rgb, alpha, m, v, n_kept) with the kept fans only
+    (reads the kept count back, so it synchronises the stream)."""
+    n = xyz.shape[0] // (K + 1)
+    outs = [torch.empty_like(t) for t in (xyz, rgb, alpha)]
+    mo = torch.empty_like(m) if m is not None else None
+    vo = torch.empty_like(v) if v is not None else None
+    n_kept = torch.zeros(1, dtype=torch.int64, device=xyz.device)
+    ws = torch.empty(max(lib().ms_prune_workspace_size(n), 1), dtype=torch.uint8, device=xyz.device)
+    check(lib().ms_prune_fans(_ptr(xyz), _ptr(rgb), _ptr(alpha), _ptr(m) if m is not None else None,
+                              _ptr(v) if v is not None else None, n, int(K), float(threshold), *[_ptr(t) for t in outs],
+                              _ptr(mo) if mo is not None else None, _ptr(vo) if vo is not None else None, _ptr(n_kept),
+                              _ptr(ws), ws.numel(), _stream(stream)))
+    k = int(n_kept.item())
+    Vk = k * (K + 1)
+    # the kernel writes the kept moments in the layout of the kept soup, [xyz 3Vk | rgb 3Vk |
+    # alpha Vk], at the front of the output
+    cut = lambda t: t[:7 * Vk] if t is not None else None
+    return outs[0][:Vk], outs[1][:Vk], outs[2][:Vk], cut(mo), cut(vo), k
+
+
 def mse(img_rgba, target_rgba, stream=None):
     """Mean squared RGB error (1-element device tensor)."""
     out = torch.empty(1, device=img_rgba.device, dtype=torch.float32)

@@ -560,6 +560,32 @@ MS_API ms_status ms_fine_tune_loss(const float *img_rgba, const float *target_rg
     return MS_OK;
 }
 
+MS_API size_t ms_prune_workspace_size(int64_t n_fans) {
+    if (n_fans < 0) return 0;
+    return align_up(prune_scratch_bytes(n_fans), 256) + 256;
+}
+
+MS_API ms_status ms_prune_fans(const float *xyz, const float *rgb, const float *alpha, const float *m, const float *v,
+                               int64_t n_fans, int32_t K, float threshold, float *xyz_out, float *rgb_out,
+                               float *alpha_out, float *m_out, float *v_out, int64_t *n_kept, void *workspace,
+                               size_t ws_bytes, void *stream) {
+    if (n_fans < 0 || K < 3 || K > kMaxK || !n_kept) return fail(MS_ERR_INVALID, "bad n_fans, K or NULL n_kept");
+    if (n_fans * (int64_t)(K + 1) >= (1ll << 32)) return fail(MS_ERR_INVALID, "too many vertices");
+    if (n_fans > 0 && (!xyz || !rgb || !alpha || !xyz_out || !rgb_out || !alpha_out || !workspace))
+        return fail(MS_ERR_INVALID, "NULL pointer");
+    if ((m == nullptr) != (m_out == nullptr) || (v == nullptr) != (v_out == nullptr))
+        return fail(MS_ERR_INVALID, "a moment array and its output must be both set or both NULL");
+    if (n_fans > 0 && ws_bytes < ms_prune_workspace_size(n_fans))
+        return fail(MS_ERR_INVALID, "workspace %zu bytes < %zu needed", ws_bytes, ms_prune_workspace_size(n_fans));
+    char *ws = static_cast<char *>(workspace);
+    void *scratch = ws ? ws + ((256 - (reinterpret_cast<uintptr_t>(ws) & 255)) & 255) : nullptr;
+    cudaError_t e = launch_prune(xyz, rgb, alpha, m, v, n_fans, K, threshold, xyz_out, rgb_out, alpha_out, m_out,
+                                 v_out, n_kept, scratch, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "prune launch");
+    if (n_fans > 0) count_launches(3);
+    return MS_OK;
+}
+
 static ms_status adam_common(float *xyz, float *rgb, float *alpha, const float *d_xyz, const float *d_rgb,
                              const float *d_alpha, float *m, float *v, int64_t V, int32_t step, int32_t *d_step,
                              float lr_color, float lr_xyz, float beta1, float beta2, float eps, void *stream) {

@@ -111,6 +111,11 @@ struct StageScope {
 };
 
 cudaError_t launch_l1(const float *img, const float *tgt, int64_t n_pixels, float *dL, float *loss, cudaStream_t st);
+// Pruning of fans whose vertex opacities are all below a threshold (prune.cu).
+size_t prune_scratch_bytes(int64_t n_fans);
+cudaError_t launch_prune(const float *xyz, const float *rgb, const float *alpha, const float *m, const float *v,
+                         int64_t n_fans, int K, float thr, float *xyz_o, float *rgb_o, float *alpha_o, float *m_o,
+                         float *v_o, int64_t *n_kept, void *scratch, cudaStream_t st);
 // Fine-tuning loss lambda L1 + (1 - lambda)(1 - SSIM) of one H x W RGBA image (ssim.cu).
 size_t ssim_scratch_bytes(int H, int W);
 cudaError_t launch_ssim_loss(const float *img, const float *tgt, int H, int W, float lam, float *dL, float *loss,

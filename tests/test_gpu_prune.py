@@ -1,0 +1,77 @@
+"""GPU parity of the pruning step (ms_prune_fans) against oracle.prune_fans: the kept
+soup and its Adam moments are data movement, so the comparison is bit-exact."""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2502_07754_gb300._lib as L
+    L.lib()
+
+
+import paper_2502_07754_gb300 as ms  # noqa: E402
+
+
+def _soup(n, K, frac_low, seed):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    V = n * (K + 1)
+    xyz = rng.normal(size=(V, 3)).astype(np.float32)
+    rgb = rng.random((V, 3)).astype(np.float32)
+    a = rng.uniform(0.0, 1.0, (n, K + 1)).astype(np.float32)
+    low = rng.random(n) < frac_low
+    a[low] *= np.float32(0.018)                                  # every vertex below exp(-4)
+    part = (~low) & (rng.random(n) < 0.2)
+    a[part, 0] = np.float32(0.001)                               # dim centre, brighter rim: kept
+    a[rng.random(n) < 0.01, :] = np.float32(math.exp(-4.0))      # on the threshold: kept
+    m = rng.normal(size=7 * V).astype(np.float32)
+    v = rng.random(7 * V).astype(np.float32)
+    return xyz, rgb, a.reshape(-1), m, v
+
+
+@pytest.mark.parametrize("n,K,frac", [(10007, 8, 0.3), (3001, 6, 0.5), (777, 8, 0.0), (500, 8, 1.0), (0, 8, 0.5)])
+def test_prune_matches_oracle_bit_for_bit(n, K, frac):
+    xyz, rgb, a, m, v = _soup(n, K, frac, 40 + n)
+    d = lambda t: torch.from_numpy(np.ascontiguousarray(t)).cuda()
+    px, pc, pa, pm, pv, k = ms.prune_fans(d(xyz), d(rgb), d(a), K, m=d(m), v=d(v))
+    thr = np.float32(math.exp(-4.0))
+    ox, oc, oa, (om, ov), fans = oracle.prune_fans(xyz, rgb, a, K, threshold=thr, moments=(m, v))
+    assert k == fans.size
+    for got, want in ((px, ox), (pc, oc), (pa, oa), (pm, om), (pv, ov)):
+        assert np.array_equal(got.cpu().numpy(), np.asarray(want, np.float32).reshape(got.shape))
+    if n > 0 and 0 < frac < 1:
+        assert 0 < k < n
+
+
+def test_prune_without_moments_and_render_after():
+    """Pruning without optimiser state, then rendering the kept soup: equal to the render
+    of the full soup with the pruned fans' faces left out (the oracle's fan list)."""
+    import synthetic
+    from gpu_util import err_report
+    w = synthetic.workload(1, n=600)
+    cam = w.cameras[0]
+    K = 8
+    xyz, rgb, a = oracle.mesh_build(w.scene, K=K, cam_center=cam.C)
+    xyz, rgb, a = xyz.astype(np.float32), rgb.astype(np.float32), a.astype(np.float32).copy()
+    rng = np.random.Generator(np.random.PCG64(8))
+    a.reshape(600, K + 1)[rng.random(600) < 0.4] *= np.float32(0.05)
+    d = lambda t: torch.from_numpy(np.ascontiguousarray(t)).cuda()
+    px, pc, pa, pm, pv, k = ms.prune_fans(d(xyz), d(rgb), d(a), K)
+    assert pm is None and pv is None
+    _, _, _, _, fans = oracle.prune_fans(xyz, rgb, a, K, threshold=np.float32(math.exp(-4.0)))
+    assert k == fans.size
+    img = ms.Renderer(k, K, cam).forward(px, pc, pa).cpu().numpy().astype(np.float64)
+    tris = oracle.fan_tris(600, K).reshape(600, K, 3)[fans].reshape(-1, 3)
+    ref, _, _ = oracle.render(xyz.astype(np.float64), rgb.astype(np.float64), a.astype(np.float64), tris, cam)
+    rep = err_report(img, ref)
+    assert rep["n_over_tol"] == 0, rep
