@@ -286,6 +286,22 @@ def stage_report(stage_ms, stage_n, info, sc, V, K, npx, local):
     return stages, roof
 
 
+def prune_report(ms_, n_fans, K, kept):
+    """Roofline entry of the pruning step: opacities read twice (4 (K+1) B per fan each),
+    then 84 B read and 84 B written per kept vertex (position, colour, opacity and their
+    two Adam moments).  The time includes the host read of the kept count."""
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    nbytes = n_fans * (K + 1) * 8 + kept * (K + 1) * 168
+    ach = nbytes / (ms_ * 1e-3) / 1e9
+    return {"ms": ms_, "bound": "hbm", "achieved": ach, "unit": "GB/s", "frac": ach / hbm, "fans": n_fans,
+            "kept": kept}
+
+
 def loss_report(ms_, npx):
     """Roofline entry of the full fine-tuning loss: two stencil passes over the image,
     algorithmic 152 B per pixel (image and target 32 B in each pass, nine gradient factor
@@ -407,6 +423,22 @@ def run_ours(args, ws, rank, local):
     torch.cuda.synchronize()
     ssim_ms = max_over_ranks(sum(a_.elapsed_time(b_) for a_, b_ in zip(s0, s1)) / args.steps, ws)
 
+    # ---- the pruning step (every 10 epochs in Sec. 3; not part of the step) on this soup
+    # with its Adam moments
+    px_ = None
+    for _ in range(2):
+        px_ = ms.prune_fans(x, c, al, K, m=adam.m, v=adam.v)
+    p0 = torch.cuda.Event(enable_timing=True)
+    p1 = torch.cuda.Event(enable_timing=True)
+    flush.zero_()
+    p0.record(stream)
+    px_ = ms.prune_fans(x, c, al, K, m=adam.m, v=adam.v)
+    p1.record(stream)
+    torch.cuda.synchronize()
+    prune_ms = max_over_ranks(p0.elapsed_time(p1), ws)
+    kept = px_[5]
+    del px_
+
     # ---- end to end through the public API from pinned host memory
     e2e = None
     if not args.no_e2e:
@@ -449,7 +481,8 @@ def run_ours(args, ws, rank, local):
             "e2e": e2e, "gpu_launches": int(launches), "clocks": clk.summary(), "roofline": roof, "stages": stages,
             "work": {"pairs": info.pairs, "rect_tests": info.rect_tests, "fragments": info.fragments,
                      "commits": info.commits, "extra_passes": info.extra_passes, "sort_bits": info.sort_bits},
-            "extra_stages": {"fine_tune_loss": loss_report(ssim_ms, W * H)}}
+            "extra_stages": {"fine_tune_loss": loss_report(ssim_ms, W * H),
+                             "prune": prune_report(prune_ms, sc.n, K, kept)}}
     if not args.no_cpu_baseline and ws == 1:
         line["cpu_baseline"] = cpu_baseline(w, K)
     print(json.dumps(line), flush=True)
