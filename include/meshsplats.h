@@ -153,6 +153,24 @@ MS_API ms_status ms_mesh_build(const float *means, const float *log_scales, cons
                                int64_t N, const ms_fan_params *fan, const float *cam_center,
                                const float *corr, float *xyz, float *rgb, float *alpha, void *stream);
 
+/*
+ * Three-fan conversion of 3D Gaussians (Sec. 3 "Transformation for 3D Gaussians"): all
+ * three scaled axes sr_c = scale_mul exp(s_c) r_c are kept and each Gaussian becomes one
+ * fan of K triangles per pair of axes, (1, 2), (1, 3), (2, 3), with the angles, colour
+ * and opacity rules of ms_mesh_build (fan->axis_rule is ignored; no corrections).  The
+ * fans meet at the centre and at the axis tips m +- sr_c that two fans both reach; the
+ * output keeps the implicit fan layout the renderer takes, so those shared vertices appear
+ * once in every fan that uses them (quarter-turn angles use exact cosine and sine, so the
+ * copies are equal bit for bit).
+ *   xyz, rgb, alpha: device, 3 N (K + 1) vertices: fan 3g + f of Gaussian g is vertices
+ *   (3g + f)(K + 1) .. + K, centre first.  Render them as 3 N fans of K triangles.
+ * Other arguments and errors as ms_mesh_build.
+ */
+MS_API ms_status ms_mesh_build_3d(const float *means, const float *log_scales, const float *quats,
+                                  const float *opacity, const void *sh, int32_t sh_dtype, int32_t sh_degree, int64_t N,
+                                  const ms_fan_params *fan, const float *cam_center, float *xyz, float *rgb,
+                                  float *alpha, void *stream);
+
 /* Bytes of workspace ms_render / ms_render_backward need for n_fans fans of K triangles. */
 MS_API size_t ms_render_workspace_size(int64_t n_fans, int32_t K, const ms_camera *cam,
                                        const ms_render_params *params);

@@ -81,6 +81,25 @@ def mesh_build(means, log_scales, quats, opacity, sh, sh_degree, K=8, scale_mul=
     return xyz, rgb, alpha
 
 
+def mesh_build_3d(means, log_scales, quats, opacity, sh, sh_degree, K=8, scale_mul=SCALE_MUL, opac_mul=OPAC_MUL,
+                  cam_center=None, stream=None):
+    """3D Gaussians -> three fans per Gaussian (ms_mesh_build_3d): (xyz, rgb, alpha) with
+    3 N (K+1) vertices, to be rendered as 3 N fans of K triangles."""
+    N = means.shape[0]
+    dev = means.device
+    V = 3 * N * (K + 1)
+    xyz = torch.empty(V, 3, device=dev, dtype=torch.float32)
+    rgb = torch.empty(V, 3, device=dev, dtype=torch.float32)
+    alpha = torch.empty(V, device=dev, dtype=torch.float32)
+    fp = _lib.FanParams(int(K), float(scale_mul), float(opac_mul), 1)
+    sh_dtype = 0 if sh.dtype == torch.float32 else 1
+    cc = (C.c_float * 3)(*[float(x) for x in cam_center]) if cam_center is not None else None
+    check(lib().ms_mesh_build_3d(_ptr(means), _ptr(log_scales), _ptr(quats), _ptr(opacity), _ptr(sh), sh_dtype,
+                                 int(sh_degree), N, C.byref(fp), cc, _ptr(xyz), _ptr(rgb), _ptr(alpha),
+                                 _stream(stream)))
+    return xyz, rgb, alpha
+
+
 class Renderer:
     """Owns a render workspace for one (fan count, K, camera, params) and grows its pair
     capacity when a render reports MS_ERR_CAPACITY."""

@@ -359,10 +359,10 @@ MS_API void ms_render_params_default(ms_render_params *p) {
     p->depth_bits = 0;
 }
 
-MS_API ms_status ms_mesh_build(const float *means, const float *log_scales, const float *quats, const float *opacity,
-                               const void *sh, int32_t sh_dtype, int32_t sh_degree, int64_t N, const ms_fan_params *fan,
-                               const float *cam_center, const float *corr, float *xyz, float *rgb, float *alpha,
-                               void *stream) {
+static ms_status mesh_build_common(const float *means, const float *log_scales, const float *quats,
+                                   const float *opacity, const void *sh, int32_t sh_dtype, int32_t sh_degree, int64_t N,
+                                   const ms_fan_params *fan, const float *cam_center, const float *corr, float *xyz,
+                                   float *rgb, float *alpha, bool three, void *stream) {
     if (!fan) return fail(MS_ERR_INVALID, "fan params NULL");
     if (N < 0) return fail(MS_ERR_INVALID, "N < 0");
     if (fan->K < 3 || fan->K > kMaxK) return fail(MS_ERR_INVALID, "K=%d outside 3..%d", fan->K, kMaxK);
@@ -373,18 +373,25 @@ MS_API ms_status ms_mesh_build(const float *means, const float *log_scales, cons
     if (!means || !log_scales || !quats || !opacity || !sh || !xyz || !rgb || !alpha)
         return fail(MS_ERR_INVALID, "NULL pointer");
     if (reinterpret_cast<uintptr_t>(quats) & 15) return fail(MS_ERR_INVALID, "quats must be 16-byte aligned");
-    if (N * (int64_t)(fan->K + 1) >= (1ll << 32)) return fail(MS_ERR_INVALID, "too many vertices");
+    if (N * (int64_t)(fan->K + 1) * (three ? 3 : 1) >= (1ll << 32)) return fail(MS_ERR_INVALID, "too many vertices");
     MeshBuildConst kc;
     memset(&kc, 0, sizeof(kc));
     kc.K = fan->K;
     kc.scale_mul = fan->scale_mul;
     kc.opac_mul = fan->opac_mul;
     kc.axis_rule = fan->axis_rule;
+    kc.three = three ? 1 : 0;
     const double PI = 3.14159265358979323846;
     for (int i = 0; i < fan->K; ++i) {
         const double th = -PI + 2.0 * PI * i / fan->K;
         kc.cs[i] = (float)cos(th);
         kc.sn[i] = (float)sin(th);
+        if (three && (4 * i) % fan->K == 0) {   // a quarter turn: exact, so shared tips coincide
+            static const float qc[4] = {-1.0f, 0.0f, 1.0f, 0.0f}, qs[4] = {0.0f, -1.0f, 0.0f, 1.0f};
+            const int q = (4 * i) / fan->K;
+            kc.cs[i] = qc[q & 3];
+            kc.sn[i] = qs[q & 3];
+        }
     }
     kc.shc[0] = (float)(0.5 * sqrt(1.0 / PI));
     kc.shc[1] = (float)sqrt(3.0 / (4.0 * PI));
@@ -411,6 +418,22 @@ MS_API ms_status ms_mesh_build(const float *means, const float *log_scales, cons
     if (e != cudaSuccess) return cuda_fail(e, "mesh_build launch");
     count_launches(1);
     return MS_OK;
+}
+
+MS_API ms_status ms_mesh_build(const float *means, const float *log_scales, const float *quats, const float *opacity,
+                               const void *sh, int32_t sh_dtype, int32_t sh_degree, int64_t N, const ms_fan_params *fan,
+                               const float *cam_center, const float *corr, float *xyz, float *rgb, float *alpha,
+                               void *stream) {
+    return mesh_build_common(means, log_scales, quats, opacity, sh, sh_dtype, sh_degree, N, fan, cam_center, corr, xyz,
+                             rgb, alpha, false, stream);
+}
+
+MS_API ms_status ms_mesh_build_3d(const float *means, const float *log_scales, const float *quats,
+                                  const float *opacity, const void *sh, int32_t sh_dtype, int32_t sh_degree, int64_t N,
+                                  const ms_fan_params *fan, const float *cam_center, float *xyz, float *rgb,
+                                  float *alpha, void *stream) {
+    return mesh_build_common(means, log_scales, quats, opacity, sh, sh_dtype, sh_degree, N, fan, cam_center, nullptr,
+                             xyz, rgb, alpha, true, stream);
 }
 
 MS_API size_t ms_render_workspace_size(int64_t n_fans, int32_t K, const ms_camera *cam, const ms_render_params *params) {

@@ -1,9 +1,14 @@
 // Gaussian -> triangle-fan conversion with SH colour (Sec. 3, "MeshSplats
-// Transformation for Flat Gaussians", Eq. 2 and the vertex equation after it).
+// Transformation for Flat Gaussians", Eq. 2 and the vertex equation after it; and
+// "Transformation for 3D Gaussians": all three scaled axes kept, one fan per pair of axes
+// (1, 2), (1, 3), (2, 3), written as three implicit fans of K triangles per Gaussian whose
+// shared vertices -- the centre and the axis tips two fans reach -- are copies; the
+// angle table then holds exact cosine and sine at quarter turns, so the copies are equal
+// bit for bit).
 //
 // One thread per Gaussian.  The block's vertices are assembled in shared memory and
 // leave in 16-byte coalesced stores, so each output byte crosses HBM once:
-// read 44 B + SH, write 28 (K+1) B per Gaussian.
+// read 44 B + SH, write 28 (K+1) B per fan.
 #include <math.h>
 
 #include "ms_common.cuh"
@@ -101,9 +106,10 @@ __global__ void __launch_bounds__(kMBThreads) mesh_build_kernel(
     const float *__restrict__ corr, float *__restrict__ xyz, float *__restrict__ rgb, float *__restrict__ alpha) {
     extern __shared__ float smem[];
     const int K = kc.K, KV = K + 1;
-    float *s_xyz = smem;                          // kMBThreads * KV * 3
-    float *s_rgb = s_xyz + kMBThreads * KV * 3;   // kMBThreads * KV * 3
-    float *s_a = s_rgb + kMBThreads * KV * 3;     // kMBThreads * KV
+    const int GV = (kc.three ? 3 : 1) * KV;      // vertices per Gaussian
+    float *s_xyz = smem;                          // kMBThreads * GV * 3
+    float *s_rgb = s_xyz + kMBThreads * GV * 3;   // kMBThreads * GV * 3
+    float *s_a = s_rgb + kMBThreads * GV * 3;     // kMBThreads * GV
 
     const int64_t g0 = (int64_t)blockIdx.x * kMBThreads;
     const int64_t g = g0 + threadIdx.x;
@@ -156,9 +162,31 @@ __global__ void __launch_bounds__(kMBThreads) mesh_build_kernel(
             col[ch] = fmaxf(acc, 0.0f);
         }
         const float sig = __ldg(opacity + g);
+        const int lv = threadIdx.x * GV;
+        if (kc.three) {
+            float sr[3][3];   // sr[c] = scale_mul exp(s_c) r_c
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const float sc = kc.scale_mul * expf(s[c]);
+#pragma unroll
+                for (int r = 0; r < 3; ++r) sr[c][r] = sc * R[3 * r + c];
+            }
+            for (int fan = 0; fan < 3; ++fan) {
+                const int fa = fan == 2 ? 1 : 0, fb = fan == 0 ? 1 : 2;
+                for (int k = 0; k < KV; ++k) {
+                    const int v = lv + fan * KV + k;
+#pragma unroll
+                    for (int r = 0; r < 3; ++r) {
+                        s_xyz[3 * v + r] = k == 0 ? m[r]
+                                                  : m[r] + (kc.cs[k - 1] * sr[fa][r] + kc.sn[k - 1] * sr[fb][r]);
+                        s_rgb[3 * v + r] = col[r];
+                    }
+                    s_a[v] = k == 0 ? sig : kc.opac_mul * sig;
+                }
+            }
+        }
         const float *cr = corr ? corr + g * 2 * KV : nullptr;
-        const int lv = threadIdx.x * KV;
-        for (int k = 0; k < KV; ++k) {
+        for (int k = 0; k < KV && !kc.three; ++k) {
             float p[3];
             if (k == 0) {
                 p[0] = m[0]; p[1] = m[1]; p[2] = m[2];
@@ -179,18 +207,18 @@ __global__ void __launch_bounds__(kMBThreads) mesh_build_kernel(
         }
     }
     __syncthreads();
-    const int64_t v0 = g0 * KV;
-    block_store(xyz + 3 * v0, s_xyz, 3 * nloc * KV);
-    block_store(rgb + 3 * v0, s_rgb, 3 * nloc * KV);
-    block_store(alpha + v0, s_a, nloc * KV);
+    const int64_t v0 = g0 * GV;
+    block_store(xyz + 3 * v0, s_xyz, 3 * nloc * GV);
+    block_store(rgb + 3 * v0, s_rgb, 3 * nloc * GV);
+    block_store(alpha + v0, s_a, nloc * GV);
 }
 
 template <int DEG>
 cudaError_t launch_deg(bool bf16, const float *means, const float *log_scales, const float *quats,
                        const float *opacity, const void *sh, int64_t N, const MeshBuildConst &kc, const float *corr,
                        float *xyz, float *rgb, float *alpha, cudaStream_t st) {
-    const int KV = kc.K + 1;
-    const size_t smem = sizeof(float) * kMBThreads * KV * 7;
+    const int GV = (kc.three ? 3 : 1) * (kc.K + 1);
+    const size_t smem = sizeof(float) * kMBThreads * GV * 7;
     const unsigned grid = (unsigned)((N + kMBThreads - 1) / kMBThreads);
     if (bf16) {
         auto fn = mesh_build_kernel<DEG, true>;

@@ -19,6 +19,7 @@ struct MeshBuildConst {
     int has_cam;
     float cc[3];
     int sh_vec_ok;          // SH base pointer 16-byte aligned
+    int three;              // three fans per Gaussian (3D conversion), else one flat fan
 };
 
 cudaError_t launch_mesh_build(const float *means, const float *log_scales, const float *quats, const float *opacity,
