@@ -166,6 +166,17 @@ MS_API ms_status ms_mesh_build(const float *means, const float *log_scales, cons
  *   (3g + f)(K + 1) .. + K, centre first.  Render them as 3 N fans of K triangles.
  * Other arguments and errors as ms_mesh_build.
  */
+/*
+ * Copy map of the three-fan layout of ms_mesh_build_3d (host only, no device work): for
+ * each of the 3 (K + 1) vertex slots of one Gaussian (fan f, vertex k at slot f (K + 1) + k)
+ * writes to first_copy the slot of the first copy of the same vertex (a slot that is its
+ * own first copy maps to itself; the centre of every fan maps to slot 0).  Summing the
+ * gradients of a vertex's copies and giving every copy the sum keeps the copies equal
+ * under a fine-tune.  Returns the number of distinct vertices per Gaussian (19 for
+ * K = 8), or -1 for K outside 3..16 or a NULL pointer.
+ */
+MS_API int32_t ms_three_fan_copies(int32_t K, int32_t *first_copy);
+
 MS_API ms_status ms_mesh_build_3d(const float *means, const float *log_scales, const float *quats,
                                   const float *opacity, const void *sh, int32_t sh_dtype, int32_t sh_degree, int64_t N,
                                   const ms_fan_params *fan, const float *cam_center, float *xyz, float *rgb,

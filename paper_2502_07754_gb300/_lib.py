@@ -60,6 +60,7 @@ _SIGS = {
     "ms_render_params_default": (None, [_P]),
     "ms_mesh_build": (C.c_int, [_P, _P, _P, _P, _P, C.c_int32, C.c_int32, C.c_int64, _P, _P, _P, _P, _P, _P, _P]),
     "ms_mesh_build_3d": (C.c_int, [_P, _P, _P, _P, _P, C.c_int32, C.c_int32, C.c_int64, _P, _P, _P, _P, _P, _P]),
+    "ms_three_fan_copies": (C.c_int32, [C.c_int32, _P]),
     "ms_render_workspace_size": (C.c_size_t, [C.c_int64, C.c_int32, _P, _P]),
     "ms_render": (C.c_int, [_P, _P, _P, C.c_int64, C.c_int32, _P, _P, _P, _P, C.c_size_t, _P]),
     "ms_render_backward": (C.c_int, [_P, _P, _P, C.c_int64, C.c_int32, _P, _P, _P, _P, _P, _P, _P, _P, C.c_size_t,

@@ -100,6 +100,16 @@ def mesh_build_3d(means, log_scales, quats, opacity, sh, sh_degree, K=8, scale_m
     return xyz, rgb, alpha
 
 
+def three_fan_copies(K):
+    """Copy map of one Gaussian's 3 (K+1) three-fan vertex slots (ms_three_fan_copies):
+    (first-copy slot of every slot as a list, number of distinct vertices)."""
+    buf = (C.c_int32 * (3 * (K + 1)))()
+    n = lib().ms_three_fan_copies(int(K), buf)
+    if n < 0:
+        raise ValueError(f"K={K} outside 3..16")
+    return list(buf), int(n)
+
+
 class Renderer:
     """Owns a render workspace for one (fan count, K, camera, params) and grows its pair
     capacity when a render reports MS_ERR_CAPACITY."""

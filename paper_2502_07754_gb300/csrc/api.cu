@@ -428,6 +428,42 @@ MS_API ms_status ms_mesh_build(const float *means, const float *log_scales, cons
                              rgb, alpha, false, stream);
 }
 
+MS_API int32_t ms_three_fan_copies(int32_t K, int32_t *first_copy) {
+    if (K < 3 || K > kMaxK || !first_copy) return -1;
+    const int KV = K + 1;
+    // a slot of fan f (axes (1,2), (1,3), (2,3)) at angle i reaches the tip of axis c with
+    // sign s when the angle is a quarter turn; the centre is slot 0 of every fan
+    auto tip = [&](int f, int i, int &axis, int &sign) -> bool {
+        if ((4 * i) % K != 0) return false;
+        const int q = ((4 * i) / K) & 3;   // angle (q - 2) pi / 2
+        const int a = f == 2 ? 1 : 0, b = f == 0 ? 1 : 2;
+        if (q == 0 || q == 2) { axis = a; sign = q == 2 ? 1 : -1; }
+        else { axis = b; sign = q == 3 ? 1 : -1; }
+        return true;
+    };
+    int distinct = 1;
+    for (int f = 0; f < 3; ++f) {
+        first_copy[f * KV] = 0;
+        for (int i = 0; i < K; ++i) {
+            const int slot = f * KV + 1 + i;
+            first_copy[slot] = slot;
+            int ax, sg;
+            if (tip(f, i, ax, sg)) {
+                for (int g = 0; g < f && first_copy[slot] == slot; ++g)
+                    for (int j = 0; j < K; ++j) {
+                        int ax2, sg2;
+                        if (tip(g, j, ax2, sg2) && ax2 == ax && sg2 == sg) {
+                            first_copy[slot] = g * KV + 1 + j;
+                            break;
+                        }
+                    }
+            }
+            if (first_copy[slot] == slot) ++distinct;
+        }
+    }
+    return distinct;
+}
+
 MS_API ms_status ms_mesh_build_3d(const float *means, const float *log_scales, const float *quats,
                                   const float *opacity, const void *sh, int32_t sh_dtype, int32_t sh_degree, int64_t N,
                                   const ms_fan_params *fan, const float *cam_center, float *xyz, float *rgb,

@@ -115,3 +115,17 @@ def test_implicit_fan_copies_render_like_the_shared_mesh():
     fans, _, _ = oracle.render(fx, fc, fa, oracle.fan_tris(w.scene.n * 3, K), cam)
     assert np.array_equal(shared, fans)
     assert shared[..., 3].max() > 0.1
+
+
+@pytest.mark.parametrize("K", list(range(3, 17)))
+def test_library_copy_map_matches_the_oracle(K):
+    """ms_three_fan_copies (host code of the library, no device work) against the copy map
+    of the oracle's implicit-fan layout: two slots are copies exactly when they copy the
+    same unique vertex, and each slot maps to the first of them."""
+    import paper_2502_07754_gb300 as ms
+    first, n = ms.three_fan_copies(K)
+    nv, _ = TF.fan_layout(K)
+    assert n == nv
+    src = TF.as_implicit_fans(np.zeros((nv, 3)), np.zeros((nv, 3)), np.zeros(nv), K, nv)[3]
+    want = [int(np.nonzero(src == src[s])[0].min()) for s in range(src.size)]
+    assert first == want
