@@ -417,6 +417,8 @@ def prune_fans(xyz, rgb, alpha, K, threshold=math.exp(-4.0), m=None, v=None, str
                               _ptr(v) if v is not None else None, n, int(K), float(threshold), *[_ptr(t) for t in outs],
                               _ptr(mo) if mo is not None else None, _ptr(vo) if vo is not None else None, _ptr(n_kept),
                               _ptr(ws), ws.numel(), _stream(stream)))
+    if stream is not None:
+        stream.synchronize()   # the count is read on the host; .item() waits on the current stream only
     k = int(n_kept.item())
     Vk = k * (K + 1)
     # the kernel writes the kept moments in the layout of the kept soup, [xyz 3Vk | rgb 3Vk |
