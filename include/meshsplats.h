@@ -455,9 +455,9 @@ MS_API ms_status ms_adam_step_counted(float *xyz, float *rgb, float *alpha, cons
 /*
  * Forward render without a caller workspace.  The paper has no counterpart: this entry
  * point exists for callers that cannot allocate device memory -- a plugin whose host
- * application owns the GPU memory budget, code running while a stream is being captured
- * into a CUDA graph (cudaMalloc cannot be captured), or a latency-critical loop that
- * cannot afford cudaMalloc's implicit device synchronisation.  It behaves like
+ * application owns the GPU memory budget and hands out no allocations, or a service that
+ * reserves all of its device memory at start-up and forbids allocation afterwards.  It
+ * behaves like
  * ms_render (same inputs, output, camera and params; everything in device memory owned
  * by the caller) but its scratch is a 64 MiB file-scope device array inside the library,
  * held by every GPU that loads the library until the process exits.  Renders whose

@@ -1,9 +1,8 @@
 // ms_render_noalloc: the forward render with its scratch in a fixed device array.
 //
 // Some callers cannot allocate device memory: a plugin whose host application owns the
-// GPU memory budget, code that runs while a stream is being captured into a CUDA graph
-// (cudaMalloc is not capturable), or a latency-critical loop where cudaMalloc's
-// implicit device synchronisation is not acceptable.  They cannot provide the
+// GPU memory budget and hands out no allocations, or a service that reserves all of its
+// device memory at start-up and forbids allocation afterwards.  They cannot provide the
 // workspace that ms_render needs, so this entry point uses a file-scope device array
 // instead.  Inputs and the output image are still the caller's.
 //
