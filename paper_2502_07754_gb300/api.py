@@ -26,9 +26,20 @@ def _ptr(t):
     return C.c_void_p(t.data_ptr())
 
 
-def _stream(stream=None):
-    s = stream if stream is not None else torch.cuda.current_stream()
-    return C.c_void_p(s.cuda_stream)
+def _stream(stream=None, *used):
+    """Handle of the stream a call runs on.  When the caller names a stream other than the
+    current one, that stream first waits for the current stream (where the inputs, outputs
+    and workspaces were written or allocated), and every tensor in `used` is marked as used
+    on it so that the caching allocator does not hand its memory out again before the
+    call's work there has finished."""
+    cur = torch.cuda.current_stream()
+    if stream is None or stream == cur:
+        return C.c_void_p(cur.cuda_stream)
+    stream.wait_stream(cur)
+    for t in used:
+        if t is not None:
+            t.record_stream(stream)
+    return C.c_void_p(stream.cuda_stream)
 
 
 def camera_struct(cam) -> _lib.Camera:
@@ -77,7 +88,7 @@ def mesh_build(means, log_scales, quats, opacity, sh, sh_degree, K=8, scale_mul=
     cc = (C.c_float * 3)(*[float(x) for x in cam_center]) if cam_center is not None else None
     check(lib().ms_mesh_build(_ptr(means), _ptr(log_scales), _ptr(quats), _ptr(opacity), _ptr(sh), sh_dtype,
                               int(sh_degree), N, C.byref(fp), cc, _ptr(corr), _ptr(xyz), _ptr(rgb), _ptr(alpha),
-                              _stream(stream)))
+                              _stream(stream, xyz, rgb, alpha)))
     return xyz, rgb, alpha
 
 
@@ -96,7 +107,7 @@ def mesh_build_3d(means, log_scales, quats, opacity, sh, sh_degree, K=8, scale_m
     cc = (C.c_float * 3)(*[float(x) for x in cam_center]) if cam_center is not None else None
     check(lib().ms_mesh_build_3d(_ptr(means), _ptr(log_scales), _ptr(quats), _ptr(opacity), _ptr(sh), sh_dtype,
                                  int(sh_degree), N, C.byref(fp), cc, _ptr(xyz), _ptr(rgb), _ptr(alpha),
-                                 _stream(stream)))
+                                 _stream(stream, xyz, rgb, alpha)))
     return xyz, rgb, alpha
 
 
@@ -141,7 +152,8 @@ class Renderer:
             out = torch.empty(self.cam.height, self.cam.width, 4, device=xyz.device, dtype=torch.float32)
         for _ in range(4):
             check(lib().ms_render(_ptr(xyz), _ptr(rgb), _ptr(alpha), self.n_fans, self.K, C.byref(self.cam),
-                                  C.byref(self.params), _ptr(out), _ptr(self.ws), self.ws.numel(), _stream(stream)))
+                                  C.byref(self.params), _ptr(out), _ptr(self.ws), self.ws.numel(),
+                                  _stream(stream, out, self.ws)))
             if not check_status:
                 return out
             st, inf = self.info(stream)
@@ -165,7 +177,7 @@ class Renderer:
             check(lib().ms_render_backward(_ptr(xyz), _ptr(rgb), _ptr(alpha), self.n_fans, self.K,
                                            C.byref(self.cam), C.byref(self.params), _ptr(out_rgba),
                                            _ptr(dL.contiguous()), None, None, None, _ptr(self.ws), self.ws.numel(),
-                                           _stream(stream)))
+                                           _stream(stream, self.ws)))
             return None
         if d_xyz is None:
             d_xyz = torch.zeros_like(xyz)
@@ -173,7 +185,8 @@ class Renderer:
             d_alpha = torch.zeros_like(alpha)
         check(lib().ms_render_backward(_ptr(xyz), _ptr(rgb), _ptr(alpha), self.n_fans, self.K, C.byref(self.cam),
                                        C.byref(self.params), _ptr(out_rgba), _ptr(dL.contiguous()), _ptr(d_xyz),
-                                       _ptr(d_rgb), _ptr(d_alpha), _ptr(self.ws), self.ws.numel(), _stream(stream)))
+                                       _ptr(d_rgb), _ptr(d_alpha), _ptr(self.ws), self.ws.numel(),
+                                       _stream(stream, d_xyz, d_rgb, d_alpha, self.ws)))
         return d_xyz, d_rgb, d_alpha
 
     def grad_ptr(self):
@@ -240,7 +253,7 @@ class BatchRenderer:
         for _ in range(4):
             check(lib().ms_batch_render(_ptr(xyz), _ptr(rgb), _ptr(alpha), self.n_fans, self.K, self.cams,
                                         self.n_views, C.byref(self.params), outs, _ptr(self.ws), self.ws.numel(),
-                                        _stream(stream)))
+                                        _stream(stream, flat, self.ws)))
             if not check_status:
                 return flat
             st, inf = self.info(stream)
@@ -298,7 +311,7 @@ class BatchRenderer:
             check(lib().ms_batch_render_backward(_ptr(xyz), _ptr(rgb), _ptr(alpha), self.n_fans, self.K, self.cams,
                                                  self.n_views, C.byref(self.params), self._ptrs(flat),
                                                  self._ptrs(dL_flat), None, None, None, _ptr(self.ws),
-                                                 self.ws.numel(), _stream(stream)))
+                                                 self.ws.numel(), _stream(stream, self.ws)))
             return None
         if d_xyz is None:
             d_xyz = torch.zeros_like(xyz)
@@ -307,7 +320,8 @@ class BatchRenderer:
         check(lib().ms_batch_render_backward(_ptr(xyz), _ptr(rgb), _ptr(alpha), self.n_fans, self.K, self.cams,
                                              self.n_views, C.byref(self.params), self._ptrs(flat),
                                              self._ptrs(dL_flat), _ptr(d_xyz), _ptr(d_rgb), _ptr(d_alpha),
-                                             _ptr(self.ws), self.ws.numel(), _stream(stream)))
+                                             _ptr(self.ws), self.ws.numel(),
+                                             _stream(stream, d_xyz, d_rgb, d_alpha, self.ws)))
         return d_xyz, d_rgb, d_alpha
 
 
@@ -335,7 +349,7 @@ class SplatRenderer(BatchRenderer):
         for _ in range(4):
             check(lib().ms_splat_render(_ptr(means), _ptr(log_scales), _ptr(quats), _ptr(opacity), _ptr(rgb),
                                         self.n_fans, self.axis_rule, self.cams, self.n_views, C.byref(self.params),
-                                        outs, _ptr(self.ws), self.ws.numel(), _stream(stream)))
+                                        outs, _ptr(self.ws), self.ws.numel(), _stream(stream, flat, self.ws)))
             st, inf = self.info(stream)
             if st == _lib.MS_ERR_CAPACITY:
                 if inf.pairs > inf.pair_capacity:
@@ -383,7 +397,7 @@ def l1_loss(img_rgba, target_rgba, stream=None):
     dL = torch.empty_like(img_rgba)
     loss = torch.empty(1, device=img_rgba.device, dtype=torch.float32)
     check(lib().ms_l1_loss(_ptr(img_rgba), _ptr(target_rgba), img_rgba.numel() // 4, _ptr(dL), _ptr(loss),
-                           _stream(stream)))
+                           _stream(stream, dL, loss)))
     return loss, dL
 
 
@@ -398,7 +412,7 @@ def fine_tune_loss(img_rgba, target_rgba, lam=0.6, workspace=None, stream=None):
     dL = torch.empty_like(img_rgba)
     loss = torch.empty(1, device=img_rgba.device, dtype=torch.float32)
     check(lib().ms_fine_tune_loss(_ptr(img_rgba), _ptr(target_rgba), H, W, float(lam), _ptr(dL), _ptr(loss),
-                                  _ptr(workspace), workspace.numel(), _stream(stream)))
+                                  _ptr(workspace), workspace.numel(), _stream(stream, dL, loss, workspace)))
     return loss, dL
 
 
@@ -416,7 +430,7 @@ def prune_fans(xyz, rgb, alpha, K, threshold=math.exp(-4.0), m=None, v=None, str
     check(lib().ms_prune_fans(_ptr(xyz), _ptr(rgb), _ptr(alpha), _ptr(m) if m is not None else None,
                               _ptr(v) if v is not None else None, n, int(K), float(threshold), *[_ptr(t) for t in outs],
                               _ptr(mo) if mo is not None else None, _ptr(vo) if vo is not None else None, _ptr(n_kept),
-                              _ptr(ws), ws.numel(), _stream(stream)))
+                              _ptr(ws), ws.numel(), _stream(stream, *outs, mo, vo, n_kept, ws)))
     if stream is not None:
         stream.synchronize()   # the count is read on the host; .item() waits on the current stream only
     k = int(n_kept.item())
@@ -430,7 +444,7 @@ def prune_fans(xyz, rgb, alpha, K, threshold=math.exp(-4.0), m=None, v=None, str
 def mse(img_rgba, target_rgba, stream=None):
     """Mean squared RGB error (1-element device tensor)."""
     out = torch.empty(1, device=img_rgba.device, dtype=torch.float32)
-    check(lib().ms_mse(_ptr(img_rgba), _ptr(target_rgba), img_rgba.numel() // 4, _ptr(out), _stream(stream)))
+    check(lib().ms_mse(_ptr(img_rgba), _ptr(target_rgba), img_rgba.numel() // 4, _ptr(out), _stream(stream, out)))
     return out
 
 
@@ -439,7 +453,7 @@ def fan_corrections(xyz0, a0, xyz1, a1, K, stream=None):
     N = xyz0.shape[0] // (K + 1)
     corr = torch.empty(N, 2 * (K + 1), device=xyz0.device, dtype=torch.float32)
     check(lib().ms_fan_corrections(_ptr(xyz0), _ptr(a0), _ptr(xyz1), _ptr(a1), N, int(K), _ptr(corr),
-                                   _stream(stream)))
+                                   _stream(stream, corr)))
     return corr
 
 
@@ -531,7 +545,7 @@ class FanMLP:
         N = log_scales.shape[0]
         X = torch.empty(N, self.N_IN, device=self.device)
         check(lib().ms_mlp_features(*self._gauss(log_scales, quats, opacity, sh, sh_degree), N, _ptr(X),
-                                    _stream(stream)))
+                                    _stream(stream, X)))
         return X
 
     def forward(self, log_scales, quats, opacity, sh, sh_degree, out=None, stream=None):
@@ -539,7 +553,7 @@ class FanMLP:
         N = log_scales.shape[0]
         corr = out if out is not None else torch.empty(N, self.n_out, device=self.device)
         check(lib().ms_mlp_forward(*self._gauss(log_scales, quats, opacity, sh, sh_degree), N, _ptr(self.packed),
-                                   self.n_out, _ptr(corr), _stream(stream)))
+                                   self.n_out, _ptr(corr), _stream(stream, corr)))
         return corr
 
     def compute_grads(self, X, T, stream=None):
@@ -549,7 +563,7 @@ class FanMLP:
         if self.ws is None or self.ws.numel() < need:
             self.ws = torch.empty(max(need, 256), dtype=torch.uint8, device=self.device)
         check(lib().ms_mlp_grads(_ptr(X), _ptr(T), n, self.n_out, _ptr(self.packed), _ptr(self.grads),
-                                 _ptr(self.loss), _ptr(self.ws), self.ws.numel(), _stream(stream)))
+                                 _ptr(self.loss), _ptr(self.ws), self.ws.numel(), _stream(stream, self.ws)))
         return self.grads, self.loss
 
     def adam(self, lr=1e-3, betas=(0.9, 0.999), eps=1e-8, stream=None):

@@ -75,3 +75,26 @@ def test_prune_without_moments_and_render_after():
     ref, _, _ = oracle.render(xyz.astype(np.float64), rgb.astype(np.float64), a.astype(np.float64), tris, cam)
     rep = err_report(img, ref)
     assert rep["n_over_tol"] == 0, rep
+
+
+def test_prune_on_a_side_stream_while_the_current_stream_is_busy():
+    """The binding orders a named stream after the current one: inputs written and
+    outputs allocated on the current stream are ready before the kernels read them, and
+    the kept count read back is the kernels' result, not the allocation's zero fill."""
+    K, n = 8, 20011
+    xyz, rgb, a, m, v = _soup(n, K, 0.3, 7)
+    d = lambda t: torch.from_numpy(np.ascontiguousarray(t)).cuda()
+    X, Cc, m_d, v_d = d(xyz), d(rgb), d(m), d(v)
+    A = torch.zeros(a.size, device="cuda")
+    big = torch.randn(4096, 4096, device="cuda")
+    for _ in range(8):                                   # keep the current stream busy ...
+        big = big @ big / 64.0
+    A.copy_(d(a))                                        # ... and write an input behind that work
+    side = torch.cuda.Stream()
+    px, pc, pa, pm, pv, k = ms.prune_fans(X, Cc, A, K, m=m_d, v=v_d, stream=side)
+    torch.cuda.synchronize()
+    _, _, oa, (om, _), fans = oracle.prune_fans(xyz, rgb, a, K, threshold=np.float32(math.exp(-4.0)),
+                                                moments=(m, v))
+    assert k == fans.size and 0 < k < n
+    assert np.array_equal(pa.cpu().numpy(), np.asarray(oa, np.float32).reshape(-1))
+    assert np.array_equal(pm.cpu().numpy(), np.asarray(om, np.float32).reshape(-1))
