@@ -38,6 +38,10 @@ def lib():
                                  C.c_int, C.c_int, C.c_int, P, P, P]
         L.orc_render_backward.argtypes = [C.c_int64, P, P, P, C.c_int64, P, P, P, C.c_int, C.c_int,
                                           C.c_int, C.c_int, C.c_int, P, P, P, P]
+        L.orc_render_ex.argtypes = [C.c_int64, P, P, P, C.c_int64, P, P, P, C.c_int, C.c_int, C.c_int,
+                                    C.c_int, C.c_int, C.c_int, C.c_int, P, P, P, P]
+        L.orc_render_backward_ex.argtypes = [C.c_int64, P, P, P, C.c_int64, P, P, P, C.c_int, C.c_int,
+                                             C.c_int, C.c_int, C.c_int, C.c_int, P, P, P, P]
         L.orc_sh_basis.argtypes = [C.c_int, P, P]
         L.orc_quat_to_rot.argtypes = [P, P]
         L.orc_fan_tris.argtypes = [C.c_int64, C.c_int32, P]
@@ -129,24 +133,50 @@ def _window(cam, window):
     return tuple(int(v) for v in window)
 
 
-def render(xyz, rgb, alpha, tris, cam, bg=(0.0, 0.0, 0.0), window=None, brute=False, nthreads=0):
-    """Returns (rgba (h, w, 4) float64, fragments per pixel (h, w) int32, culled triangle count)."""
+# Decisions (coverage, order): "fp64" the plain FP64 definition (the default); "fp32" both
+# by the binary32 formulas on binary32 projections; "rel32" coverage by the binary32
+# formulas on fan-relative rounded FP64 projections and order by the FP64 depth -- the
+# decisions the library's kernels take (see ms_oracle.c).
+DECIDE = {"fp32": 0, "fp64": 1, "rel32": 2}
+
+
+def render(xyz, rgb, alpha, tris, cam, bg=(0.0, 0.0, 0.0), window=None, brute=False, nthreads=0, decide="fp64",
+           signature=False):
+    """Returns (rgba (h, w, 4) float64, fragments per pixel (h, w) int32, culled triangle count),
+    plus per-pixel uint64 hashes of the ordered triangle ids when signature=True.  decide:
+    "fp32" takes coverage and order by the binary32 formulas, "fp64" by the plain FP64
+    definition (see ms_oracle.c)."""
     x0, y0, x1, y1 = _window(cam, window)
     out = np.zeros((max(y1 - y0, 0), max(x1 - x0, 0), 4))
     nfrag = np.zeros(out.shape[:2], np.int32)
+    sig = np.zeros(out.shape[:2], np.uint64) if signature else None
     nc = np.zeros(1, np.int64)
     xyz, rgb, alpha = _c(xyz, np.float64), _c(rgb, np.float64), _c(alpha, np.float64)
     tris = _c(tris, np.int32)
     cs = camera_struct(cam)
     bgv = _c(bg, np.float64)
-    rc = lib().orc_render(xyz.shape[0], _p(xyz), _p(rgb), _p(alpha), tris.shape[0], _p(tris), C.byref(cs),
-                          _p(bgv), x0, y0, x1, y1, int(bool(brute)), int(nthreads), _p(out), _p(nfrag), _p(nc))
+    rc = lib().orc_render_ex(xyz.shape[0], _p(xyz), _p(rgb), _p(alpha), tris.shape[0], _p(tris), C.byref(cs),
+                             _p(bgv), x0, y0, x1, y1, int(bool(brute)), int(nthreads), DECIDE[decide], _p(out),
+                             _p(nfrag), _p(sig), _p(nc))
     if rc:
         raise RuntimeError(f"orc_render failed ({rc})")
+    if signature:
+        return out, nfrag, int(nc[0]), sig
     return out, nfrag, int(nc[0])
 
 
-def render_backward(xyz, rgb, alpha, tris, cam, dL, bg=(0.0, 0.0, 0.0), window=None, nthreads=0):
+def decision_mismatch(xyz, rgb, alpha, tris, cam, window=None, nthreads=0, decide="rel32"):
+    """Renders the window with the given decisions and with FP64 decisions.  Returns (image
+    with FP64 decisions, boolean mask of the pixels whose fragment sets or order differ
+    between the two, image with the given decisions)."""
+    ia, _, _, sa = render(xyz, rgb, alpha, tris, cam, window=window, nthreads=nthreads, decide=decide,
+                          signature=True)
+    i64, _, _, s64 = render(xyz, rgb, alpha, tris, cam, window=window, nthreads=nthreads, decide="fp64",
+                            signature=True)
+    return i64, sa != s64, ia
+
+
+def render_backward(xyz, rgb, alpha, tris, cam, dL, bg=(0.0, 0.0, 0.0), window=None, nthreads=0, decide="fp64"):
     """Exact reverse pass; returns (d_xyz, d_rgb, d_alpha) in FP64."""
     x0, y0, x1, y1 = _window(cam, window)
     xyz, rgb, alpha = _c(xyz, np.float64), _c(rgb, np.float64), _c(alpha, np.float64)
@@ -157,8 +187,9 @@ def render_backward(xyz, rgb, alpha, tris, cam, dL, bg=(0.0, 0.0, 0.0), window=N
     gx, gc, ga = np.zeros((V, 3)), np.zeros((V, 3)), np.zeros(V)
     cs = camera_struct(cam)
     bgv = _c(bg, np.float64)
-    rc = lib().orc_render_backward(V, _p(xyz), _p(rgb), _p(alpha), tris.shape[0], _p(tris), C.byref(cs),
-                                   _p(bgv), x0, y0, x1, y1, int(nthreads), _p(dL), _p(gx), _p(gc), _p(ga))
+    rc = lib().orc_render_backward_ex(V, _p(xyz), _p(rgb), _p(alpha), tris.shape[0], _p(tris), C.byref(cs),
+                                      _p(bgv), x0, y0, x1, y1, int(nthreads), DECIDE[decide], _p(dL), _p(gx),
+                                      _p(gc), _p(ga))
     if rc:
         raise RuntimeError(f"orc_render_backward failed ({rc})")
     return gx, gc, ga
@@ -209,6 +240,21 @@ def adam_step(params, grads, m, v, step, lrs, betas=(0.9, 0.999), eps=1e-15):
         vh = v[i] / (1 - b2 ** step)
         p -= lrs[i] * mh / (np.sqrt(vh) + eps)
     np.clip(params[-1], 0.0, 1.0, out=params[-1])
+
+
+LR_XYZ_RATIO = float(np.exp(-3.0))   # Sec. 3: vertex positions learn at exp(-3) times lr_color
+
+
+def fan_adam_step(xyz, rgb, alpha, d_xyz, d_rgb, d_alpha, m, v, step, lr_color, betas=(0.9, 0.999), eps=1e-15):
+    """One Adam step of the fan soup as Sec. 3 ("Optimization and Pruning") sets it up:
+    colours and opacities at lr_color, vertex positions at exp(-3) lr_color, the opacity
+    clamped to [0, 1] afterwards.  xyz, rgb (V x 3) and alpha (V) are updated in place;
+    m and v are the moments in the layout [xyz 3V | rgb 3V | alpha V] (zero before step 1),
+    updated in place; step counts from 1."""
+    V = np.asarray(alpha).size
+    views = lambda t: [t[:3 * V].reshape(V, 3), t[3 * V:6 * V].reshape(V, 3), t[6 * V:7 * V]]
+    adam_step([xyz, rgb, alpha], [d_xyz, d_rgb, d_alpha], views(m), views(v), step,
+              [lr_color * LR_XYZ_RATIO, lr_color, lr_color], betas, eps)
 
 
 PRUNE_THRESHOLD = float(np.exp(-4.0))

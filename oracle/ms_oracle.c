@@ -24,10 +24,24 @@
  *   colours, C += T a c then T *= (1 - a), output RGB = C + T bg and alpha = 1 - T;
  *   triangles with a vertex at Z <= znear or beyond the +-2^17 px guard band are culled.
  *
- * Decisions.  Coverage and fragment order are decided in IEEE binary32 with
- * round-to-nearest-even and no fused multiply-add (built with -ffp-contract=off),
- * evaluating left to right exactly the expressions in decide_vertex(), tri_area2(),
- * edge_canon(), oriented_edge() and frag_depth() below.  Everything else is FP64.
+ * Decisions.  Coverage and fragment order are taken in one of two precisions:
+ *   binary32 (decide = 0): IEEE binary32 with round-to-nearest-even and no fused
+ *     multiply-add (built with -ffp-contract=off), evaluating left to right exactly the
+ *     expressions in decide_vertex(), tri_area2(), edge_canon(), oriented_edge() and
+ *     frag_depth() below;
+ *   FP64 (decide = 1): the plain definition in FP64 -- the FP64 projection of each
+ *     vertex, the three edge functions with the top-left rule, and the fragment depth
+ *     Z_f = 1 / sum_k (lambda_k / Z_k) -- in frag_depth64();
+ *   mixed (decide = 2): culling on each vertex's FP64 projection rounded to binary32
+ *     (round_vertex()); coverage by the binary32 formulas of tri_area2(), edge_canon(),
+ *     oriented_edge() and frag_depth() applied to positions relative to an integer origin
+ *     o = floor of the FP64 screen position of the triangle's first vertex (a fan's centre,
+ *     shared by all of its triangles): each vertex at the binary32 rounding of its FP64
+ *     position minus o, the pixel centre at (i + 0.5 - o.x, j + 0.5 - o.y) exactly; and the
+ *     order by the FP64 depth of value_depth() -- the split the library's kernels implement.
+ * The FP64 depth is clamped to the range of its triangle's vertex depths, where a covered
+ * centre lies; the clamp acts only where rounding puts a decided centre just outside the
+ * exact triangle.  Everything else is FP64 in every mode.
  */
 #include "ms_oracle.h"
 
@@ -273,6 +287,51 @@ static int frag_depth(const dvert *A, int64_t ia, const dvert *B, int64_t ib, co
     return 1;
 }
 
+/* FP64 decisions: the same rules without the binary32 rounding.  A vertex is valid when
+ * Z > znear and its FP64 screen position lies within the guard band; the edge value of a
+ * vertex pair is evaluated from the lower vertex index and negated for the other
+ * direction, so two triangles sharing an edge see exactly opposite values (watertight);
+ * an edge passes when E > 0, or E == 0 and it is a top or left edge (direction with
+ * ey < 0, or ey == 0 and ex > 0, in y-down screen space for the positively oriented
+ * triangle); the depth is area2 / sum_k (E_k / Z_k) = 1 / sum_k (lambda_k / Z_k). */
+typedef struct {
+    double xs, ys, Z;
+    int valid;
+} dvert64;
+
+static double tri_area2_64(const dvert64 *A, const dvert64 *B, const dvert64 *C) {
+    return (B->xs - A->xs) * (C->ys - A->ys) - (B->ys - A->ys) * (C->xs - A->xs);
+}
+
+static int oriented_edge64(const dvert64 *vu, int64_t iu, const dvert64 *vv, int64_t iv,
+                           double px, double py, double *E) {
+    const dvert64 *lo = iu < iv ? vu : vv, *hi = iu < iv ? vv : vu;
+    double e = (hi->xs - lo->xs) * (py - lo->ys) - (hi->ys - lo->ys) * (px - lo->xs);
+    double ex = vv->xs - vu->xs, ey = vv->ys - vu->ys;
+    if (!(iu < iv)) e = -e;
+    *E = e;
+    return e > 0.0 || (e == 0.0 && (ey < 0.0 || (ey == 0.0 && ex > 0.0)));
+}
+
+static int frag_depth64(const dvert64 *A, int64_t ia, const dvert64 *B, int64_t ib, const dvert64 *C,
+                        int64_t ic, double area2, double px, double py, double *Zf) {
+    const dvert64 *P0 = A, *P1 = B, *P2 = C;
+    int64_t i0 = ia, i1 = ib, i2 = ic;
+    if (area2 < 0.0) {
+        P1 = C; i1 = ic;
+        P2 = B; i2 = ib;
+        area2 = -area2;
+    }
+    double E0, E1, E2;
+    if (!oriented_edge64(P1, i1, P2, i2, px, py, &E0)) return 0;
+    if (!oriented_edge64(P2, i2, P0, i0, px, py, &E1)) return 0;
+    if (!oriented_edge64(P0, i0, P1, i1, px, py, &E2)) return 0;
+    double z = area2 / (E0 / P0->Z + E1 / P1->Z + E2 / P2->Z);
+    double zlo = fmin(fmin(A->Z, B->Z), C->Z), zhi = fmax(fmax(A->Z, B->Z), C->Z);
+    *Zf = fmin(fmax(z, zlo), zhi);
+    return 1;
+}
+
 /* ------------------------------------------------------------------------------------ */
 /* Values (FP64)                                                                        */
 /* ------------------------------------------------------------------------------------ */
@@ -308,6 +367,16 @@ static void persp_bary(const vvert *A, const vvert *B, const vvert *C, double px
     *Wsum = W;
 }
 
+/* FP64 depth of pixel centre p on triangle (A,B,C): 1 / sum_k (lambda_k / Z_k) with
+ * lambda_k = E_k / area2 (orientation cancels), clamped to the vertices' depth range. */
+static double value_depth(const vvert *A, const vvert *B, const vvert *C, double px, double py) {
+    double E[3], mu[3], W;
+    persp_bary(A, B, C, px, py, E, mu, &W);
+    double z = (E[0] + E[1] + E[2]) / W;
+    double zlo = fmin(fmin(A->Z, B->Z), C->Z), zhi = fmax(fmax(A->Z, B->Z), C->Z);
+    return fmin(fmax(z, zlo), zhi);
+}
+
 /* Per-vertex projection as seen by the renderer: decided binary32 screen position and
  * depth (dec[4] = xs, ys, Z, valid) and the FP64 values (val[3] = xs, ys, Z). */
 void orc_project(const orc_camera *cam, const double p[3], float dec[4], double val[3]) {
@@ -325,7 +394,7 @@ void orc_project(const orc_camera *cam, const double p[3], float dec[4], double 
 
 typedef struct {
     int32_t pix;   /* index within the band */
-    float z;
+    double z;      /* decided depth (a binary32 value in binary32 mode) */
     int64_t tri;
 } frag;
 
@@ -334,7 +403,7 @@ typedef struct {
     size_t n, cap;
 } fragvec;
 
-static int fv_push(fragvec *v, int32_t pix, float z, int64_t tri) {
+static int fv_push(fragvec *v, int32_t pix, double z, int64_t tri) {
     if (v->n == v->cap) {
         size_t nc = v->cap ? v->cap * 2 : 4096;
         frag *nf = (frag *)realloc(v->f, nc * sizeof(frag));
@@ -346,6 +415,37 @@ static int fv_push(fragvec *v, int32_t pix, float z, int64_t tri) {
     v->f[v->n].z = z;
     v->f[v->n].tri = tri;
     v->n++;
+    return 0;
+}
+
+/* Gradient contributions of one worker, (vertex, dxyz[3], drgb[3], dalpha) per entry,
+ * summed into the caller's arrays in worker order once all workers are done. */
+typedef struct {
+    int64_t v;
+    double g[7];
+} gradent;
+
+typedef struct {
+    gradent *e;
+    size_t n, cap;
+} gradvec;
+
+/* Appends three zeroed entries for the vertices of one triangle (one allocation step, so
+ * the three pointers stay valid together). */
+static int gv_add3(gradvec *v, const int64_t vid[3], double *out[3]) {
+    if (v->n + 3 > v->cap) {
+        size_t nc = v->cap ? v->cap * 2 : 4096;
+        gradent *ne = (gradent *)realloc(v->e, nc * sizeof(gradent));
+        if (!ne) return 1;
+        v->e = ne;
+        v->cap = nc;
+    }
+    for (int k = 0; k < 3; ++k) {
+        gradent *g = &v->e[v->n++];
+        g->v = vid[k];
+        for (int i = 0; i < 7; ++i) g->g[i] = 0.0;
+        out[k] = g->g;
+    }
     return 0;
 }
 
@@ -365,6 +465,8 @@ typedef struct {
     const orc_camera *cam;
     const double *bg;
     const dvert *dv;
+    const dvert64 *dv64;    /* FP64 coverage when non-NULL */
+    int order64;            /* binary32 coverage: order by the FP64 depth */
     const vvert *vv;
     int x0, x1, by0, by1, brute;
     /* forward outputs */
@@ -372,23 +474,74 @@ typedef struct {
     int32_t *out_nfrag;
     int wx0, wy0, ww;       /* window origin and width for output indexing */
     /* backward */
+    uint64_t *out_sig;      /* per pixel: hash of the ordered triangle ids (optional) */
     const double *dL;
-    double *g;              /* V x 7 accumulator (xyz, rgb, alpha) for this worker */
+    gradvec gl;             /* backward: this worker's per-(fragment, vertex) contributions */
     int err;
 } band_job;
 
-static int collect(band_job *j, fragvec *fv) {
+/* collect() in FP64 decisions. */
+static int collect64(band_job *j, fragvec *fv) {
     int bw = j->x1 - j->x0;
     for (int64_t t = 0; t < j->T; ++t) {
         int64_t ia = j->tris[3 * t], ib = j->tris[3 * t + 1], ic = j->tris[3 * t + 2];
-        const dvert *A = &j->dv[ia], *B = &j->dv[ib], *C = &j->dv[ic];
+        const dvert64 *A = &j->dv64[ia], *B = &j->dv64[ib], *C = &j->dv64[ic];
         if (!(A->valid && B->valid && C->valid)) continue;
+        double area2 = tri_area2_64(A, B, C);
+        if (!(area2 != 0.0)) continue;
+        int px0 = j->x0, px1 = j->x1 - 1, py0 = j->by0, py1 = j->by1 - 1;
+        if (!j->brute) {
+            double mnx = fmin(fmin(A->xs, B->xs), C->xs), mxx = fmax(fmax(A->xs, B->xs), C->xs);
+            double mny = fmin(fmin(A->ys, B->ys), C->ys), mxy = fmax(fmax(A->ys, B->ys), C->ys);
+            int bx0 = (int)floor(mnx) - 2, bx1 = (int)floor(mxx) + 2;
+            int by0 = (int)floor(mny) - 2, by1 = (int)floor(mxy) + 2;
+            if (bx0 > px0) px0 = bx0;
+            if (bx1 < px1) px1 = bx1;
+            if (by0 > py0) py0 = by0;
+            if (by1 < py1) py1 = by1;
+        }
+        for (int py = py0; py <= py1; ++py)
+            for (int px = px0; px <= px1; ++px) {
+                double zf;
+                if (frag_depth64(A, ia, B, ib, C, ic, area2, px + 0.5, py + 0.5, &zf))
+                    if (fv_push(fv, (py - j->by0) * bw + (px - j->x0), zf, t)) return 1;
+            }
+    }
+    qsort(fv->f, fv->n, sizeof(frag), frag_cmp);
+    return 0;
+}
+
+/* Mixed mode: a vertex relative to the integer origin (ox, oy), rounded to binary32. */
+static dvert rel_vertex(const dvert *d, const vvert *w, double ox, double oy) {
+    dvert r = *d;
+    r.xs = (float)(w->xs - ox);
+    r.ys = (float)(w->ys - oy);
+    return r;
+}
+
+static int collect(band_job *j, fragvec *fv) {
+    if (j->dv64) return collect64(j, fv);
+    int bw = j->x1 - j->x0;
+    for (int64_t t = 0; t < j->T; ++t) {
+        int64_t ia = j->tris[3 * t], ib = j->tris[3 * t + 1], ic = j->tris[3 * t + 2];
+        const dvert *A0 = &j->dv[ia], *B0 = &j->dv[ib], *C0 = &j->dv[ic];
+        if (!(A0->valid && B0->valid && C0->valid)) continue;
+        double ox = 0.0, oy = 0.0;
+        dvert Ar = *A0, Br = *B0, Cr = *C0;
+        if (j->order64) {
+            ox = floor(j->vv[ia].xs);
+            oy = floor(j->vv[ia].ys);
+            Ar = rel_vertex(A0, &j->vv[ia], ox, oy);
+            Br = rel_vertex(B0, &j->vv[ib], ox, oy);
+            Cr = rel_vertex(C0, &j->vv[ic], ox, oy);
+        }
+        const dvert *A = &Ar, *B = &Br, *C = &Cr;
         float area2 = tri_area2(A, B, C);
         if (!(area2 != 0.0f)) continue;
         int px0 = j->x0, px1 = j->x1 - 1, py0 = j->by0, py1 = j->by1 - 1;
         if (!j->brute) {
-            float mnx = fminf(fminf(A->xs, B->xs), C->xs), mxx = fmaxf(fmaxf(A->xs, B->xs), C->xs);
-            float mny = fminf(fminf(A->ys, B->ys), C->ys), mxy = fmaxf(fmaxf(A->ys, B->ys), C->ys);
+            float mnx = fminf(fminf(A0->xs, B0->xs), C0->xs), mxx = fmaxf(fmaxf(A0->xs, B0->xs), C0->xs);
+            float mny = fminf(fminf(A0->ys, B0->ys), C0->ys), mxy = fmaxf(fmaxf(A0->ys, B0->ys), C0->ys);
             int bx0 = (int)floorf(mnx) - 2, bx1 = (int)floorf(mxx) + 2;
             int by0 = (int)floorf(mny) - 2, by1 = (int)floorf(mxy) + 2;
             if (bx0 > px0) px0 = bx0;
@@ -399,8 +552,12 @@ static int collect(band_job *j, fragvec *fv) {
         for (int py = py0; py <= py1; ++py)
             for (int px = px0; px <= px1; ++px) {
                 float zf;
-                if (frag_depth(A, ia, B, ib, C, ic, area2, (float)px + 0.5f, (float)py + 0.5f, &zf))
-                    if (fv_push(fv, (py - j->by0) * bw + (px - j->x0), zf, t)) return 1;
+                if (frag_depth(A, ia, B, ib, C, ic, area2, (float)(px - ox) + 0.5f, (float)(py - oy) + 0.5f,
+                               &zf)) {
+                    double z = j->order64 ? value_depth(&j->vv[ia], &j->vv[ib], &j->vv[ic], px + 0.5, py + 0.5)
+                                          : (double)zf;
+                    if (fv_push(fv, (py - j->by0) * bw + (px - j->x0), z, t)) return 1;
+                }
             }
     }
     qsort(fv->f, fv->n, sizeof(frag), frag_cmp);
@@ -432,7 +589,12 @@ static void *fwd_worker(void *arg) {
             int32_t pix = (py - j->by0) * bw + (px - j->x0);
             double T = 1.0, C[3] = {0, 0, 0};
             int32_t n = 0;
+            uint64_t h = 1469598103934665603ull;   /* FNV-1a over the ordered triangle ids */
             while (i < fv.n && fv.f[i].pix == pix) {
+                for (int b = 0; b < 8; ++b) {
+                    h ^= (uint64_t)(((uint64_t)fv.f[i].tri >> (8 * b)) & 0xff);
+                    h *= 1099511628211ull;
+                }
                 double mu[3], E[3], W, c[3], a;
                 frag_value(j, fv.f[i].tri, px + 0.5, py + 0.5, mu, E, &W, c, &a);
                 for (int ch = 0; ch < 3; ++ch) C[ch] += T * a * c[ch];
@@ -444,6 +606,7 @@ static void *fwd_worker(void *arg) {
             for (int ch = 0; ch < 3; ++ch) j->out_rgba[o + ch] = C[ch] + T * j->bg[ch];
             j->out_rgba[o + 3] = 1.0 - T;
             if (j->out_nfrag) j->out_nfrag[(size_t)(py - j->wy0) * j->ww + (px - j->wx0)] = n;
+            if (j->out_sig) j->out_sig[(size_t)(py - j->wy0) * j->ww + (px - j->wx0)] = h;
         }
     free(fv.f);
     return 0;
@@ -479,9 +642,11 @@ static void pixel_backward(band_job *j, const frag *fl, int n, int px, int py) {
 
         int64_t t = fl[f].tri;
         int64_t id[3] = {j->tris[3 * t], j->tris[3 * t + 1], j->tris[3 * t + 2]};
+        double *gvk[3];
+        if (gv_add3(&j->gl, id, gvk)) { j->err = 3; return; }
         double gmu[3];
         for (int k = 0; k < 3; ++k) {
-            double *gv = j->g + 7 * id[k];
+            double *gv = gvk[k];
             gmu[k] = da * j->alpha[id[k]];
             for (int ch = 0; ch < 3; ++ch) {
                 gv[3 + ch] += muf[f][k] * dc[ch];
@@ -515,7 +680,7 @@ static void pixel_backward(band_job *j, const frag *fl, int n, int px, int py) {
             double gX = gx[k] * cam->fx / P->Z;
             double gY = gy[k] * cam->fy / P->Z;
             double gZv = gZ[k] - gx[k] * cam->fx * P->X / (P->Z * P->Z) - gy[k] * cam->fy * P->Y / (P->Z * P->Z);
-            double *gv = j->g + 7 * id[k];
+            double *gv = gvk[k];
             for (int r = 0; r < 3; ++r)
                 gv[r] += (double)cam->R_cw[r] * gX + (double)cam->R_cw[3 + r] * gY + (double)cam->R_cw[6 + r] * gZv;
         }
@@ -547,52 +712,77 @@ typedef struct {
     const orc_camera *cam;
     const double *xyz;
     dvert *dv;
+    dvert64 *dv64;
     vvert *vv;
     int64_t v0, v1;
+    int rounded;            /* decided vertices from the rounded FP64 projection */
 } vert_job;
+
+/* Decided vertex of the mixed mode: the FP64 screen position and depth rounded to
+ * binary32 (round to nearest), 1/Z of the rounded depth, validity on the rounded values. */
+static void round_vertex(const orc_camera *cam, const vvert *w, dvert *o) {
+    o->xs = (float)w->xs;
+    o->ys = (float)w->ys;
+    o->Z = (float)w->Z;
+    o->iz = 1.0f / o->Z;
+    o->valid = (o->Z > cam->znear) && (fabsf(o->xs) <= GUARD_PX) && (fabsf(o->ys) <= GUARD_PX);
+}
 
 static void *vert_worker(void *arg) {
     vert_job *j = (vert_job *)arg;
     for (int64_t v = j->v0; v < j->v1; ++v) {
         const double *p = j->xyz + 3 * v;
-        decide_vertex(j->cam, (float)p[0], (float)p[1], (float)p[2], &j->dv[v]);
         value_vertex(j->cam, p, &j->vv[v]);
+        if (j->rounded)
+            round_vertex(j->cam, &j->vv[v], &j->dv[v]);
+        else
+            decide_vertex(j->cam, (float)p[0], (float)p[1], (float)p[2], &j->dv[v]);
+        if (j->dv64) {
+            const vvert *w = &j->vv[v];
+            dvert64 *d = &j->dv64[v];
+            d->xs = w->xs;
+            d->ys = w->ys;
+            d->Z = w->Z;
+            d->valid = (w->Z > (double)j->cam->znear) && (fabs(w->xs) <= (double)GUARD_PX) &&
+                       (fabs(w->ys) <= (double)GUARD_PX);
+        }
     }
     return 0;
 }
 
 static int run_pass(int64_t V, const double *xyz, const double *rgb, const double *alpha,
                     int64_t T, const int32_t *tris, const orc_camera *cam, const double bg[3],
-                    int x0, int y0, int x1, int y1, int brute, int nthreads,
-                    double *out_rgba, int32_t *out_nfrag, int64_t *n_culled,
+                    int x0, int y0, int x1, int y1, int brute, int nthreads, int decide,
+                    double *out_rgba, int32_t *out_nfrag, uint64_t *out_sig, int64_t *n_culled,
                     const double *dL, double *d_xyz, double *d_rgb, double *d_alpha) {
     if (x1 <= x0 || y1 <= y0) return 0;
+    if (decide < 0 || decide > 2) return 4;
+    const int decide64 = decide == 1;
     int nt = resolve_threads(nthreads);
     int backward = dL != 0;
-    if (backward) {
-        /* one V x 7 accumulator per worker; keep the total under ~2 GB */
-        double per = (double)V * 7 * 8;
-        int cap = per > 0 ? (int)(2.0e9 / per) : nt;
-        if (cap < 1) cap = 1;
-        if (nt > cap) nt = cap;
-    }
     if (nt > y1 - y0) nt = y1 - y0;
     g_last_threads = nt;
     dvert *dv = (dvert *)malloc(sizeof(dvert) * (V > 0 ? V : 1));
     vvert *vv = (vvert *)malloc(sizeof(vvert) * (V > 0 ? V : 1));
-    if (!dv || !vv) { free(dv); free(vv); return 3; }
+    dvert64 *dv64 = decide64 ? (dvert64 *)malloc(sizeof(dvert64) * (V > 0 ? V : 1)) : 0;
+    if (!dv || !vv || (decide64 && !dv64)) { free(dv); free(vv); free(dv64); return 3; }
     pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * nt);
     vert_job *vj = (vert_job *)malloc(sizeof(vert_job) * nt);
     for (int i = 0; i < nt; ++i) {
-        vj[i].cam = cam; vj[i].xyz = xyz; vj[i].dv = dv; vj[i].vv = vv;
+        vj[i].cam = cam; vj[i].xyz = xyz; vj[i].dv = dv; vj[i].dv64 = dv64; vj[i].vv = vv;
         vj[i].v0 = V * i / nt; vj[i].v1 = V * (i + 1) / nt;
+        vj[i].rounded = decide == 2;
         pthread_create(&th[i], 0, vert_worker, &vj[i]);
     }
     for (int i = 0; i < nt; ++i) pthread_join(th[i], 0);
     if (n_culled) {
         int64_t c = 0;
-        for (int64_t t = 0; t < T; ++t)
-            if (!(dv[tris[3 * t]].valid && dv[tris[3 * t + 1]].valid && dv[tris[3 * t + 2]].valid)) ++c;
+        for (int64_t t = 0; t < T; ++t) {
+            int64_t a = tris[3 * t], b = tris[3 * t + 1], cc = tris[3 * t + 2];
+            int ok = decide64 ? (dv64[a].valid && dv64[b].valid && dv64[cc].valid)
+                              : (dv[a].valid && dv[b].valid && dv[cc].valid);
+            if (!ok) ++c;
+        }
         *n_culled = c;
     }
     band_job *bj = (band_job *)calloc(nt, sizeof(band_job));
@@ -600,50 +790,62 @@ static int run_pass(int64_t V, const double *xyz, const double *rgb, const doubl
     for (int i = 0; i < nt; ++i) {
         band_job *j = &bj[i];
         j->V = V; j->T = T; j->xyz = xyz; j->rgb = rgb; j->alpha = alpha; j->tris = tris;
-        j->cam = cam; j->bg = bg; j->dv = dv; j->vv = vv;
+        j->cam = cam; j->bg = bg; j->dv = dv; j->dv64 = dv64; j->vv = vv; j->order64 = decide == 2;
         j->x0 = x0; j->x1 = x1; j->brute = brute;
         j->by0 = y0 + (int)((int64_t)(y1 - y0) * i / nt);
         j->by1 = y0 + (int)((int64_t)(y1 - y0) * (i + 1) / nt);
-        j->out_rgba = out_rgba; j->out_nfrag = out_nfrag;
+        j->out_rgba = out_rgba; j->out_nfrag = out_nfrag; j->out_sig = out_sig;
         j->wx0 = x0; j->wy0 = y0; j->ww = x1 - x0;
         j->dL = dL;
-        if (backward) {
-            j->g = (double *)calloc((size_t)(V > 0 ? V : 1) * 7, sizeof(double));
-            if (!j->g) err = 3;
-        }
     }
-    if (!err) {
-        for (int i = 0; i < nt; ++i) pthread_create(&th[i], 0, backward ? bwd_worker : fwd_worker, &bj[i]);
-        for (int i = 0; i < nt; ++i) pthread_join(th[i], 0);
-        for (int i = 0; i < nt; ++i)
-            if (bj[i].err) err = bj[i].err;
-    }
+    for (int i = 0; i < nt; ++i) pthread_create(&th[i], 0, backward ? bwd_worker : fwd_worker, &bj[i]);
+    for (int i = 0; i < nt; ++i) pthread_join(th[i], 0);
+    for (int i = 0; i < nt; ++i)
+        if (bj[i].err) err = bj[i].err;
     if (backward && !err) {
+        /* contributions summed in band order, then fragment order: deterministic */
         for (int i = 0; i < nt; ++i)
-            for (int64_t v = 0; v < V; ++v) {
-                const double *g = bj[i].g + 7 * v;
-                for (int r = 0; r < 3; ++r) d_xyz[3 * v + r] += g[r];
-                for (int r = 0; r < 3; ++r) d_rgb[3 * v + r] += g[3 + r];
-                d_alpha[v] += g[6];
+            for (size_t e = 0; e < bj[i].gl.n; ++e) {
+                const gradent *g = &bj[i].gl.e[e];
+                int64_t v = g->v;
+                for (int r = 0; r < 3; ++r) d_xyz[3 * v + r] += g->g[r];
+                for (int r = 0; r < 3; ++r) d_rgb[3 * v + r] += g->g[3 + r];
+                d_alpha[v] += g->g[6];
             }
     }
-    for (int i = 0; i < nt; ++i) free(bj[i].g);
-    free(bj); free(vj); free(th); free(dv); free(vv);
+    for (int i = 0; i < nt; ++i) free(bj[i].gl.e);
+    free(bj); free(vj); free(th); free(dv); free(vv); free(dv64);
     return err;
+}
+
+int orc_render_ex(int64_t V, const double *xyz, const double *rgb, const double *alpha,
+                  int64_t T, const int32_t *tris, const orc_camera *cam, const double bg[3],
+                  int x0, int y0, int x1, int y1, int brute, int nthreads, int decide,
+                  double *out_rgba, int32_t *out_nfrag, uint64_t *out_sig, int64_t *n_culled) {
+    return run_pass(V, xyz, rgb, alpha, T, tris, cam, bg, x0, y0, x1, y1, brute, nthreads, decide,
+                    out_rgba, out_nfrag, out_sig, n_culled, 0, 0, 0, 0);
 }
 
 int orc_render(int64_t V, const double *xyz, const double *rgb, const double *alpha,
                int64_t T, const int32_t *tris, const orc_camera *cam, const double bg[3],
                int x0, int y0, int x1, int y1, int brute, int nthreads,
                double *out_rgba, int32_t *out_nfrag, int64_t *n_culled) {
-    return run_pass(V, xyz, rgb, alpha, T, tris, cam, bg, x0, y0, x1, y1, brute, nthreads,
-                    out_rgba, out_nfrag, n_culled, 0, 0, 0, 0);
+    return orc_render_ex(V, xyz, rgb, alpha, T, tris, cam, bg, x0, y0, x1, y1, brute, nthreads, 0,
+                         out_rgba, out_nfrag, 0, n_culled);
+}
+
+int orc_render_backward_ex(int64_t V, const double *xyz, const double *rgb, const double *alpha,
+                           int64_t T, const int32_t *tris, const orc_camera *cam, const double bg[3],
+                           int x0, int y0, int x1, int y1, int nthreads, int decide,
+                           const double *dL_drgba, double *d_xyz, double *d_rgb, double *d_alpha) {
+    return run_pass(V, xyz, rgb, alpha, T, tris, cam, bg, x0, y0, x1, y1, 0, nthreads, decide,
+                    0, 0, 0, 0, dL_drgba, d_xyz, d_rgb, d_alpha);
 }
 
 int orc_render_backward(int64_t V, const double *xyz, const double *rgb, const double *alpha,
                         int64_t T, const int32_t *tris, const orc_camera *cam, const double bg[3],
                         int x0, int y0, int x1, int y1, int nthreads,
                         const double *dL_drgba, double *d_xyz, double *d_rgb, double *d_alpha) {
-    return run_pass(V, xyz, rgb, alpha, T, tris, cam, bg, x0, y0, x1, y1, 0, nthreads,
-                    0, 0, 0, dL_drgba, d_xyz, d_rgb, d_alpha);
+    return orc_render_backward_ex(V, xyz, rgb, alpha, T, tris, cam, bg, x0, y0, x1, y1, nthreads, 0,
+                                  dL_drgba, d_xyz, d_rgb, d_alpha);
 }

@@ -9,9 +9,13 @@
  * attributes, compositing, gradients) is computed in FP64 from exactly widened
  * FP32/BF16 inputs.  The two discrete decisions of the renderer -- whether a pixel
  * centre is covered by a triangle, and the front-to-back order of the fragments of
- * a pixel -- are taken in IEEE FP32 by the formulas written out in ms_oracle.c
- * (section "Decisions"), the same formulas the GPU kernels evaluate, so that both
- * sides take each decision in the same precision.
+ * a pixel -- are taken in one of three ways (`decide`): 1, the plain definition in
+ * FP64; 0, both in IEEE FP32 by the formulas written out in ms_oracle.c (section
+ * "Decisions"); 2, coverage by those binary32 edge formulas on the vertices' FP64
+ * projections rounded to binary32, and the order by the FP64 depth (the split the
+ * library's header states for its kernels), so that both sides can take each decision
+ * in the same precision.  Comparing the modes pixel by pixel measures what
+ * deciding in binary32 changes.
  */
 #ifndef MS_ORACLE_H
 #define MS_ORACLE_H
@@ -76,6 +80,17 @@ int orc_render(int64_t V, const double *xyz, const double *rgb, const double *al
                double *out_rgba, int32_t *out_nfrag, int64_t *n_culled);
 
 /*
+ * orc_render with the decisions chosen (decide: 0 binary32, 1 FP64, 2 binary32 coverage
+ * and FP64 order; any other value returns 4) and, when
+ * out_sig is non-NULL, a 64-bit FNV-1a hash per pixel of its ordered list of triangle ids
+ * (the pixel's decisions: equal hashes mean the same fragments in the same order).
+ */
+int orc_render_ex(int64_t V, const double *xyz, const double *rgb, const double *alpha,
+                  int64_t T, const int32_t *tris, const orc_camera *cam, const double bg[3],
+                  int x0, int y0, int x1, int y1, int brute, int nthreads, int decide,
+                  double *out_rgba, int32_t *out_nfrag, uint64_t *out_sig, int64_t *n_culled);
+
+/*
  * Exact reverse pass of orc_render over the full fragment lists (no early
  * termination).  dL_drgba has the window's shape; gradients ACCUMULATE into
  * d_xyz (V x 3), d_rgb (V x 3), d_alpha (V).  Coverage and order are held fixed.
@@ -84,6 +99,12 @@ int orc_render_backward(int64_t V, const double *xyz, const double *rgb, const d
                         int64_t T, const int32_t *tris, const orc_camera *cam, const double bg[3],
                         int x0, int y0, int x1, int y1, int nthreads,
                         const double *dL_drgba, double *d_xyz, double *d_rgb, double *d_alpha);
+
+/* orc_render_backward with the decision precision chosen as in orc_render_ex. */
+int orc_render_backward_ex(int64_t V, const double *xyz, const double *rgb, const double *alpha,
+                           int64_t T, const int32_t *tris, const orc_camera *cam, const double bg[3],
+                           int x0, int y0, int x1, int y1, int nthreads, int decide,
+                           const double *dL_drgba, double *d_xyz, double *d_rgb, double *d_alpha);
 
 /*
  * Source-Gaussian render (ms_oracle_splat.c): the scene's flat Gaussians drawn as

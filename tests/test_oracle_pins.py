@@ -207,20 +207,24 @@ def test_camera_principal_point_and_fov_edge():
 # Coverage: top-left rule, watertightness, brute force (Sec. 3 rasterisation)
 # --------------------------------------------------------------------------------------
 
-def _render_2d(verts2d, tris, w=16, h=16, rgb=None, alpha=None, z=None):
+DECISIONS = ("fp64", "rel32", "fp32")   # every decision mode of the oracle obeys the coverage pins
+
+
+def _render_2d(verts2d, tris, w=16, h=16, rgb=None, alpha=None, z=None, decide="fp64"):
     V = len(verts2d)
     zz = np.ones(V) if z is None else np.asarray(z, np.float64)
     xyz = np.array([[x * zz[i], y * zz[i], zz[i]] for i, (x, y) in enumerate(verts2d)])
     rgb = np.ones((V, 3)) if rgb is None else rgb
     alpha = np.full(V, 0.5) if alpha is None else alpha
-    return oracle.render(xyz, rgb, alpha, np.asarray(tris, np.int32), flat_camera(w, h), brute=True)
+    return oracle.render(xyz, rgb, alpha, np.asarray(tris, np.int32), flat_camera(w, h), brute=True, decide=decide)
 
 
-def test_top_left_rule_square():
+@pytest.mark.parametrize("decide", DECISIONS)
+def test_top_left_rule_square(decide):
     # square [2.5, 10.5]^2 from two triangles: the top and left edges own their pixel centres
     v = [(2.5, 2.5), (10.5, 2.5), (10.5, 10.5), (2.5, 10.5)]
     for tris in ([[0, 1, 2], [0, 2, 3]], [[1, 2, 3], [1, 3, 0]], [[0, 2, 1], [3, 2, 0]]):
-        _, nf, _ = _render_2d(v, tris)
+        _, nf, _ = _render_2d(v, tris, decide=decide)
         want = np.zeros((16, 16), np.int32)
         want[2:10, 2:10] = 1
         assert np.array_equal(nf, want)
@@ -230,7 +234,8 @@ def _fraction_side(a, b, p):
     return (b[0] - a[0]) * (p[1] - a[1]) - (b[1] - a[1]) * (p[0] - a[0])
 
 
-def test_fan_watertight_exact_ties():
+@pytest.mark.parametrize("decide", DECISIONS)
+def test_fan_watertight_exact_ties(decide):
     """A fan whose spokes and rims pass exactly through pixel centres: every centre
     inside is covered once, including the shared centre vertex."""
     c = (8.5, 8.5)
@@ -239,7 +244,7 @@ def test_fan_watertight_exact_ties():
     verts = [c] + ring
     tris = [[0, 1 + j, 1 + (j + 1) % K] for j in range(K)]
     for order in (tris, [[t[0], t[2], t[1]] for t in tris]):
-        _, nf, _ = _render_2d(verts, order)
+        _, nf, _ = _render_2d(verts, order, decide=decide)
         F = [(Fraction(x), Fraction(y)) for x, y in ring]
         # orientation: interior where the edge function is positive
         sgn = 1 if _fraction_side(F[0], F[1], (Fraction(c[0]), Fraction(c[1]))) > 0 else -1
@@ -262,23 +267,25 @@ def test_fan_watertight_exact_ties():
                 assert nf[py, px] == want, (px, py)
 
 
-def test_brute_force_equals_bbox_mode():
+@pytest.mark.parametrize("decide", DECISIONS)
+def test_brute_force_equals_bbox_mode(decide):
     w = synthetic.workload(1, n=300)
     xyz, rgb, a = oracle.mesh_build(w.scene, K=8, cam_center=w.cameras[0].C)
     tris = oracle.fan_tris(w.scene.n, 8)
     xyz = xyz.astype(np.float32)
-    r1, n1, _ = oracle.render(xyz, rgb, a, tris, w.cameras[0], brute=True)
-    r2, n2, _ = oracle.render(xyz, rgb, a, tris, w.cameras[0], brute=False, nthreads=3)
+    r1, n1, _ = oracle.render(xyz, rgb, a, tris, w.cameras[0], brute=True, decide=decide)
+    r2, n2, _ = oracle.render(xyz, rgb, a, tris, w.cameras[0], brute=False, nthreads=3, decide=decide)
     assert np.array_equal(n1, n2)
     assert np.array_equal(r1, r2)
 
 
-def test_fronto_parallel_fan_pixel_count_matches_area():
+@pytest.mark.parametrize("decide", DECISIONS)
+def test_fronto_parallel_fan_pixel_count_matches_area(decide):
     K = 8
     sc = one_gaussian([0, 0, 0], [math.log(0.4), math.log(0.3), -8.0], [1, 0, 0, 0], sigma=0.5)
     cam = synthetic.make_camera((0.0, 0.0, 4.0), 256, 256)
     xyz, rgb, a = oracle.mesh_build(sc, K=K, axis_rule=1)
-    _, nf, _ = oracle.render(xyz.astype(np.float32), rgb, a, oracle.fan_tris(1, K), cam)
+    _, nf, _ = oracle.render(xyz.astype(np.float32), rgb, a, oracle.fan_tris(1, K), cam, decide=decide)
     s = cam.fy / 4.0
     r1, r2 = 2.7 * 0.4 * s, 2.7 * 0.3 * s
     area = 0.5 * K * r1 * r2 * math.sin(2 * math.pi / K)
