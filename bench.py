@@ -246,11 +246,13 @@ def stage_report(stage_ms, stage_n, info, sc, V, K, npx, local):
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     n_sm = torch.cuda.get_device_properties(local).multi_processor_count
     alu_peak = n_sm * 128 * sm_max * 1e6 / 1e12           # FP32 lane-ops per second, TOP/s
+    # the method's coverage work counted once (the count pass that sizes the fragment
+    # buffer re-derives it, an implementation choice that is not counted)
     cov_ops = info.rect_tests * 10 * K + info.fragments * 40
     # backward: per composited fragment ~35 lane-ops of adjoint compositing and ~385 of the
     # chain to the vertices (double-float centre projection, two vertex offsets,
     # barycentrics and their adjoint); no coverage work
-    comp_ops = {"raster": 2 * cov_ops, "raster_bwd": info.commits * 420}
+    comp_ops = {"raster": cov_ops, "raster_bwd": info.commits * 420}
     tc_flops = {"mlp": sc.n * MLP_FLOPS_PER_ROW}
     tc_peak = float(peaks.get("bf16_tflops", 1900.0))
     nb = (sc.sh_degree + 1) ** 2 * 3 * (2 if sc.sh_bf16 else 4)

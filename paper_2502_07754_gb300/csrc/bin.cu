@@ -14,6 +14,7 @@ namespace ms {
 namespace {
 
 constexpr int kBinThreads = 256;
+constexpr float kKeyMargin = 1.0f - 0x1p-20f;
 
 struct BinArgs {
     const float *xyz;
@@ -80,9 +81,14 @@ __global__ void __launch_bounds__(kBinThreads) bin_kernel(const __grid_constant_
         uint32_t vmask = 0;
         float mnx = 3.0e38f, mxx = -3.0e38f, mny = 3.0e38f, mxy = -3.0e38f, zmin = 3.0e38f;
         float4 *dec = a.dec + (size_t)view * a.V + (size_t)(f0 + tid) * KV;
+        // the fan's integer origin: the floor of its centre's exact screen position
+        const DfVert c0 = df_project(cam, p[0], p[1], p[2]);
+        const float ox = df_floor(c0.x), oy = df_floor(c0.y);
         for (int k = 0; k < KV; ++k) {
-            const DVert d = decide_vertex(cam, p[3 * k], p[3 * k + 1], p[3 * k + 2]);
-            dec[k] = make_float4(d.xs, d.ys, d.Z, d.iz);
+            const DVert d = decide_vertex(cam, k == 0 ? c0 : df_project(cam, p[3 * k], p[3 * k + 1], p[3 * k + 2]),
+                                          ox, oy);
+            // (xr, yr, Z or -1 if invalid, the origin's x / y in the first two vertices)
+            dec[k] = make_float4(d.xr, d.yr, d.valid ? d.Z : -1.0f, k == 0 ? ox : (k == 1 ? oy : 0.0f));
             if (d.valid) vmask |= 1u << k;
             mnx = fminf(mnx, d.xs); mxx = fmaxf(mxx, d.xs);
             mny = fminf(mny, d.ys); mxy = fmaxf(mxy, d.ys);
@@ -93,7 +99,7 @@ __global__ void __launch_bounds__(kBinThreads) bin_kernel(const __grid_constant_
             mnx = 3.0e38f; mxx = -3.0e38f; mny = 3.0e38f; mxy = -3.0e38f; zmin = 3.0e38f;
             for (int k = 0; k < KV; ++k) {
                 if (!vertex_used(tmask, k, K)) continue;
-                const DVert d = decide_vertex(cam, p[3 * k], p[3 * k + 1], p[3 * k + 2]);
+                const DVert d = decide_vertex(cam, df_project(cam, p[3 * k], p[3 * k + 1], p[3 * k + 2]), ox, oy);
                 mnx = fminf(mnx, d.xs); mxx = fmaxf(mxx, d.xs);
                 mny = fminf(mny, d.ys); mxy = fmaxf(mxy, d.ys);
                 zmin = fminf(zmin, d.Z);
@@ -110,7 +116,9 @@ __global__ void __launch_bounds__(kBinThreads) bin_kernel(const __grid_constant_
                 count = (uint32_t)(w * h);
                 s_rect[tid][0] = (uint32_t)tx0 | ((uint32_t)ty0 << 16);
                 s_rect[tid][1] = (uint32_t)w | ((uint32_t)h << 16);
-                s_q[tid] = depth_q(zmin * a.key_scale, depth_bits);
+                // a lower bound of every fragment depth of the fan: the smallest rounded
+                // vertex depth, lowered by 2^-20 to cover its rounding
+                s_q[tid] = depth_q(zmin * (a.key_scale * kKeyMargin), depth_bits);
             }
         }
     }

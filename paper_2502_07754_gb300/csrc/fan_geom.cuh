@@ -28,6 +28,19 @@ __device__ __forceinline__ FanRect rect_from_bounds(float mnx, float mxx, float 
     return r;
 }
 
+// rect_from_bounds for bounds given relative to the integer origin (ox, oy): identical
+// pixel arithmetic in the relative frame, shifted by the origin.
+__device__ __forceinline__ FanRect rect_from_bounds_rel(float mnx, float mxx, float mny, float mxy, int ox, int oy,
+                                                        int W, int H) {
+    FanRect r;
+    r.i0 = max((int)ceilf(mnx - 0.75f) + ox, 0);
+    r.i1 = min((int)floorf(mxx - 0.25f) + ox, W - 1);
+    r.j0 = max((int)ceilf(mny - 0.75f) + oy, 0);
+    r.j1 = min((int)floorf(mxy - 0.25f) + oy, H - 1);
+    r.empty = r.i0 > r.i1 || r.j0 > r.j1;
+    return r;
+}
+
 // Triangle j of a fan is valid when the centre and both of its boundary vertices are.
 __device__ __forceinline__ uint32_t tri_valid_mask(uint32_t vmask, int K) {
     uint32_t t = 0;

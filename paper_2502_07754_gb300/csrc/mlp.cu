@@ -46,9 +46,11 @@ constexpr uint32_t kTdZ2t = kTdYt + kOutPad * kRows * 2;   // dZ2^T [128][128]
 constexpr uint32_t kTdZ1t = kTdZ2t + kHid * kRows * 2;     // dZ1^T [128][128]
 constexpr uint32_t kTileBytes = kTdZ1t + kHid * kRows * 2;
 
-__device__ __forceinline__ float gelu(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
+// Exact GELU x Phi(x), with Phi(x) = erfc(-x / sqrt 2) / 2: the complementary form keeps
+// the small negative tail (x < -5) that 1 + erf(x / sqrt 2) cancels to zero in binary32.
+__device__ __forceinline__ float gelu(float x) { return 0.5f * x * erfcf(-x * 0.70710678118654752f); }
 __device__ __forceinline__ float gelu_grad(float x) {
-    return 0.5f * (1.0f + erff(x * 0.70710678118654752f)) + x * 0.39894228040143268f * __expf(-0.5f * x * x);
+    return 0.5f * erfcf(-x * 0.70710678118654752f) + x * 0.39894228040143268f * __expf(-0.5f * x * x);
 }
 
 __device__ __forceinline__ uint16_t bf16_bits(float x) { return __bfloat16_as_ushort(__float2bfloat16_rn(x)); }

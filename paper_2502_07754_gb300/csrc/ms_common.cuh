@@ -1,15 +1,17 @@
 // Shared device helpers of the MeshSplats CUDA library (sm_103a).
 //
-// The "decision" functions evaluate, in IEEE binary32 with the round-to-nearest
-// intrinsics (which the compiler never fuses into FMAs), exactly the coverage and
-// depth formulas stated in include/meshsplats.h; the value functions (barycentrics,
-// interpolation, compositing, gradients) are free FP32 arithmetic.
+// The "decision" functions evaluate the coverage formulas stated in
+// include/meshsplats.h in IEEE binary32 with the round-to-nearest intrinsics (which the
+// compiler never fuses into FMAs), on vertex positions taken from a double-float
+// projection; the fragment order uses a double-float depth.  The value functions
+// (barycentrics, interpolation, compositing, gradients) are free FP32 arithmetic.
 #pragma once
 
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include "../../include/meshsplats.h"
+#include "dfloat.cuh"
 
 namespace ms {
 
@@ -93,33 +95,73 @@ __device__ __forceinline__ int view_of_pixel(const ViewTable &t, unsigned long l
 }
 
 // ---------------------------------------------------------------------------------
-// Decisions (binary32, no contraction)
+// Decisions
 // ---------------------------------------------------------------------------------
 
-struct DVert {
-    float xs, ys, Z, iz;
-    bool valid;
-};
+// Double-float dot product of a binary32 row R with the double-float vector d: exact
+// products of the high parts (FMA residuals), their sum by two-sums, and the remaining
+// error terms summed in binary32.
+__device__ __forceinline__ dfl df_row_dot(const float *R, dfl d0, dfl d1, dfl d2) {
+    const dfl p0 = df_two_prod(R[0], d0.h), p1 = df_two_prod(R[1], d1.h), p2 = df_two_prod(R[2], d2.h);
+    const dfl s = df_two_sum(p0.h, p1.h);
+    const dfl t = df_two_sum(s.h, p2.h);
+    const float l = __fadd_rn(__fadd_rn(__fadd_rn(s.l, t.l), __fadd_rn(__fadd_rn(p0.l, p1.l), p2.l)),
+                              fmaf(R[0], d0.l, fmaf(R[1], d1.l, __fmul_rn(R[2], d2.l))));
+    return df_fast_two_sum(t.h, l);
+}
 
-__device__ __forceinline__ DVert decide_vertex(const CamDev &c, float px, float py, float pz) {
-    float dx = __fsub_rn(px, c.C[0]);
-    float dy = __fsub_rn(py, c.C[1]);
-    float dz = __fsub_rn(pz, c.C[2]);
-    float X = __fadd_rn(__fadd_rn(__fmul_rn(c.R[0], dx), __fmul_rn(c.R[1], dy)), __fmul_rn(c.R[2], dz));
-    float Y = __fadd_rn(__fadd_rn(__fmul_rn(c.R[3], dx), __fmul_rn(c.R[4], dy)), __fmul_rn(c.R[5], dz));
-    float Z = __fadd_rn(__fadd_rn(__fmul_rn(c.R[6], dx), __fmul_rn(c.R[7], dy)), __fmul_rn(c.R[8], dz));
-    DVert o;
-    o.xs = __fadd_rn(__fmul_rn(c.fx, __fdiv_rn(X, Z)), c.cx);
-    o.ys = __fadd_rn(__fmul_rn(c.fy, __fdiv_rn(Y, Z)), c.cy);
-    o.Z = Z;
-    o.iz = __frcp_rn(Z);
-    o.valid = (Z > c.znear) && (fabsf(o.xs) <= kGuardPx) && (fabsf(o.ys) <= kGuardPx);
+// f (N / Z) + c in double-float, the quotient from one reciprocal of Z.h and a
+// double-float residual correction.
+__device__ __forceinline__ dfl df_screen_coord(dfl N, dfl Z, float rz, float f, float c) {
+    const float q1 = __fmul_rn(N.h, rz);
+    const float r = __fadd_rn(fmaf(-q1, Z.h, N.h), fmaf(-q1, Z.l, N.l));
+    const dfl q = df_fast_two_sum(q1, __fmul_rn(r, rz));
+    dfl a = df_mul_f(q, f);
+    return df_add_f(a, c);
+}
+
+// Camera-space position (X, Y, Z) and screen position (x, y) of a world point, all in
+// double-float: d = p - C is exact, then the rotation and the pinhole division.
+struct DfVert {
+    dfl X, Y, Z, x, y;
+};
+__device__ __forceinline__ DfVert df_project(const CamDev &c, float px, float py, float pz) {
+    const dfl d0 = df_two_sum(px, -c.C[0]), d1 = df_two_sum(py, -c.C[1]), d2 = df_two_sum(pz, -c.C[2]);
+    DfVert o;
+    o.X = df_row_dot(c.R, d0, d1, d2);
+    o.Y = df_row_dot(c.R + 3, d0, d1, d2);
+    o.Z = df_row_dot(c.R + 6, d0, d1, d2);
+    const float rz = __frcp_rn(o.Z.h);
+    o.x = df_screen_coord(o.X, o.Z, rz, c.fx, c.cx);
+    o.y = df_screen_coord(o.Y, o.Z, rz, c.fy, c.cy);
     return o;
 }
 
-// The validity rule of decide_vertex, from stored decided values.
-__device__ __forceinline__ bool vertex_valid(const CamDev &c, float xs, float ys, float Z) {
-    return (Z > c.znear) && (fabsf(xs) <= kGuardPx) && (fabsf(ys) <= kGuardPx);
+// A vertex as the coverage decisions see it: the double-float screen position rounded to
+// binary32 (xs, ys) and relative to its fan's integer origin (xr, yr) = nearest binary32
+// value of (x - ox, y - oy), its rounded depth Z, and the validity rule on the rounded
+// values (Z > znear, |xs|, |ys| <= 2^17).
+struct DVert {
+    float xs, ys, xr, yr, Z;
+    bool valid;
+};
+
+// Nearest binary32 value of v - o for an integer-valued binary32 o (exact two-sum of the
+// high part, then the low parts).
+__device__ __forceinline__ float df_offset(dfl v, float o) {
+    const dfl s = df_two_sum(v.h, -o);
+    return __fadd_rn(s.h, __fadd_rn(s.l, v.l));
+}
+
+__device__ __forceinline__ DVert decide_vertex(const CamDev &c, const DfVert &v, float ox, float oy) {
+    DVert o;
+    o.xs = df_round(v.x);
+    o.ys = df_round(v.y);
+    o.xr = df_offset(v.x, ox);
+    o.yr = df_offset(v.y, oy);
+    o.Z = df_round(v.Z);
+    o.valid = (o.Z > c.znear) && (fabsf(o.xs) <= kGuardPx) && (fabsf(o.ys) <= kGuardPx);
+    return o;
 }
 
 __device__ __forceinline__ float dec_area2(float xa, float ya, float xb, float yb, float xc, float yc) {
@@ -136,15 +178,6 @@ __device__ __forceinline__ float dec_edge(float ex, float ey, float lx, float ly
 // Top-left acceptance of an oriented edge value E with direction (ex, ey).
 __device__ __forceinline__ bool edge_pass(float E, float ex, float ey) {
     return E > 0.0f || (E == 0.0f && (ey < 0.0f || (ey == 0.0f && ex > 0.0f)));
-}
-
-__device__ __forceinline__ float dec_depth(float area2, float E0, float iz0, float E1, float iz1, float E2,
-                                           float iz2, float Za, float Zb, float Zc) {
-    float w = __fadd_rn(__fadd_rn(__fmul_rn(E0, iz0), __fmul_rn(E1, iz1)), __fmul_rn(E2, iz2));
-    float z = __fdiv_rn(area2, w);
-    float zlo = fminf(fminf(Za, Zb), Zc);
-    float zhi = fmaxf(fmaxf(Za, Zb), Zc);
-    return fminf(fmaxf(z, zlo), zhi);
 }
 
 // Quantised depth used in sort keys and in the commit test: the top `bits` bits of

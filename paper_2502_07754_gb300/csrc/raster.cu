@@ -162,8 +162,9 @@ __global__ void __launch_bounds__(kRastWarps * 32) raster_kernel(const __grid_co
                 if (SPLAT)
                     hits = splat_hit(s_spl[f], *sc.cam, a.spl.trunc, (double)px + 0.5, (double)py + 0.5, sp_t, sp_a)
                                ? 1u : 0u;
-                else
-                    hits = cover_mask<KT>(S, STG, K, f, flags, (float)px + 0.5f, (float)py + 0.5f);
+                else   // decisions in the fan's relative frame (the origin is an integer)
+                    hits = cover_mask<KT>(S, STG, K, f, flags, (float)(px - (int)S.ox[f]) + 0.5f,
+                                          (float)(py - (int)S.oy[f]) + 0.5f);
                 if (hits) lp = (py - ty0) * TILE + (px - tx0);
             }
             const int nf = __popc(hits);
@@ -199,18 +200,12 @@ __global__ void __launch_bounds__(kRastWarps * 32) raster_kernel(const __grid_co
                 const uint32_t b = s_base[lp];
                 if (b != 0xffffffffu) {
                     const float pxc = (float)px + 0.5f, pyc = (float)py + 0.5f;
-                    const uint32_t pix = (uint32_t)(pix_base + (unsigned long long)py * (unsigned)sc.W + (unsigned)px);
                     for (uint32_t hm = hits; hm; hm &= hm - 1, ++slot) {
                         const int j = __ffs(hm) - 1;
                         const int jn = (j + 1 == K) ? 0 : j + 1;
-                        const bool neg = ((flags >> 16) >> j) & 1u;
-                        float E0, E1, E2;
-                        tri_edges(S, STG, K, f, flags, j, pxc, pyc, E0, E1, E2);
                         const float izc = S.viz[f];
                         const float izj = S.viz[(1 + j) * STG + f], izn = S.viz[(1 + jn) * STG + f];
-                        const float zf = dec_depth(S.area[j * STG + f], E0, izc, E1, neg ? izn : izj, E2,
-                                                   neg ? izj : izn, S.vz[f], S.vz[(1 + j) * STG + f],
-                                                   S.vz[(1 + jn) * STG + f]);
+                        const dfl zf = frag_depth_df(S, STG, f, j, jn, pxc, pyc, *sc.cam);
                         // perspective-correct barycentrics from the accurate centre offsets
                         const float ox = __fsub_rn(S.cxh[f], pxc) + S.cxl[f];
                         const float oy = __fsub_rn(S.cyh[f], pyc) + S.cyl[f];
@@ -229,8 +224,8 @@ __global__ void __launch_bounds__(kRastWarps * 32) raster_kernel(const __grid_co
                         const float c2 = m0 * S.cb[vc] + m1 * S.cb[vj] + m2 * S.cb[vn];
                         const uint32_t tri = S.fan[f] * (uint32_t)K + (uint32_t)j;
                         float4 *rec = a.frags + (size_t)kRecFwd * ((size_t)b + slot);
-                        rec[0] = make_float4(zf, __uint_as_float(tri), __uint_as_float(S.q[f]), al);
-                        rec[1] = make_float4(c0, c1, c2, __uint_as_float(pix));
+                        rec[0] = make_float4(zf.h, __uint_as_float(tri), __uint_as_float(S.q[f]), al);
+                        rec[1] = make_float4(c0, c1, c2, zf.l);
                     }
                 }
             }

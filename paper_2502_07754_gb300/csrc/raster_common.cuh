@@ -1,6 +1,7 @@
 // Shared pieces of the rasterisation kernels: double-float projection of a fan
-// centre (value path), the shared-memory stage of a chunk of fans, and the per-pixel
-// coverage walk over a staged fan's K triangles with the binary32 decision formulas.
+// centre (value path), the shared-memory stage of a chunk of fans, the per-pixel
+// coverage walk over a staged fan's K triangles with the binary32 decision formulas on
+// fan-relative vertex positions, and the double-float fragment depth that orders them.
 #pragma once
 
 #include "fan_geom.cuh"
@@ -19,11 +20,11 @@ struct SceneDev {
     int K;
     const CamDev *cam;   // points into the kernel's __grid_constant__ view table
     int W, H;
-    const float4 *dec;   // this view's decided vertices (xs, ys, Z, 1/Z), written by binning
+    const float4 *dec;   // this view's decided vertices (xr, yr, Z or -1, origin), written by binning
 };
 
 // ------------------------------------------------------------------------------------
-// Double-float helpers (Knuth two-sum, FMA two-product)
+// Double-float helpers of the value path (Knuth two-sum, FMA two-product)
 // ------------------------------------------------------------------------------------
 
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
@@ -63,20 +64,20 @@ __device__ __forceinline__ void df_screen(float Xh, float Xl, float Zh, float Zl
 // positions relative to a pixel carry ~1e-6 px error instead of the ~1e-4 px of a
 // plain binary32 projection at 1080p.
 struct CentreProj {
-    float Xh, Yh, Zh;
+    float Xh, Yh, Zh, Zl;
     float xh, xl, yh, yl;
 };
 __device__ __forceinline__ CentreProj project_centre(const CamDev &c, const float m[3]) {
     float dh[3], dl[3];
 #pragma unroll
     for (int r = 0; r < 3; ++r) two_sum(m[r], -c.C[r], dh[r], dl[r]);
-    float Xl, Yl, Zl;
+    float Xl, Yl;
     CentreProj o;
     df_dot(c.R, dh, dl, o.Xh, Xl);
     df_dot(c.R + 3, dh, dl, o.Yh, Yl);
-    df_dot(c.R + 6, dh, dl, o.Zh, Zl);
-    df_screen(o.Xh, Xl, o.Zh, Zl, c.fx, c.cx, o.xh, o.xl);
-    df_screen(o.Yh, Yl, o.Zh, Zl, c.fy, c.cy, o.yh, o.yl);
+    df_dot(c.R + 6, dh, dl, o.Zh, o.Zl);
+    df_screen(o.Xh, Xl, o.Zh, o.Zl, c.fx, c.cx, o.xh, o.xl);
+    df_screen(o.Yh, Yl, o.Zh, o.Zl, c.fy, c.cy, o.yh, o.yl);
     return o;
 }
 __device__ __forceinline__ void vertex_offset(const CamDev &c, const CentreProj &cp, const float d[3], float &du,
@@ -92,6 +93,17 @@ __device__ __forceinline__ void vertex_offset(const CamDev &c, const CentreProj 
     dv = c.fy * (dY * cp.Zh - cp.Yh * dZ) * den;
 }
 
+// Camera-space offset R (p - m) of a vertex from its fan centre, in double-float (the
+// world difference of two binary32 values is exact as a two-sum).
+struct DfVec {
+    dfl x, y, z;
+};
+__device__ __forceinline__ DfVec df_view_offset(const CamDev &c, const float m[3], const float *p) {
+    const dfl d0 = df_two_sum(__ldg(p), -m[0]), d1 = df_two_sum(__ldg(p + 1), -m[1]);
+    const dfl d2 = df_two_sum(__ldg(p + 2), -m[2]);
+    return DfVec{df_row_dot(c.R, d0, d1, d2), df_row_dot(c.R + 3, d0, d1, d2), df_row_dot(c.R + 6, d0, d1, d2)};
+}
+
 // ------------------------------------------------------------------------------------
 // Shared-memory stage (structure of arrays over CH slots)
 // ------------------------------------------------------------------------------------
@@ -102,22 +114,26 @@ struct Stage {
     uint32_t *q;                  // [CH] quantised depth bound
     uint32_t *fan;                // [CH] fan id
     uint32_t *stie, *rtie;        // [CH] top-left tie bits of the spoke / rim directions
-    float *vx, *vy, *vz, *viz;    // [KV][CH] decided vertices
+    float *ox, *oy;               // [CH] integer origin of the fan's relative positions
+    float *vx, *vy;               // [KV][CH] decided vertices relative to the origin
     float *sdx, *sdy;             // [K][CH] spoke directions b_i - c
     float *rdx, *rdy;             // [K][CH] rim directions, lower index to higher
     float *area;                  // [K][CH] |area2|
     float *cxh, *cxl, *cyh, *cyl; // [CH] double-float screen position of the centre (values)
     float *du, *dv;               // [K][CH] screen offsets of the boundary vertices (values)
     float *cr, *cg, *cb, *ca;     // [KV][CH] vertex colour and opacity (values)
+    float *zh, *zl;               // [KV][CH] double-float view depth of each vertex (values)
+    float *viz;                   // [KV][CH] 1 / depth (values: barycentric weights)
+    float *pah, *pal, *pbh, *pbl, *pnh, *pnl;   // [K][CH] triangle plane n.x fy, n.y fx, n.z fx fy (values)
 };
 
 // What a stage holds: decisions only (count), or decisions and values (fill).
 enum StageLevel { kStageDecide = 0, kStageValues = 1 };
 
 __host__ __device__ __forceinline__ size_t stage_bytes(int CH, int K, int level) {
-    const int dec = 4 * (K + 1) + 5 * K;
-    const int val = level >= kStageValues ? 4 + 2 * K + 4 * (K + 1) : 0;
-    return (size_t)CH * (16 + 20 + 4 * (dec + val));
+    const int dec = 2 * (K + 1) + 5 * K;
+    const int val = level >= kStageValues ? 4 + 2 * K + 4 * (K + 1) + 3 * (K + 1) + 6 * K : 0;
+    return (size_t)CH * (16 + 20 + 8 + 4 * (dec + val));
 }
 
 __device__ __forceinline__ Stage stage_ptrs(char *base, int CH, int K, int level) {
@@ -130,10 +146,10 @@ __device__ __forceinline__ Stage stage_ptrs(char *base, int CH, int K, int level
     s.stie = s.fan + CH;
     s.rtie = s.stie + CH;
     float *f = reinterpret_cast<float *>(s.rtie + CH);
+    s.ox = f; f += CH;
+    s.oy = f; f += CH;
     s.vx = f; f += KV * CH;
     s.vy = f; f += KV * CH;
-    s.vz = f; f += KV * CH;
-    s.viz = f; f += KV * CH;
     s.sdx = f; f += K * CH;
     s.sdy = f; f += K * CH;
     s.rdx = f; f += K * CH;
@@ -149,7 +165,16 @@ __device__ __forceinline__ Stage stage_ptrs(char *base, int CH, int K, int level
         s.cr = f; f += KV * CH;
         s.cg = f; f += KV * CH;
         s.cb = f; f += KV * CH;
-        s.ca = f;
+        s.ca = f; f += KV * CH;
+        s.zh = f; f += KV * CH;
+        s.zl = f; f += KV * CH;
+        s.viz = f; f += KV * CH;
+        s.pah = f; f += K * CH;
+        s.pal = f; f += K * CH;
+        s.pbh = f; f += K * CH;
+        s.pbl = f; f += K * CH;
+        s.pnh = f; f += K * CH;
+        s.pnl = f;
     }
     return s;
 }
@@ -192,9 +217,9 @@ __device__ __forceinline__ void stage_fans(const SceneDev &a, const Stage &s, in
             const float4 d = __ldg(dv + k);   // the binning pass's decide_vertex, bit for bit
             s.vx[k * CH + slot] = d.x;
             s.vy[k * CH + slot] = d.y;
-            s.vz[k * CH + slot] = d.z;
-            s.viz[k * CH + slot] = d.w;
-            if (vertex_valid(*a.cam, d.x, d.y, d.z)) vmask |= 1u << k;
+            if (d.z > 0.0f) vmask |= 1u << k;   // binning marks invalid vertices with Z = -1
+            if (k == 0) s.ox[slot] = d.w;
+            if (k == 1) s.oy[slot] = d.w;
         }
     vmask = group_or<LPF>(vmask);
     __syncwarp();   // the group's vertex rows are complete
@@ -245,7 +270,7 @@ __device__ __forceinline__ void stage_fans(const SceneDev &a, const Stage &s, in
     stie = group_or<LPF>(stie);
     rtie = group_or<LPF>(rtie);
     if (active && sub == 0) {
-        const FanRect r = rect_from_bounds(mnx, mxx, mny, mxy, a.W, a.H);
+        const FanRect r = rect_from_bounds_rel(mnx, mxx, mny, mxy, (int)s.ox[slot], (int)s.oy[slot], a.W, a.H);
         s.stie[slot] = stie;
         s.rtie[slot] = rtie;
         s.flags[slot] = (tmask == 0 || r.empty) ? 0u : flags;
@@ -253,30 +278,89 @@ __device__ __forceinline__ void stage_fans(const SceneDev &a, const Stage &s, in
         s.fan[slot] = fan;
         s.rect[slot] = make_int4(r.i0, r.i1, r.j0, r.j1);
     }
-    if (level < kStageValues || !active) return;
-    const float m[3] = {__ldg(p), __ldg(p + 1), __ldg(p + 2)};
-    const CentreProj cp = project_centre(*a.cam, m);
-    if (sub == 0) {
-        s.cxh[slot] = cp.xh;
-        s.cxl[slot] = cp.xl;
-        s.cyh[slot] = cp.yh;
-        s.cyl[slot] = cp.yl;
+    if (level < kStageValues) return;   // uniform across the warp
+    float m[3] = {0.0f, 0.0f, 0.0f};
+    dfl zc = df_make(1.0f);
+    if (active) {
+        m[0] = __ldg(p);
+        m[1] = __ldg(p + 1);
+        m[2] = __ldg(p + 2);
+        const CentreProj cp = project_centre(*a.cam, m);
+        zc = df_fast_two_sum(cp.Zh, cp.Zl);
+        if (sub == 0) {
+            s.cxh[slot] = cp.xh;
+            s.cxl[slot] = cp.xl;
+            s.cyh[slot] = cp.yh;
+            s.cyl[slot] = cp.yl;
+            s.zh[slot] = zc.h;
+            s.zl[slot] = zc.l;
+            s.viz[slot] = 1.0f / zc.h;
+        }
+        for (int i = sub; i < K; i += LPF) {
+            const float *pi = p + 3 * (1 + i);
+            const float d[3] = {__ldg(pi) - m[0], __ldg(pi + 1) - m[1], __ldg(pi + 2) - m[2]};
+            float du, dv, X, Y, Z;
+            vertex_offset(*a.cam, cp, d, du, dv, X, Y, Z);
+            s.du[i * CH + slot] = du;
+            s.dv[i * CH + slot] = dv;
+            // exact-order geometry, first half: the double-float view offset e = R (b_i - c)
+            // (kept in the plane arrays until the planes replace it) and view depth
+            const DfVec e = df_view_offset(*a.cam, m, pi);
+            const dfl zv = df_add(zc, e.z);
+            s.zh[(1 + i) * CH + slot] = zv.h;
+            s.zl[(1 + i) * CH + slot] = zv.l;
+            s.viz[(1 + i) * CH + slot] = 1.0f / zv.h;
+            s.pah[i * CH + slot] = e.x.h;
+            s.pal[i * CH + slot] = e.x.l;
+            s.pbh[i * CH + slot] = e.y.h;
+            s.pbl[i * CH + slot] = e.y.l;
+            s.pnh[i * CH + slot] = e.z.h;
+            s.pnl[i * CH + slot] = e.z.l;
+        }
+        const float *col = a.rgb + (size_t)fan * KV * 3;
+        const float *al = a.alpha + (size_t)fan * KV;
+        for (int k = sub; k < KV; k += LPF) {
+            s.cr[k * CH + slot] = __ldg(col + 3 * k);
+            s.cg[k * CH + slot] = __ldg(col + 3 * k + 1);
+            s.cb[k * CH + slot] = __ldg(col + 3 * k + 2);
+            s.ca[k * CH + slot] = __ldg(al + k);
+        }
     }
-    for (int i = sub; i < K; i += LPF) {
-        const float d[3] = {__ldg(p + 3 * (1 + i)) - m[0], __ldg(p + 3 * (1 + i) + 1) - m[1],
-                            __ldg(p + 3 * (1 + i) + 2) - m[2]};
-        float du, dv, X, Y, Z;
-        vertex_offset(*a.cam, cp, d, du, dv, X, Y, Z);
-        s.du[i * CH + slot] = du;
-        s.dv[i * CH + slot] = dv;
+    __syncwarp();   // every offset of the group is staged
+    // second half: per triangle (c, b_j, b_j+1) the plane normal n = e_j x e_j+1 in
+    // double-float, scaled to (n.x fy, n.y fx, n.z fx fy), written over the offsets once the
+    // whole warp has read them
+    constexpr int NJ = (kMaxK + LPF - 1) / LPF;
+    dfl pa[NJ], pb[NJ], pn[NJ];
+#pragma unroll
+    for (int t = 0; t < NJ; ++t) {
+        const int j = sub + t * LPF;
+        if (active && j < K) {
+            const int jn = (j + 1 == K) ? 0 : j + 1;
+            const int u = j * CH + slot, w = jn * CH + slot;
+            const dfl e1x = {s.pah[u], s.pal[u]}, e1y = {s.pbh[u], s.pbl[u]}, e1z = {s.pnh[u], s.pnl[u]};
+            const dfl e2x = {s.pah[w], s.pal[w]}, e2y = {s.pbh[w], s.pbl[w]}, e2z = {s.pnh[w], s.pnl[w]};
+            const dfl nx = df_add_fast(df_mul(e1y, e2z), df_neg(df_mul(e1z, e2y)));
+            const dfl ny = df_add_fast(df_mul(e1z, e2x), df_neg(df_mul(e1x, e2z)));
+            const dfl nz = df_add_fast(df_mul(e1x, e2y), df_neg(df_mul(e1y, e2x)));
+            pa[t] = df_mul_f(nx, a.cam->fy);
+            pb[t] = df_mul_f(ny, a.cam->fx);
+            pn[t] = df_mul_f(df_mul_f(nz, a.cam->fx), a.cam->fy);
+        }
     }
-    const float *col = a.rgb + (size_t)fan * KV * 3;
-    const float *al = a.alpha + (size_t)fan * KV;
-    for (int k = sub; k < KV; k += LPF) {
-        s.cr[k * CH + slot] = __ldg(col + 3 * k);
-        s.cg[k * CH + slot] = __ldg(col + 3 * k + 1);
-        s.cb[k * CH + slot] = __ldg(col + 3 * k + 2);
-        s.ca[k * CH + slot] = __ldg(al + k);
+    __syncwarp();   // all offsets read
+#pragma unroll
+    for (int t = 0; t < NJ; ++t) {
+        const int j = sub + t * LPF;
+        if (active && j < K) {
+            const int u = j * CH + slot;
+            s.pah[u] = pa[t].h;
+            s.pal[u] = pa[t].l;
+            s.pbh[u] = pb[t].h;
+            s.pbl[u] = pb[t].l;
+            s.pnh[u] = pn[t].h;
+            s.pnl[u] = pn[t].l;
+        }
     }
 }
 
@@ -322,22 +406,36 @@ __device__ __forceinline__ uint32_t cover_mask(const Stage &S, int CH, int K, in
     return hits;
 }
 
-// Oriented edge values of triangle j of staged fan f at a pixel centre it covers (E0
-// opposite P0 = centre, E1 opposite P1, E2 opposite P2 of the decision formulas).
-__device__ __forceinline__ void tri_edges(const Stage &S, int CH, int K, int f, uint32_t flags, int j, float pxc,
-                                          float pyc, float &E0, float &E1, float &E2) {
-    const int jn = (j + 1 == K) ? 0 : j + 1;
-    const bool neg = ((flags >> 16) >> j) & 1u;
-    const bool wrap = (j + 1 == K);
-    const int lo = wrap ? 0 : j;
-    const float Rc = dec_edge(S.rdx[j * CH + f], S.rdy[j * CH + f], S.vx[(1 + lo) * CH + f], S.vy[(1 + lo) * CH + f],
-                              pxc, pyc);
-    E0 = (wrap != neg) ? -Rc : Rc;
-    const float qx = __fsub_rn(pxc, S.vx[f]), qy = __fsub_rn(pyc, S.vy[f]);
-    const float Sj = __fsub_rn(__fmul_rn(S.sdx[j * CH + f], qy), __fmul_rn(S.sdy[j * CH + f], qx));
-    const float Sn = __fsub_rn(__fmul_rn(S.sdx[jn * CH + f], qy), __fmul_rn(S.sdy[jn * CH + f], qx));
-    E1 = neg ? -Sj : -Sn;
-    E2 = neg ? Sn : Sj;
+// Depth of triangle j of staged fan f at the pixel centre (pxc, pyc) (absolute screen
+// coordinates), in double-float: the view depth where the pixel's ray meets the
+// triangle's plane, Z = Zc + Zc (n.x (xc - x) / fx + n.y (yc - y) / fy) / (n . r) with
+// r = ((x - cx) / fx, (y - cy) / fy, 1) and (xc, yc, Zc) the centre's screen position and
+// depth (both scaled here by fx fy); this equals 1 / sum_k (lambda_k / Z_k) of the
+// perspective-correct barycentrics.  Clamped to the triangle's vertex depths, where a
+// covered centre lies (the clamp only acts where the decided coverage and the exact
+// plane differ by rounding; a ray parallel to the plane takes the nearest vertex depth).
+__device__ __forceinline__ dfl frag_depth_df(const Stage &S, int CH, int f, int j, int jn, float pxc, float pyc,
+                                             const CamDev &c) {
+    const int t = j * CH + f;
+    const dfl pa = {S.pah[t], S.pal[t]}, pb = {S.pbh[t], S.pbl[t]}, pn = {S.pnh[t], S.pnl[t]};
+    const dfl ox = df_add_f(df_two_sum(S.cxh[f], -pxc), S.cxl[f]);
+    const dfl oy = df_add_f(df_two_sum(S.cyh[f], -pyc), S.cyl[f]);
+    const dfl num = df_add_fast(df_mul(pa, ox), df_mul(pb, oy));
+    const dfl den = df_add_fast(df_add_fast(df_mul(pa, df_two_sum(pxc, -c.cx)), df_mul(pb, df_two_sum(pyc, -c.cy))), pn);
+    const dfl zc = {S.zh[f], S.zl[f]};
+    const dfl z1 = {S.zh[(1 + j) * CH + f], S.zl[(1 + j) * CH + f]};
+    const dfl z2 = {S.zh[(1 + jn) * CH + f], S.zl[(1 + jn) * CH + f]};
+    dfl lo = zc, hi = zc;
+    if (df_lt(z1, lo)) lo = z1;
+    if (df_lt(z2, lo)) lo = z2;
+    if (df_lt(hi, z1)) hi = z1;
+    if (df_lt(hi, z2)) hi = z2;
+    if (den.h == 0.0f) return lo;
+    dfl z = df_add_fast(zc, df_div(df_mul(zc, num), den));
+    if (!(z.h == z.h)) return lo;   // NaN
+    if (df_lt(z, lo)) z = lo;
+    if (df_lt(hi, z)) z = hi;
+    return z;
 }
 
 // ------------------------------------------------------------------------------------

@@ -8,7 +8,8 @@
 // deep, so the order is exact.  If the buffer overflows, the thread remembers the
 // nearest dropped fragment and the earliest record it dropped, finishes the pass with
 // everything strictly nearer, and re-reads its own records from that point, skipping
-// fragments at or before the last committed one.  Order: (depth, triangle id).
+// fragments at or before the last committed one.  Order: (depth, triangle id), the depth
+// a double-float value (high part in the record's first word, low part in its last).
 // Compositing stops once the transmittance falls below T_eps.
 //
 // Both passes visit the pixels in orders that pixel_order_kernel builds after the pixel
@@ -119,8 +120,10 @@ __global__ void __launch_bounds__(kOrderThreads) pixel_order_kernel(const uint32
         }
 }
 
-__device__ __forceinline__ bool frag_less(float za, uint32_t ta, float zb, uint32_t tb) {
-    return za < zb || (za == zb && ta < tb);
+// (depth, triangle) order of two fragments; depths are normalised double-float values,
+// so comparing (high, low) lexicographically compares their values.
+__device__ __forceinline__ bool frag_less(float za, float la, uint32_t ta, float zb, float lb, uint32_t tb) {
+    return za < zb || (za == zb && (la < lb || (la == lb && ta < tb)));
 }
 
 template <int KB>
@@ -138,13 +141,13 @@ __global__ void __launch_bounds__(kResolveThreads) resolve_kernel(const __grid_c
     float4 *rec = a.frags + (size_t)RS * off;
 
     float T = 1.0f, C0 = 0.0f, C1 = 0.0f, C2 = 0.0f;
-    float kz[KB];              // pending fragments sorted by (depth, triangle)
+    float kz[KB], kl[KB];      // pending fragments sorted by (depth, triangle): depth high, low
     uint32_t kt[KB], ki[KB];   // triangle id, record index
     int nb = 0;
-    float fz = 0.0f;           // last committed (depth, triangle); depths are > 0
+    float fz = 0.0f, fl = 0.0f;   // last committed (depth, triangle); depths are > 0
     uint32_t ft = 0;
     bool has_front = false;
-    float dz = 0.0f;           // nearest dropped fragment of this pass
+    float dz = 0.0f, dl = 0.0f;   // nearest dropped fragment of this pass
     uint32_t dt = 0;
     bool dropped = false;
     int restart = 0x7fffffff;
@@ -166,11 +169,12 @@ __global__ void __launch_bounds__(kResolveThreads) resolve_kernel(const __grid_c
         a.corder[off + ncom] = ki[0];
         ++ncom;
         fz = kz[0];
+        fl = kl[0];
         ft = kt[0];
         has_front = true;
 #pragma unroll
         for (int i = 0; i + 1 < KB; ++i) {
-            kz[i] = kz[i + 1]; kt[i] = kt[i + 1]; ki[i] = ki[i + 1];
+            kz[i] = kz[i + 1]; kl[i] = kl[i + 1]; kt[i] = kt[i + 1]; ki[i] = ki[i + 1];
         }
         --nb;
         if (T < a.T_eps) {
@@ -183,25 +187,27 @@ __global__ void __launch_bounds__(kResolveThreads) resolve_kernel(const __grid_c
     while (!done) {
         for (int i = start; i < n && !done; ++i) {
             const float4 r0 = rec[RS * i];
-            const float z = r0.x;
+            const float z = r0.x, zl = rec[RS * i + 1].w;
             const uint32_t tri = __float_as_uint(r0.y), qk = __float_as_uint(r0.z);
             while (nb > 0 && !done && depth_q(kz[0], a.depth_bits) < qk) commit_front();
             if (done) break;
-            if (has_front && !frag_less(fz, ft, z, tri)) continue;   // committed in an earlier pass
-            if (dropped && !frag_less(z, tri, dz, dt)) {
+            if (has_front && !frag_less(fz, fl, ft, z, zl, tri)) continue;   // committed in an earlier pass
+            if (dropped && !frag_less(z, zl, tri, dz, dl, dt)) {
                 restart = min(restart, i);
                 continue;
             }
             if (nb == KB) {
-                if (frag_less(z, tri, kz[KB - 1], kt[KB - 1])) {
+                if (frag_less(z, zl, tri, kz[KB - 1], kl[KB - 1], kt[KB - 1])) {
                     dz = kz[KB - 1];   // evict the deepest pending fragment
+                    dl = kl[KB - 1];
                     dt = kt[KB - 1];
                     dropped = true;
                     restart = min(restart, (int)ki[KB - 1]);
                     --nb;
                 } else {
-                    if (!dropped || frag_less(z, tri, dz, dt)) {
+                    if (!dropped || frag_less(z, zl, tri, dz, dl, dt)) {
                         dz = z;
+                        dl = zl;
                         dt = tri;
                     }
                     dropped = true;
@@ -213,16 +219,16 @@ __global__ void __launch_bounds__(kResolveThreads) resolve_kernel(const __grid_c
 #pragma unroll
             for (int s = KB - 1; s >= 1; --s) {
                 if (s <= nb && !placed) {
-                    if (frag_less(z, tri, kz[s - 1], kt[s - 1])) {
-                        kz[s] = kz[s - 1]; kt[s] = kt[s - 1]; ki[s] = ki[s - 1];
+                    if (frag_less(z, zl, tri, kz[s - 1], kl[s - 1], kt[s - 1])) {
+                        kz[s] = kz[s - 1]; kl[s] = kl[s - 1]; kt[s] = kt[s - 1]; ki[s] = ki[s - 1];
                     } else {
-                        kz[s] = z; kt[s] = tri; ki[s] = (uint32_t)i;
+                        kz[s] = z; kl[s] = zl; kt[s] = tri; ki[s] = (uint32_t)i;
                         placed = true;
                     }
                 }
             }
             if (!placed) {
-                kz[0] = z; kt[0] = tri; ki[0] = (uint32_t)i;
+                kz[0] = z; kl[0] = zl; kt[0] = tri; ki[0] = (uint32_t)i;
             }
             ++nb;
         }

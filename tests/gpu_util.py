@@ -40,10 +40,26 @@ def gpu_render(xyz, rgb, a, K, cam, **kw):
     return out.cpu().numpy().astype(np.float64), r, (X, Cc, A)
 
 
-def oracle_render(xyz, rgb, a, K, cam, window=None, bg=(0.0, 0.0, 0.0)):
+def oracle_render(xyz, rgb, a, K, cam, window=None, bg=(0.0, 0.0, 0.0), decide="fp64"):
     n_fans = xyz.shape[0] // (K + 1)
     return oracle.render(xyz.astype(np.float64), rgb.astype(np.float64), a.astype(np.float64),
-                         oracle.fan_tris(n_fans, K), cam, bg=bg, window=window)
+                         oracle.fan_tris(n_fans, K), cam, bg=bg, window=window, decide=decide)
+
+
+def fp64_report(img, xyz, rgb, a, K, cam, window=None, tol=1e-4):
+    """GPU image (of the window) against the oracle with FP64 decisions.  The kernels decide
+    coverage in binary32 on fan-relative positions; the pixels where those decisions differ
+    from FP64 ones are found on the oracle (its "rel32" mode) and reported.  Returns the
+    error report over all pixels plus the mismatch count and the largest error outside the
+    mismatched pixels."""
+    n_fans = xyz.shape[0] // (K + 1)
+    ref, mm, _ = oracle.decision_mismatch(xyz.astype(np.float64), rgb.astype(np.float64), a.astype(np.float64),
+                                          oracle.fan_tris(n_fans, K), cam, window=window)
+    rep = err_report(img, ref, tol)
+    d = np.abs(img - ref).max(axis=-1)
+    rep["decision_mismatch"] = int(mm.sum())
+    rep["max_abs_outside_mismatch"] = float(d[~mm].max()) if (~mm).any() else 0.0
+    return rep, ref
 
 
 def err_report(gpu, orc, tol=1e-4):

@@ -52,6 +52,58 @@ def test_backward_matches_oracle_reverse_pass():
         assert nbad == 0, (name, nbad, rel)
 
 
+def test_backward_deep_stack_matches_oracle_reverse_pass():
+    """The adjoint where the forward needed extra passes: 60 nearly coplanar fans over the
+    same pixels (more pending fragments than the buffer holds), compositing without early
+    termination, against the oracle's exact reverse pass entry by entry."""
+    rng = np.random.default_rng(3)
+    n = 60
+    means = np.c_[rng.normal(0, 0.02, (n, 2)), rng.normal(0, 0.002, n)].astype(np.float32)
+    q = rng.normal(0, 0.05, (n, 4)) + np.array([math.sqrt(0.5), 0, -math.sqrt(0.5), 0])
+    q = (q / np.linalg.norm(q, axis=1, keepdims=True)).astype(np.float32)
+    sh = np.zeros((n, 1, 3), np.float32)
+    sh[:, 0, :] = rng.normal(0, 1, (n, 3))
+    sc = synthetic.Scene(means, np.array([[-9, math.log(0.15), math.log(0.12)]] * n, np.float32), q,
+                         rng.uniform(0.05, 0.3, n).astype(np.float32), sh, 0)
+    cam = synthetic.make_camera((0.3, 0.2, 2.0), 96, 80)
+    xyz, rgb, a = oracle_mesh_f32(sc, 8)
+    for kb in (8, 16):
+        img, r, (X, Cc, A) = gpu_render(xyz, rgb, a, 8, cam, kbuf=kb, T_eps=1e-30)
+        assert r.last_info.extra_passes > 0
+        dL = np.random.default_rng(1).normal(size=img.shape)
+        gx, gc, ga = _gpu_grads(r, X, Cc, A, img, dL)
+        ox, oc, oa = oracle.render_backward(xyz.astype(np.float64), rgb, a, oracle.fan_tris(n, 8), cam, dL)
+        for name, g, o in (("xyz", gx, ox), ("rgb", gc, oc), ("alpha", ga, oa)):
+            nbad, rel = _close(g, o)
+            print(json.dumps({"case": "deep-stack", "kbuf": kb, "grad": name, "n_bad": nbad, "max_rel_to_max": rel}))
+            assert nbad == 0, (name, nbad, rel)
+
+
+def test_backward_clustered_1m_window_matches_oracle_reverse_pass():
+    """The adjoint of the 1M-Gaussian 1080p render with the loss gradient confined to a
+    96 x 96 window over the blobs (deep, nearly coplanar stacks): every vertex gradient
+    against the oracle's reverse pass over that window."""
+    w = synthetic.workload(3)
+    cam = w.cameras[0]
+    sc = w.scene
+    xyz, rgb, a = oracle_mesh_f32(sc, 8, cam.C)
+    img, r, (X, Cc, A) = gpu_render(xyz, rgb, a, 8, cam, T_eps=1e-30)
+    x0, y0, x1, y1 = win = (912, 492, 1008, 588)
+    dLw = np.random.default_rng(2).normal(size=(y1 - y0, x1 - x0, 4))
+    dL = np.zeros(img.shape)
+    dL[y0:y1, x0:x1] = dLw
+    gx, gc, ga = _gpu_grads(r, X, Cc, A, img, dL)
+    ox, oc, oa = oracle.render_backward(xyz.astype(np.float64), rgb, a, oracle.fan_tris(sc.n, 8), cam, dLw,
+                                        window=win)
+    touched = (np.abs(ox).sum(1) + np.abs(oc).sum(1) + np.abs(oa)) > 0
+    assert touched.sum() > 1000
+    for name, g, o in (("xyz", gx, ox), ("rgb", gc, oc), ("alpha", ga, oa)):
+        nbad, rel = _close(g, o)
+        print(json.dumps({"case": "clustered-1M-window", "grad": name, "n_bad": nbad, "max_rel_to_max": rel,
+                          "vertices": int(touched.sum())}))
+        assert nbad == 0, (name, nbad, rel)
+
+
 def test_autograd_function_matches_direct_backward():
     import paper_2502_07754_gb300 as ms
     w = synthetic.workload(1, n=300)
@@ -128,6 +180,7 @@ def test_finetune_gradients_vs_fp64_finite_differences():
         dL[win[1]:win[3], win[0]:win[2], :3] = np.sign(C_o[..., :3] - tgt[..., :3]) * scale
     gx, gc, ga = _gpu_grads(r, X, Cc, A, img, dL)
     worst = 0.0
+    skipped = 0
     for g, win, sel, vsel, tris, own, tgt in picked:
         P0 = xyz[vsel].astype(np.float64)
         C0 = rgb[vsel].astype(np.float64)
@@ -136,37 +189,56 @@ def test_finetune_gradients_vs_fp64_finite_differences():
         dLw = dL[win[1]:win[3], win[0]:win[2]]
 
         def loss(P, Cv, Av):
-            o, _, _ = oracle.render(P, Cv, Av, tris, cam, window=win, nthreads=1)
-            return float((np.abs(o[..., :3] - tgt[..., :3]) * (dLw[..., :3] != 0)).sum() * scale)
+            o, _, _, sig = oracle.render(P, Cv, Av, tris, cam, window=win, nthreads=1, signature=True)
+            return float((np.abs(o[..., :3] - tgt[..., :3]) * (dLw[..., :3] != 0)).sum() * scale), sig
+
+        _, sig0 = loss(P0, C0, A0)
+
+        def fd_position(li, c):
+            # central difference with visibility held fixed, as the adjoint defines it: a
+            # step that changes any pixel's fragments or their order (FP64 decisions flip
+            # on sub-ulp moves between nearly coplanar surfels) is redrawn 16x smaller; a
+            # component that still flips sits on a visibility boundary and is left out
+            h = float(np.spacing(np.float32(P0[li, c]))) / 8
+            for _ in range(4):
+                Pp, Pm = P0.copy(), P0.copy()
+                Pp[li, c] += h
+                Pm[li, c] -= h
+                (lp, sp), (lm, sm) = loss(Pp, C0, A0), loss(Pm, C0, A0)
+                if np.array_equal(sp, sig0) and np.array_equal(sm, sig0):
+                    return (lp - lm) / (2 * h)
+                h /= 16
+            return None
 
         fd, gg = [], []
         for k in range(K + 1):
             li, vi = own * (K + 1) + k, g * (K + 1) + k
             for c in range(3):
-                h = float(np.spacing(np.float32(P0[li, c]))) / 8
-                Pp, Pm = P0.copy(), P0.copy()
-                Pp[li, c] += h
-                Pm[li, c] -= h
-                fd.append((loss(Pp, C0, A0) - loss(Pm, C0, A0)) / (2 * h))
+                d = fd_position(li, c)
+                if d is None:
+                    skipped += 1
+                    continue
+                fd.append(d)
                 gg.append(gx[vi, c])
             for c in range(3):
                 h = 1e-6
                 Cp, Cm = C0.copy(), C0.copy()
                 Cp[li, c] += h
                 Cm[li, c] -= h
-                fd.append((loss(P0, Cp, A0) - loss(P0, Cm, A0)) / (2 * h))
+                fd.append((loss(P0, Cp, A0)[0] - loss(P0, Cm, A0)[0]) / (2 * h))
                 gg.append(gc[vi, c])
             h = 1e-6
             Ap, Am = A0.copy(), A0.copy()
             Ap[li] += h
             Am[li] -= h
-            fd.append((loss(P0, C0, Ap) - loss(P0, C0, Am)) / (2 * h))
+            fd.append((loss(P0, C0, Ap)[0] - loss(P0, C0, Am)[0]) / (2 * h))
             gg.append(ga[vi])
         fd, gg = np.array(fd), np.array(gg)
         rel = np.linalg.norm(gg - fd) / max(np.linalg.norm(fd), 1e-30)
         worst = max(worst, rel)
         assert rel <= 1e-2, (g, rel)
-    print(json.dumps({"fd_fans": 64, "worst_rel_err": worst}))
+    print(json.dumps({"fd_fans": 64, "worst_rel_err": worst, "position_components_on_a_visibility_boundary": skipped}))
+    assert skipped <= 64 * 27 // 20, skipped   # nearly all components are differentiable
 
 
 def test_l1_loss_and_adam_match_oracle():
