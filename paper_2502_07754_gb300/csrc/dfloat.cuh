@@ -95,6 +95,15 @@ __device__ __forceinline__ dfl df_div(dfl a, dfl b) {
     return df_fast_two_sum(q1, q2);
 }
 
+// a / b from one reciprocal of b.h: q1 = a.h / b.h to a few units, the residual a - q1 b
+// from two FMAs (the high one exact or nearly so), and a correction quotient.
+__device__ __forceinline__ dfl df_div_rcp(dfl a, dfl b) {
+    const float r = __frcp_rn(b.h);
+    const float q1 = __fmul_rn(a.h, r);
+    const float res = __fadd_rn(fmaf(-q1, b.h, a.h), fmaf(-q1, b.l, a.l));
+    return df_fast_two_sum(q1, __fmul_rn(res, r));
+}
+
 // Value order of normalised double-float numbers: lexicographic on (h, l).
 __device__ __forceinline__ bool df_lt(dfl a, dfl b) { return a.h < b.h || (a.h == b.h && a.l < b.l); }
 

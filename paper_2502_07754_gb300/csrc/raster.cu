@@ -12,7 +12,7 @@
 // items turns them into each item's starting slot within the pixel and gives the
 // pixel totals; an exclusive scan over pixels gives record offsets.  Fill pass: the
 // same walk writes one 32-byte record per fragment at offset + item slot + running
-// index -- depth, triangle id, the fan's depth bound, opacity, colour, pixel -- so a
+// index -- depth (high), triangle id, the fan's depth bound, depth (low), colour, opacity -- so a
 // pixel's records come out in tile-list order, which the resolve relies on.
 #include "raster_common.cuh"
 
@@ -192,8 +192,8 @@ __global__ void __launch_bounds__(kRastWarps * 32) raster_kernel(const __grid_co
                 if (b != 0xffffffffu) {
                     const SplatSlot &sl = s_spl[f];
                     float4 *rec = a.frags + (size_t)kRecFwd * ((size_t)b + slot);
-                    rec[0] = make_float4(sp_t, __uint_as_float(S.fan[f]), __uint_as_float(S.q[f]), sp_a);
-                    rec[1] = make_float4(sl.col[0], sl.col[1], sl.col[2], 0.0f);
+                    rec[0] = make_float4(sp_t, __uint_as_float(S.fan[f]), __uint_as_float(S.q[f]), 0.0f);
+                    rec[1] = make_float4(sl.col[0], sl.col[1], sl.col[2], sp_a);
                 }
             }
             if (MODE == kFill && nf) {
@@ -205,7 +205,7 @@ __global__ void __launch_bounds__(kRastWarps * 32) raster_kernel(const __grid_co
                         const int jn = (j + 1 == K) ? 0 : j + 1;
                         const float izc = S.viz[f];
                         const float izj = S.viz[(1 + j) * STG + f], izn = S.viz[(1 + jn) * STG + f];
-                        const dfl zf = frag_depth_df(S, STG, f, j, jn, pxc, pyc, *sc.cam);
+                        const dfl zf = frag_depth_df(S, STG, K, f, j, pxc, pyc, *sc.cam);
                         // perspective-correct barycentrics from the accurate centre offsets
                         const float ox = __fsub_rn(S.cxh[f], pxc) + S.cxl[f];
                         const float oy = __fsub_rn(S.cyh[f], pyc) + S.cyl[f];
@@ -224,8 +224,8 @@ __global__ void __launch_bounds__(kRastWarps * 32) raster_kernel(const __grid_co
                         const float c2 = m0 * S.cb[vc] + m1 * S.cb[vj] + m2 * S.cb[vn];
                         const uint32_t tri = S.fan[f] * (uint32_t)K + (uint32_t)j;
                         float4 *rec = a.frags + (size_t)kRecFwd * ((size_t)b + slot);
-                        rec[0] = make_float4(zf.h, __uint_as_float(tri), __uint_as_float(S.q[f]), al);
-                        rec[1] = make_float4(c0, c1, c2, zf.l);
+                        rec[0] = make_float4(zf.h, __uint_as_float(tri), __uint_as_float(S.q[f]), zf.l);
+                        rec[1] = make_float4(c0, c1, c2, al);
                     }
                 }
             }

@@ -64,20 +64,19 @@ __device__ __forceinline__ void df_screen(float Xh, float Xl, float Zh, float Zl
 // positions relative to a pixel carry ~1e-6 px error instead of the ~1e-4 px of a
 // plain binary32 projection at 1080p.
 struct CentreProj {
-    float Xh, Yh, Zh, Zl;
+    float Xh, Yh, Zh, Xl, Yl, Zl;
     float xh, xl, yh, yl;
 };
 __device__ __forceinline__ CentreProj project_centre(const CamDev &c, const float m[3]) {
     float dh[3], dl[3];
 #pragma unroll
     for (int r = 0; r < 3; ++r) two_sum(m[r], -c.C[r], dh[r], dl[r]);
-    float Xl, Yl;
     CentreProj o;
-    df_dot(c.R, dh, dl, o.Xh, Xl);
-    df_dot(c.R + 3, dh, dl, o.Yh, Yl);
+    df_dot(c.R, dh, dl, o.Xh, o.Xl);
+    df_dot(c.R + 3, dh, dl, o.Yh, o.Yl);
     df_dot(c.R + 6, dh, dl, o.Zh, o.Zl);
-    df_screen(o.Xh, Xl, o.Zh, o.Zl, c.fx, c.cx, o.xh, o.xl);
-    df_screen(o.Yh, Yl, o.Zh, o.Zl, c.fy, c.cy, o.yh, o.yl);
+    df_screen(o.Xh, o.Xl, o.Zh, o.Zl, c.fx, c.cx, o.xh, o.xl);
+    df_screen(o.Yh, o.Yl, o.Zh, o.Zl, c.fy, c.cy, o.yh, o.yl);
     return o;
 }
 __device__ __forceinline__ void vertex_offset(const CamDev &c, const CentreProj &cp, const float d[3], float &du,
@@ -122,9 +121,10 @@ struct Stage {
     float *cxh, *cxl, *cyh, *cyl; // [CH] double-float screen position of the centre (values)
     float *du, *dv;               // [K][CH] screen offsets of the boundary vertices (values)
     float *cr, *cg, *cb, *ca;     // [KV][CH] vertex colour and opacity (values)
-    float *zh, *zl;               // [KV][CH] double-float view depth of each vertex (values)
     float *viz;                   // [KV][CH] 1 / depth (values: barycentric weights)
-    float *pah, *pal, *pbh, *pbl, *pnh, *pnl;   // [K][CH] triangle plane n.x fy, n.y fx, n.z fx fy (values)
+    // exact-order depth (frag_depth_df), double-float (high, low):
+    float *pc;                    // [6][CH] fx X_c, fy Y_c, Z_c of the centre
+    float *exh, *exl, *eyh, *eyl, *ezh, *ezl;   // [K][CH] view offsets R (b_i - c) of the boundary vertices
 };
 
 // What a stage holds: decisions only (count), or decisions and values (fill).
@@ -132,7 +132,7 @@ enum StageLevel { kStageDecide = 0, kStageValues = 1 };
 
 __host__ __device__ __forceinline__ size_t stage_bytes(int CH, int K, int level) {
     const int dec = 2 * (K + 1) + 5 * K;
-    const int val = level >= kStageValues ? 4 + 2 * K + 4 * (K + 1) + 3 * (K + 1) + 6 * K : 0;
+    const int val = level >= kStageValues ? 4 + 2 * K + 4 * (K + 1) + (K + 1) + 6 + 6 * K : 0;
     return (size_t)CH * (16 + 20 + 8 + 4 * (dec + val));
 }
 
@@ -166,15 +166,14 @@ __device__ __forceinline__ Stage stage_ptrs(char *base, int CH, int K, int level
         s.cg = f; f += KV * CH;
         s.cb = f; f += KV * CH;
         s.ca = f; f += KV * CH;
-        s.zh = f; f += KV * CH;
-        s.zl = f; f += KV * CH;
         s.viz = f; f += KV * CH;
-        s.pah = f; f += K * CH;
-        s.pal = f; f += K * CH;
-        s.pbh = f; f += K * CH;
-        s.pbl = f; f += K * CH;
-        s.pnh = f; f += K * CH;
-        s.pnl = f;
+        s.pc = f; f += 6 * CH;
+        s.exh = f; f += K * CH;
+        s.exl = f; f += K * CH;
+        s.eyh = f; f += K * CH;
+        s.eyl = f; f += K * CH;
+        s.ezh = f; f += K * CH;
+        s.ezl = f;
     }
     return s;
 }
@@ -278,89 +277,50 @@ __device__ __forceinline__ void stage_fans(const SceneDev &a, const Stage &s, in
         s.fan[slot] = fan;
         s.rect[slot] = make_int4(r.i0, r.i1, r.j0, r.j1);
     }
-    if (level < kStageValues) return;   // uniform across the warp
-    float m[3] = {0.0f, 0.0f, 0.0f};
-    dfl zc = df_make(1.0f);
-    if (active) {
-        m[0] = __ldg(p);
-        m[1] = __ldg(p + 1);
-        m[2] = __ldg(p + 2);
-        const CentreProj cp = project_centre(*a.cam, m);
-        zc = df_fast_two_sum(cp.Zh, cp.Zl);
-        if (sub == 0) {
-            s.cxh[slot] = cp.xh;
-            s.cxl[slot] = cp.xl;
-            s.cyh[slot] = cp.yh;
-            s.cyl[slot] = cp.yl;
-            s.zh[slot] = zc.h;
-            s.zl[slot] = zc.l;
-            s.viz[slot] = 1.0f / zc.h;
-        }
-        for (int i = sub; i < K; i += LPF) {
-            const float *pi = p + 3 * (1 + i);
-            const float d[3] = {__ldg(pi) - m[0], __ldg(pi + 1) - m[1], __ldg(pi + 2) - m[2]};
-            float du, dv, X, Y, Z;
-            vertex_offset(*a.cam, cp, d, du, dv, X, Y, Z);
-            s.du[i * CH + slot] = du;
-            s.dv[i * CH + slot] = dv;
-            // exact-order geometry, first half: the double-float view offset e = R (b_i - c)
-            // (kept in the plane arrays until the planes replace it) and view depth
-            const DfVec e = df_view_offset(*a.cam, m, pi);
-            const dfl zv = df_add(zc, e.z);
-            s.zh[(1 + i) * CH + slot] = zv.h;
-            s.zl[(1 + i) * CH + slot] = zv.l;
-            s.viz[(1 + i) * CH + slot] = 1.0f / zv.h;
-            s.pah[i * CH + slot] = e.x.h;
-            s.pal[i * CH + slot] = e.x.l;
-            s.pbh[i * CH + slot] = e.y.h;
-            s.pbl[i * CH + slot] = e.y.l;
-            s.pnh[i * CH + slot] = e.z.h;
-            s.pnl[i * CH + slot] = e.z.l;
-        }
-        const float *col = a.rgb + (size_t)fan * KV * 3;
-        const float *al = a.alpha + (size_t)fan * KV;
-        for (int k = sub; k < KV; k += LPF) {
-            s.cr[k * CH + slot] = __ldg(col + 3 * k);
-            s.cg[k * CH + slot] = __ldg(col + 3 * k + 1);
-            s.cb[k * CH + slot] = __ldg(col + 3 * k + 2);
-            s.ca[k * CH + slot] = __ldg(al + k);
-        }
+    if (level < kStageValues || !active) return;
+    const float m[3] = {__ldg(p), __ldg(p + 1), __ldg(p + 2)};
+    const CentreProj cp = project_centre(*a.cam, m);
+    const dfl zc = df_fast_two_sum(cp.Zh, cp.Zl);
+    if (sub == 0) {
+        s.cxh[slot] = cp.xh;
+        s.cxl[slot] = cp.xl;
+        s.cyh[slot] = cp.yh;
+        s.cyl[slot] = cp.yl;
+        s.viz[slot] = 1.0f / zc.h;
+        const dfl xf = df_mul_f(df_fast_two_sum(cp.Xh, cp.Xl), a.cam->fx);
+        const dfl yf = df_mul_f(df_fast_two_sum(cp.Yh, cp.Yl), a.cam->fy);
+        s.pc[slot] = xf.h;
+        s.pc[CH + slot] = xf.l;
+        s.pc[2 * CH + slot] = yf.h;
+        s.pc[3 * CH + slot] = yf.l;
+        s.pc[4 * CH + slot] = zc.h;
+        s.pc[5 * CH + slot] = zc.l;
     }
-    __syncwarp();   // every offset of the group is staged
-    // second half: per triangle (c, b_j, b_j+1) the plane normal n = e_j x e_j+1 in
-    // double-float, scaled to (n.x fy, n.y fx, n.z fx fy), written over the offsets once the
-    // whole warp has read them
-    constexpr int NJ = (kMaxK + LPF - 1) / LPF;
-    dfl pa[NJ], pb[NJ], pn[NJ];
-#pragma unroll
-    for (int t = 0; t < NJ; ++t) {
-        const int j = sub + t * LPF;
-        if (active && j < K) {
-            const int jn = (j + 1 == K) ? 0 : j + 1;
-            const int u = j * CH + slot, w = jn * CH + slot;
-            const dfl e1x = {s.pah[u], s.pal[u]}, e1y = {s.pbh[u], s.pbl[u]}, e1z = {s.pnh[u], s.pnl[u]};
-            const dfl e2x = {s.pah[w], s.pal[w]}, e2y = {s.pbh[w], s.pbl[w]}, e2z = {s.pnh[w], s.pnl[w]};
-            const dfl nx = df_add_fast(df_mul(e1y, e2z), df_neg(df_mul(e1z, e2y)));
-            const dfl ny = df_add_fast(df_mul(e1z, e2x), df_neg(df_mul(e1x, e2z)));
-            const dfl nz = df_add_fast(df_mul(e1x, e2y), df_neg(df_mul(e1y, e2x)));
-            pa[t] = df_mul_f(nx, a.cam->fy);
-            pb[t] = df_mul_f(ny, a.cam->fx);
-            pn[t] = df_mul_f(df_mul_f(nz, a.cam->fx), a.cam->fy);
-        }
+    for (int i = sub; i < K; i += LPF) {
+        const float *pi = p + 3 * (1 + i);
+        const float d[3] = {__ldg(pi) - m[0], __ldg(pi + 1) - m[1], __ldg(pi + 2) - m[2]};
+        float du, dv, X, Y, Z;
+        vertex_offset(*a.cam, cp, d, du, dv, X, Y, Z);
+        s.du[i * CH + slot] = du;
+        s.dv[i * CH + slot] = dv;
+        // the exact view offset e = R (b_i - c) in double-float, for the fragment depths
+        const DfVec e = df_view_offset(*a.cam, m, pi);
+        s.viz[(1 + i) * CH + slot] = 1.0f / df_add(zc, e.z).h;
+        const int u = i * CH + slot;
+        s.exh[u] = e.x.h;
+        s.exl[u] = e.x.l;
+        s.eyh[u] = e.y.h;
+        s.eyl[u] = e.y.l;
+        s.ezh[u] = e.z.h;
+        s.ezl[u] = e.z.l;
     }
-    __syncwarp();   // all offsets read
-#pragma unroll
-    for (int t = 0; t < NJ; ++t) {
-        const int j = sub + t * LPF;
-        if (active && j < K) {
-            const int u = j * CH + slot;
-            s.pah[u] = pa[t].h;
-            s.pal[u] = pa[t].l;
-            s.pbh[u] = pb[t].h;
-            s.pbl[u] = pb[t].l;
-            s.pnh[u] = pn[t].h;
-            s.pnl[u] = pn[t].l;
-        }
+    const float *col = a.rgb + (size_t)fan * KV * 3;
+    const float *al = a.alpha + (size_t)fan * KV;
+    for (int k = sub; k < KV; k += LPF) {
+        s.cr[k * CH + slot] = __ldg(col + 3 * k);
+        s.cg[k * CH + slot] = __ldg(col + 3 * k + 1);
+        s.cb[k * CH + slot] = __ldg(col + 3 * k + 2);
+        s.ca[k * CH + slot] = __ldg(al + k);
     }
 }
 
@@ -406,32 +366,38 @@ __device__ __forceinline__ uint32_t cover_mask(const Stage &S, int CH, int K, in
     return hits;
 }
 
-// Depth of triangle j of staged fan f at the pixel centre (pxc, pyc) (absolute screen
-// coordinates), in double-float: the view depth where the pixel's ray meets the
-// triangle's plane, Z = Zc + Zc (n.x (xc - x) / fx + n.y (yc - y) / fy) / (n . r) with
-// r = ((x - cx) / fx, (y - cy) / fy, 1) and (xc, yc, Zc) the centre's screen position and
-// depth (both scaled here by fx fy); this equals 1 / sum_k (lambda_k / Z_k) of the
-// perspective-correct barycentrics.  Clamped to the triangle's vertex depths, where a
-// covered centre lies (the clamp only acts where the decided coverage and the exact
-// plane differ by rounding; a ray parallel to the plane takes the nearest vertex depth).
-__device__ __forceinline__ dfl frag_depth_df(const Stage &S, int CH, int f, int j, int jn, float pxc, float pyc,
+// Depth of triangle j = (c, b_j, b_j+1) of staged fan f at the pixel centre (pxc, pyc)
+// (absolute screen coordinates), in double-float: the view depth where the pixel's ray
+// r = ((x - cx) / fx, (y - cy) / fy, 1) meets the triangle's plane, Z = n . P_c / n . r with
+// n = e_j x e_j+1 the normal from the vertices' exact view offsets and P_c the centre's
+// view position (numerator and denominator both scaled by fx fy), which equals
+// 1 / sum_k (lambda_k / Z_k) of the perspective-correct barycentrics.  Clamped to the
+// triangle's vertex depths, where a covered centre lies (the clamp acts only where the
+// decided coverage and the exact plane differ by rounding; a ray parallel to the plane
+// takes the least vertex depth).
+__device__ __forceinline__ dfl frag_depth_df(const Stage &S, int CH, int K, int f, int j, float pxc, float pyc,
                                              const CamDev &c) {
-    const int t = j * CH + f;
-    const dfl pa = {S.pah[t], S.pal[t]}, pb = {S.pbh[t], S.pbl[t]}, pn = {S.pnh[t], S.pnl[t]};
-    const dfl ox = df_add_f(df_two_sum(S.cxh[f], -pxc), S.cxl[f]);
-    const dfl oy = df_add_f(df_two_sum(S.cyh[f], -pyc), S.cyl[f]);
-    const dfl num = df_add_fast(df_mul(pa, ox), df_mul(pb, oy));
-    const dfl den = df_add_fast(df_add_fast(df_mul(pa, df_two_sum(pxc, -c.cx)), df_mul(pb, df_two_sum(pyc, -c.cy))), pn);
-    const dfl zc = {S.zh[f], S.zl[f]};
-    const dfl z1 = {S.zh[(1 + j) * CH + f], S.zl[(1 + j) * CH + f]};
-    const dfl z2 = {S.zh[(1 + jn) * CH + f], S.zl[(1 + jn) * CH + f]};
+    const int jn = (j + 1 == K) ? 0 : j + 1;
+    const int u = j * CH + f, w = jn * CH + f;
+    const dfl e1x = {S.exh[u], S.exl[u]}, e1y = {S.eyh[u], S.eyl[u]}, e1z = {S.ezh[u], S.ezl[u]};
+    const dfl e2x = {S.exh[w], S.exl[w]}, e2y = {S.eyh[w], S.eyl[w]}, e2z = {S.ezh[w], S.ezl[w]};
+    const dfl xf = {S.pc[f], S.pc[CH + f]}, yf = {S.pc[2 * CH + f], S.pc[3 * CH + f]};
+    const dfl zc = {S.pc[4 * CH + f], S.pc[5 * CH + f]};
+    const dfl nx = df_add_fast(df_mul(e1y, e2z), df_neg(df_mul(e1z, e2y)));
+    const dfl ny = df_add_fast(df_mul(e1z, e2x), df_neg(df_mul(e1x, e2z)));
+    const dfl nz = df_add_fast(df_mul(e1x, e2y), df_neg(df_mul(e1y, e2x)));
+    const dfl pa = df_mul_f(nx, c.fy), pb = df_mul_f(ny, c.fx), pn = df_mul_f(df_mul_f(nz, c.fx), c.fy);
+    const dfl num = df_add_fast(df_add_fast(df_mul(pa, xf), df_mul(pb, yf)), df_mul(pn, zc));
+    const dfl den = df_add_fast(df_add_fast(df_mul(pa, df_two_sum(pxc, -c.cx)), df_mul(pb, df_two_sum(pyc, -c.cy))),
+                                pn);
+    const dfl z1 = df_add_fast(zc, e1z), z2 = df_add_fast(zc, e2z);
     dfl lo = zc, hi = zc;
     if (df_lt(z1, lo)) lo = z1;
     if (df_lt(z2, lo)) lo = z2;
     if (df_lt(hi, z1)) hi = z1;
     if (df_lt(hi, z2)) hi = z2;
     if (den.h == 0.0f) return lo;
-    dfl z = df_add_fast(zc, df_div(df_mul(zc, num), den));
+    dfl z = df_div_rcp(num, den);
     if (!(z.h == z.h)) return lo;   // NaN
     if (df_lt(z, lo)) z = lo;
     if (df_lt(hi, z)) z = hi;

@@ -9,7 +9,7 @@
 // nearest dropped fragment and the earliest record it dropped, finishes the pass with
 // everything strictly nearer, and re-reads its own records from that point, skipping
 // fragments at or before the last committed one.  Order: (depth, triangle id), the depth
-// a double-float value (high part in the record's first word, low part in its last).
+// a double-float value (high part in the record's first word, low part in its fourth).
 // Compositing stops once the transmittance falls below T_eps.
 //
 // Both passes visit the pixels in orders that pixel_order_kernel builds after the pixel
@@ -157,9 +157,8 @@ __global__ void __launch_bounds__(kResolveThreads) resolve_kernel(const __grid_c
     auto commit_front = [&]() {
         // colour and opacity are re-read from the record (an L1 / L2 hit) rather than
         // carried in the pending buffer, which keeps the buffer at three registers a slot
-        const float4 *rc = rec + (size_t)RS * ki[0];
-        const float al = rc[0].w;
-        const float4 col = rc[1];
+        const float4 col = rec[(size_t)RS * ki[0] + 1];
+        const float al = col.w;
         const float c0 = col.x, c1 = col.y, c2 = col.z;
         const float w = T * al;
         C0 += w * c0;
@@ -187,7 +186,7 @@ __global__ void __launch_bounds__(kResolveThreads) resolve_kernel(const __grid_c
     while (!done) {
         for (int i = start; i < n && !done; ++i) {
             const float4 r0 = rec[RS * i];
-            const float z = r0.x, zl = rec[RS * i + 1].w;
+            const float z = r0.x, zl = r0.w;
             const uint32_t tri = __float_as_uint(r0.y), qk = __float_as_uint(r0.z);
             while (nb > 0 && !done && depth_q(kz[0], a.depth_bits) < qk) commit_front();
             if (done) break;
@@ -283,8 +282,8 @@ __global__ void __launch_bounds__(kResolveThreads) resolve_bwd_kernel(const __gr
         const uint32_t nidx = c + 1 < n ? ord[c + 1] : 0u;   // the next index loads early
         const float4 *rc = rec + (size_t)kRecFwd * idx;
         const float4 r0 = rc[0];
-        const float al = r0.w;
         const float4 col = rc[1];
+        const float al = col.w;
         const float w = T * al;
         const float nC0 = C0 + w * col.x, nC1 = C1 + w * col.y, nC2 = C2 + w * col.z;
         const float inv = 1.0f / fmaxf(1.0f - al, 1e-6f);
