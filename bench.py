@@ -308,8 +308,9 @@ def stage_report(stage_ms, stage_n, info, sc, V, K, npx, local):
     tc_peak = float(peaks.get("bf16_tflops", 1900.0))
     nb = (sc.sh_degree + 1) ** 2 * 3 * (2 if sc.sh_bf16 else 4)
     hbm_bytes = {"mesh_build": sc.n * (44 + nb) + V * 28,
-                 "bin": V * 12 + info.pairs * 12,
-                 "sort": info.pairs * (8 + 24 * ((info.sort_bits + 7) // 8)),
+                 "bin": V * 12 + info.pairs * 8,
+                 # one histogram read, then per pass each 8-byte element read and written
+                 "sort": info.pairs * (8 + 16 * ((info.sort_bits + 7) // 8)),
                  "loss": npx * 48,
                  "adam": V * 7 * 28}
     stages = {}

@@ -101,9 +101,14 @@ RenderLayout render_layout(int64_t n_fans, int K, const ms_camera *cams, int n_v
     L.n_tiles = (int)tiles;
     L.npx = npx;
     L.tile_bits = bits_for(L.n_tiles);
-    // automatic depth bits: as many as fit (<= 27) without a further byte of sort key
-    // beyond tile bits + 20
-    L.depth_bits = p.depth_bits ? p.depth_bits : std::min(27, 8 * ((L.tile_bits + 20 + 7) / 8) - L.tile_bits);
+    // A sort element is one 64-bit word: tile | quantised depth bound | fan id, the fan id in
+    // the low fan_bits bits; the radix passes sort the tile and depth bits above them.
+    // Automatic depth bits: as many as fit (<= 27) without a further byte of sort key beyond
+    // tile bits + 20, and within the word.
+    L.fan_bits = bits_for(n_fans);
+    L.depth_bits = p.depth_bits ? p.depth_bits
+                                : std::min(std::min(27, 8 * ((L.tile_bits + 20 + 7) / 8) - L.tile_bits),
+                                           64 - L.fan_bits - L.tile_bits);
     L.key_bits = L.tile_bits + L.depth_bits;
     L.passes = (L.key_bits + 7) / 8;
     L.n_fans = n_fans;
@@ -121,7 +126,7 @@ RenderLayout render_layout(int64_t n_fans, int K, const ms_camera *cams, int n_v
     L.frag_cap = fcap;
     L.bin_fan_blocks = (n_fans + 255) / 256;
     L.bin_blocks = L.bin_fan_blocks * n_views;
-    L.sort_blocks = (cap + 4095) / 4096;
+    L.sort_blocks = (cap + 8191) / 8192;   // sort tiles of 8192 elements
     L.scan_blocks = (npx + 2047) / 2048;
     L.max_items = L.n_tiles + (cap + kItemFans - 1) / kItemFans;
     L.tscan_blocks = ((int64_t)L.n_tiles + 2047) / 2048;
@@ -136,8 +141,6 @@ RenderLayout render_layout(int64_t n_fans, int K, const ms_camera *cams, int n_v
     L.off_pbucket = o;           o = align_up(o + 2 * 256 * 4, 256);   // pixel-count histogram, fill cursors
     L.off_keys0 = o;             o = align_up(o + 8 * (size_t)cap, 256);   // (zeroed prefix ends here)
     L.off_keys1 = o;             o = align_up(o + 8 * (size_t)cap, 256);
-    L.off_vals0 = o;             o = align_up(o + 4 * (size_t)cap, 256);
-    L.off_vals1 = o;             o = align_up(o + 4 * (size_t)cap, 256);
     L.off_tile_nitems = o;       o = align_up(o + 4 * (size_t)L.n_tiles, 256);
     L.off_tile_ibase = o;        o = align_up(o + 4 * (size_t)L.n_tiles, 256);
     L.off_items = o;             o = align_up(o + 16 * (size_t)L.max_items, 256);
@@ -183,7 +186,9 @@ static ms_status check_render_args(const float *xyz, const float *rgb, const flo
     if (p.depth_bits != 0 && (p.depth_bits < 8 || p.depth_bits > 31))
         return fail(MS_ERR_INVALID, "depth_bits %d", p.depth_bits);
     L = render_layout(n_fans, K, cams, n_views, p);
-    if (L.key_bits > 64) return fail(MS_ERR_INVALID, "sort key needs %d bits", L.key_bits);
+    if (L.key_bits + L.fan_bits > 64 || L.depth_bits < 8)
+        return fail(MS_ERR_INVALID, "sort element needs %d tile + %d depth + %d fan bits (> 64 or depth < 8)",
+                    L.tile_bits, L.depth_bits, L.fan_bits);
     if (L.cap >= (1ll << 30)) return fail(MS_ERR_INVALID, "pair capacity %lld >= 2^30", (long long)L.cap);
     if (L.frag_cap >= (1ll << 32)) return fail(MS_ERR_INVALID, "fragment capacity %lld >= 2^32", (long long)L.frag_cap);
     if (L.npx >= (1ll << 32)) return fail(MS_ERR_INVALID, "%lld pixels over all views >= 2^32", (long long)L.npx);

@@ -1,5 +1,5 @@
-// Tile binning of fans: project, count overlapped tiles, scan and emit
-// (tile << depth_bits | quantised min depth, fan id) pairs -- one pass.
+// Tile binning of fans: project, count overlapped tiles, scan and emit one 64-bit sort
+// element per (tile, fan) pair, tile | quantised min depth | fan id -- one pass.
 //
 // The binning unit is the fan (K triangles sharing the centre), not the single
 // triangle: a fan is a few pixels wide, so one record per (tile, fan) instead of per
@@ -19,13 +19,12 @@ constexpr float kKeyMargin = 1.0f - 0x1p-20f;
 struct BinArgs {
     const float *xyz;
     int64_t n_fans;
-    int K, tile_shift, depth_bits;
+    int K, tile_shift, depth_bits, fan_bits;
     float key_scale;
     int64_t cap, fan_blocks;
     unsigned n_tiles, sort_bits;
     Status *st;
     unsigned long long *keys;
-    uint32_t *vals;
     ViewTable vt;
     float4 *dec;               // [view][vertex] decided (xs, ys, Z, 1/Z), read by the raster passes
     int64_t V;
@@ -40,7 +39,7 @@ __global__ void __launch_bounds__(kBinThreads) bin_kernel(const __grid_constant_
     const int64_t cap = a.cap;
     Status *st = a.st;
     unsigned long long *__restrict__ keys = a.keys;
-    uint32_t *__restrict__ vals = a.vals;
+    const int fan_bits = a.fan_bits;
     extern __shared__ float s_xyz[];   // kBinThreads * (K+1) * 3
     __shared__ uint32_t s_off[kBinThreads + 1];
     __shared__ uint32_t s_rect[kBinThreads][2];   // (tx0 | ty0 << 16), (w | h << 16)
@@ -176,8 +175,7 @@ __global__ void __launch_bounds__(kBinThreads) bin_kernel(const __grid_constant_
         const uint32_t w = r1 & 0xFFFFu;
         const uint32_t tx = (r0 & 0xFFFFu) + k % w, ty = (r0 >> 16) + k / w;
         const unsigned long long tile = tile_base + (unsigned long long)ty * tiles_x + tx;
-        keys[idx] = ((tile << depth_bits) | s_q[lo]) & tmask;
-        vals[idx] = (uint32_t)(f0 + lo);
+        keys[idx] = ((((tile << depth_bits) | s_q[lo]) << fan_bits) | (unsigned long long)(f0 + lo)) & tmask;
     }
 }
 
@@ -195,6 +193,7 @@ cudaError_t launch_bin(const RenderArgs &ra, cudaStream_t st) {
     a.tile_shift = 0;
     while ((1 << a.tile_shift) < L.tile) ++a.tile_shift;
     a.depth_bits = L.depth_bits;
+    a.fan_bits = L.fan_bits;
     a.key_scale = ra.key_scale;
     a.cap = L.cap;
     a.fan_blocks = L.bin_fan_blocks;
@@ -202,7 +201,6 @@ cudaError_t launch_bin(const RenderArgs &ra, cudaStream_t st) {
     a.sort_bits = (unsigned)(8 * L.passes);
     a.st = reinterpret_cast<Status *>(ra.ws + L.off_status);
     a.keys = reinterpret_cast<unsigned long long *>(ra.ws + L.off_keys0);
-    a.vals = reinterpret_cast<uint32_t *>(ra.ws + L.off_vals0);
     a.vt = ra.vt;
     a.dec = reinterpret_cast<float4 *>(ra.ws + L.off_dec);
     a.V = L.V;

@@ -22,10 +22,9 @@ namespace {
 
 struct RastArgs {
     const float *xyz, *rgb, *alpha;
-    int K, depth_bits;
+    int K, depth_bits, fan_bits;
     ViewTable vt;
-    const unsigned long long *keys;
-    const uint32_t *vals;
+    const unsigned long long *keys;   // sorted elements tile | depth bound | fan id
     const uint4 *items;        // (tile, start, end, index within tile)
     uint32_t *icnt;            // [item][tile pixels]: counts, then in-pixel starting slots
     const uint32_t *offsets;
@@ -114,11 +113,14 @@ __global__ void __launch_bounds__(kRastWarps * 32) raster_kernel(const __grid_co
             uint32_t q = 0, fan = 0;
             if (slot < cnt) {
                 const uint32_t li = cb + slot;
-                q = (uint32_t)(__ldg(a.keys + li) & ((1ull << a.depth_bits) - 1ull));
-                fan = __ldg(a.vals + li);
+                const unsigned long long e = __ldg(a.keys + li);
+                q = (uint32_t)((e >> a.fan_bits) & ((1ull << a.depth_bits) - 1ull));
+                fan = (uint32_t)(e & ((1ull << a.fan_bits) - 1ull));
             }
             stage_fans<LPF>(sc, S, K, lane, slot < cnt, fan, q, LEVEL);
-            if (SPLAT && lane < cnt) s_spl[lane] = splat_setup(a.spl, *sc.cam, __ldg(a.vals + cb + lane));
+            if (SPLAT && lane < cnt)
+                s_spl[lane] = splat_setup(a.spl, *sc.cam,
+                                          (uint32_t)(__ldg(a.keys + cb + lane) & ((1ull << a.fan_bits) - 1ull)));
         }
         __syncwarp();
         // The staged fans' rectangles (clipped to the tile) form one packed (fan, pixel)
@@ -439,8 +441,8 @@ RastArgs make_args(const RenderArgs &ra) {
     a.K = ra.K;
     a.vt = ra.vt;
     a.depth_bits = L.depth_bits;
+    a.fan_bits = L.fan_bits;
     a.keys = reinterpret_cast<const unsigned long long *>(ra.ws + (L.passes & 1 ? L.off_keys1 : L.off_keys0));
-    a.vals = reinterpret_cast<const uint32_t *>(ra.ws + (L.passes & 1 ? L.off_vals1 : L.off_vals0));
     a.items = reinterpret_cast<const uint4 *>(ra.ws + L.off_items);
     a.icnt = reinterpret_cast<uint32_t *>(ra.ws + L.off_icnt);
     a.offsets = reinterpret_cast<const uint32_t *>(ra.ws + L.off_offsets);
