@@ -95,6 +95,8 @@ typedef struct {
     int32_t depth_bits;     /* depth bits in the sort key, 8..31; 0 = automatic: the most (<= 27) that
                                keep the key within the bytes of tile bits + 20 */
     int64_t frag_capacity;  /* per-pixel fragment records of the workspace; 0 = 8 W H + 65536 */
+    const uint32_t *face_mask;  /* NULL: every face of every fan is drawn; else device, one word per fan,
+                                   bit j set = triangle j drawn (the faces ms_prune_faces keeps) */
 } ms_render_params;
 
 /* Device-side outcome of the last ms_render / ms_render_backward on a workspace. */
@@ -130,7 +132,8 @@ typedef enum {
 MS_API const char *ms_version(void);
 /* Message of the last host-side error of this thread (static storage). */
 MS_API const char *ms_last_error(void);
-/* Fills the defaults (tile 16, kbuf 8, T_eps 1e-5, black background, capacities 0, depth bits 0 = automatic). */
+/* Fills the defaults (tile 16, kbuf 8, T_eps 1e-5, black background, capacities 0, depth bits 0 = automatic,
+ * no face mask). */
 MS_API void ms_render_params_default(ms_render_params *p);
 
 /*
@@ -176,6 +179,21 @@ MS_API ms_status ms_mesh_build(const float *means, const float *log_scales, cons
  * K = 8), or -1 for K outside 3..16 or a NULL pointer.
  */
 MS_API int32_t ms_three_fan_copies(int32_t K, int32_t *first_copy);
+
+/*
+ * Gradients of the shared vertices of a three-fan soup (Sec. 3 "Transformation for 3D
+ * Gaussians": the three fans of a Gaussian share the centre and the axis tips two fans
+ * reach, i.e. one vertex appears as several copies in the implicit layout of
+ * ms_mesh_build_3d).  For every Gaussian, each vertex slot receives the sum of the
+ * gradients of all copies of its vertex (the gradient of the shared vertex), summed in slot
+ * order, so every copy holds the same value and an optimiser step keeps the copies equal.
+ *   Either grad (device, 16-byte aligned: the gradient sums ms_render_backward leaves in a
+ *   render workspace, at ms_render_grad_offset; two float4 per vertex) or, when grad is
+ *   NULL, d_xyz, d_rgb (3 N (K+1) x 3) and d_alpha (3 N (K+1)): device, updated in place.
+ * One kernel launch on `stream`; MS_ERR_INVALID for K outside 3..16, N < 0 or NULL arrays.
+ */
+MS_API ms_status ms_three_fan_sum_copies(float *d_xyz, float *d_rgb, float *d_alpha, void *grad, int64_t N,
+                                         int32_t K, void *stream);
 
 MS_API ms_status ms_mesh_build_3d(const float *means, const float *log_scales, const float *quats,
                                   const float *opacity, const void *sh, int32_t sh_dtype, int32_t sh_degree, int64_t N,
@@ -415,6 +433,21 @@ MS_API ms_status ms_fine_tune_loss(const float *img_rgba, const float *target_rg
  * Three kernel launches on `stream`.
  */
 MS_API size_t ms_prune_workspace_size(int64_t n_fans);
+/*
+ * The pruning step of Sec. 3 per face: bit j of a fan's face mask (face (c, b_j, b_j+1),
+ * the face_mask of ms_render_params) stays set while some vertex of the face has opacity
+ * at or above `threshold`, ANDed with the fan's earlier mask (face_mask_in, device, one
+ * word per fan; NULL = all faces).  Fans left with no face are removed with their K + 1
+ * vertices (with no earlier mask, exactly the fans ms_prune_fans removes); the others are
+ * kept whole and compacted in order, and face_mask_out (device, one word per input fan,
+ * the kept fans' masks at its front; NULL to skip) receives their masks.  Other arguments,
+ * workspace and errors as ms_prune_fans.
+ */
+MS_API ms_status ms_prune_faces(const float *xyz, const float *rgb, const float *alpha, const float *m,
+                                const float *v, const uint32_t *face_mask_in, int64_t n_fans, int32_t K,
+                                float threshold, float *xyz_out, float *rgb_out, float *alpha_out, float *m_out,
+                                float *v_out, uint32_t *face_mask_out, int64_t *n_kept, void *workspace,
+                                size_t ws_bytes, void *stream);
 MS_API ms_status ms_prune_fans(const float *xyz, const float *rgb, const float *alpha, const float *m, const float *v,
                                int64_t n_fans, int32_t K, float threshold, float *xyz_out, float *rgb_out,
                                float *alpha_out, float *m_out, float *v_out, int64_t *n_kept, void *workspace,

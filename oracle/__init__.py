@@ -280,3 +280,47 @@ def prune_fans(xyz, rgb, alpha, K, threshold=PRUNE_THRESHOLD, moments=()):
                                      m[3 * V:6 * V].reshape(V, 3)[vsel].reshape(-1), m[6 * V:7 * V][vsel]]))
     return (np.asarray(xyz).reshape(V, 3)[vsel], np.asarray(rgb).reshape(V, 3)[vsel], np.asarray(alpha).reshape(V)[vsel],
             out_m, fans)
+
+
+def face_masks(alpha, K, threshold=PRUNE_THRESHOLD, face_mask=None):
+    """Per-face pruning rule of Sec. 3 ("Optimization and Pruning") as one mask word per
+    fan: bit j (face (c, b_j, b_{j+1 mod K})) is set unless all three of the face's vertex
+    opacities are below the threshold, and stays clear once an earlier mask cleared it."""
+    a = np.asarray(alpha).reshape(-1, K + 1)
+    low = a < threshold
+    b = low[:, 1:]
+    dead = low[:, :1] & b & np.roll(b, -1, axis=1)
+    m = ((~dead).astype(np.int64) << np.arange(K)).sum(axis=1)
+    if face_mask is not None:
+        m &= np.asarray(face_mask, np.int64)
+    return m
+
+
+def prune_faces(xyz, rgb, alpha, K, face_mask=None, threshold=PRUNE_THRESHOLD, moments=()):
+    """Pruning step of Sec. 3 per face: the faces of face_masks go; a fan left with no face
+    is removed with its K + 1 vertices (its vertices are used by no face), every other fan
+    is kept whole and in order (each of its vertices lies in a kept face or is the shared
+    centre).  moments: arrays in the optimiser layout [xyz 3V | rgb 3V | alpha V], compacted
+    alike.  Returns (xyz, rgb, alpha, [moments...], masks of the kept fans, kept fan
+    indices)."""
+    masks = face_masks(alpha, K, threshold, face_mask)
+    fans = np.nonzero(masks != 0)[0]
+    a = np.asarray(alpha).reshape(-1, K + 1)
+    vsel = (fans[:, None] * (K + 1) + np.arange(K + 1)).reshape(-1)
+    V = a.size
+    out_m = []
+    for m in moments:
+        m = np.asarray(m)
+        out_m.append(np.concatenate([m[:3 * V].reshape(V, 3)[vsel].reshape(-1),
+                                     m[3 * V:6 * V].reshape(V, 3)[vsel].reshape(-1), m[6 * V:7 * V][vsel]]))
+    return (np.asarray(xyz).reshape(V, 3)[vsel], np.asarray(rgb).reshape(V, 3)[vsel],
+            np.asarray(alpha).reshape(V)[vsel], out_m, masks[fans], fans)
+
+
+def masked_fan_tris(n, K, masks=None):
+    """Triangles (fan topology) of the faces a mask keeps, in triangle order."""
+    t = fan_tris(n, K)
+    if masks is None:
+        return t
+    keep = ((np.asarray(masks, np.int64)[:, None] >> np.arange(K)) & 1).astype(bool).reshape(-1)
+    return t[keep]

@@ -33,7 +33,8 @@ class Camera(C.Structure):
 
 class RenderParams(C.Structure):
     _fields_ = [("tile", C.c_int32), ("kbuf", C.c_int32), ("T_eps", C.c_float), ("bg", C.c_float * 3),
-                ("pair_capacity", C.c_int64), ("depth_bits", C.c_int32), ("frag_capacity", C.c_int64)]
+                ("pair_capacity", C.c_int64), ("depth_bits", C.c_int32), ("frag_capacity", C.c_int64),
+                ("face_mask", C.c_void_p)]
 
 
 class RenderInfo(C.Structure):
@@ -61,6 +62,7 @@ _SIGS = {
     "ms_mesh_build": (C.c_int, [_P, _P, _P, _P, _P, C.c_int32, C.c_int32, C.c_int64, _P, _P, _P, _P, _P, _P, _P]),
     "ms_mesh_build_3d": (C.c_int, [_P, _P, _P, _P, _P, C.c_int32, C.c_int32, C.c_int64, _P, _P, _P, _P, _P, _P]),
     "ms_three_fan_copies": (C.c_int32, [C.c_int32, _P]),
+    "ms_three_fan_sum_copies": (C.c_int, [_P, _P, _P, _P, C.c_int64, C.c_int32, _P]),
     "ms_render_workspace_size": (C.c_size_t, [C.c_int64, C.c_int32, _P, _P]),
     "ms_render": (C.c_int, [_P, _P, _P, C.c_int64, C.c_int32, _P, _P, _P, _P, C.c_size_t, _P]),
     "ms_render_backward": (C.c_int, [_P, _P, _P, C.c_int64, C.c_int32, _P, _P, _P, _P, _P, _P, _P, _P, C.c_size_t,
@@ -72,6 +74,8 @@ _SIGS = {
     "ms_prune_workspace_size": (C.c_size_t, [C.c_int64]),
     "ms_prune_fans": (C.c_int, [_P, _P, _P, _P, _P, C.c_int64, C.c_int32, C.c_float, _P, _P, _P, _P, _P, _P, _P,
                                 C.c_size_t, _P]),
+    "ms_prune_faces": (C.c_int, [_P, _P, _P, _P, _P, _P, C.c_int64, C.c_int32, C.c_float, _P, _P, _P, _P, _P, _P, _P,
+                                 _P, C.c_size_t, _P]),
     "ms_adam_step": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, C.c_int64, C.c_int32, C.c_float, C.c_float, C.c_float,
                                C.c_float, C.c_float, _P]),
     "ms_batch_workspace_size": (C.c_size_t, [C.c_int64, C.c_int32, _P, C.c_int32, _P]),

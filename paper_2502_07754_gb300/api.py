@@ -56,7 +56,9 @@ def camera_struct(cam) -> _lib.Camera:
     return c
 
 
-def render_params(tile=16, kbuf=8, T_eps=1e-5, bg=(0.0, 0.0, 0.0), pair_capacity=0, depth_bits=0):
+def render_params(tile=16, kbuf=8, T_eps=1e-5, bg=(0.0, 0.0, 0.0), pair_capacity=0, depth_bits=0, face_mask=None):
+    """face_mask: None (every face drawn) or a device int32 tensor, one word per fan (bit j:
+    face j drawn); the tensor must stay alive while the parameters are used."""
     p = _lib.RenderParams()
     lib().ms_render_params_default(C.byref(p))
     p.tile, p.kbuf, p.T_eps = int(tile), int(kbuf), float(T_eps)
@@ -64,6 +66,10 @@ def render_params(tile=16, kbuf=8, T_eps=1e-5, bg=(0.0, 0.0, 0.0), pair_capacity
         p.bg[i] = float(bg[i])
     p.pair_capacity = int(pair_capacity)
     p.depth_bits = int(depth_bits)
+    if face_mask is not None:
+        if face_mask.dtype != torch.int32 or not face_mask.is_cuda or not face_mask.is_contiguous():
+            raise ValueError("face_mask must be a contiguous int32 CUDA tensor")
+        p.face_mask = face_mask.data_ptr()
     return p
 
 
@@ -119,6 +125,20 @@ def three_fan_copies(K):
     if n < 0:
         raise ValueError(f"K={K} outside 3..16")
     return list(buf), int(n)
+
+
+def three_fan_sum_copies(N, K, grads=None, renderer=None, stream=None):
+    """Gives every copy of a shared three-fan vertex the sum of its copies' gradients
+    (ms_three_fan_sum_copies), in place: either grads = (d_xyz, d_rgb, d_alpha) or the
+    gradient sums a renderer's backward left in its workspace."""
+    if renderer is not None:
+        check(lib().ms_three_fan_sum_copies(None, None, None, renderer.grad_ptr(), int(N), int(K),
+                                            _stream(stream, renderer.ws)))
+        return None
+    d_xyz, d_rgb, d_alpha = grads
+    check(lib().ms_three_fan_sum_copies(_ptr(d_xyz), _ptr(d_rgb), _ptr(d_alpha), None, int(N), int(K),
+                                        _stream(stream, d_xyz, d_rgb, d_alpha)))
+    return grads
 
 
 class Renderer:
@@ -439,6 +459,31 @@ def prune_fans(xyz, rgb, alpha, K, threshold=math.exp(-4.0), m=None, v=None, str
     # alpha Vk], at the front of the output
     cut = lambda t: t[:7 * Vk] if t is not None else None
     return outs[0][:Vk], outs[1][:Vk], outs[2][:Vk], cut(mo), cut(vo), k
+
+
+def prune_faces(xyz, rgb, alpha, K, face_mask=None, threshold=math.exp(-4.0), m=None, v=None, stream=None):
+    """Per-face pruning step (ms_prune_faces): clears the faces whose three vertex
+    opacities are all below `threshold` in each fan's face mask (int32 tensor, one word per
+    fan; None = all faces), removes fans left without faces and compacts the rest with
+    their Adam moments and masks.  Returns (xyz, rgb, alpha, m, v, face_mask, n_kept);
+    reads the kept count back, so it synchronises the stream."""
+    n = xyz.shape[0] // (K + 1)
+    outs = [torch.empty_like(t) for t in (xyz, rgb, alpha)]
+    mo = torch.empty_like(m) if m is not None else None
+    vo = torch.empty_like(v) if v is not None else None
+    mask_o = torch.empty(max(n, 1), dtype=torch.int32, device=xyz.device)
+    n_kept = torch.zeros(1, dtype=torch.int64, device=xyz.device)
+    ws = torch.empty(max(lib().ms_prune_workspace_size(n), 1), dtype=torch.uint8, device=xyz.device)
+    opt = lambda t: _ptr(t) if t is not None else None
+    check(lib().ms_prune_faces(_ptr(xyz), _ptr(rgb), _ptr(alpha), opt(m), opt(v), opt(face_mask), n, int(K),
+                               float(threshold), *[_ptr(t) for t in outs], opt(mo), opt(vo), _ptr(mask_o),
+                               _ptr(n_kept), _ptr(ws), ws.numel(),
+                               _stream(stream, *outs, mo, vo, mask_o, n_kept, ws)))
+    (stream or torch.cuda.current_stream()).synchronize()
+    k = int(n_kept.item())
+    Vk = k * (K + 1)
+    cut = lambda t: t[:7 * Vk] if t is not None else None
+    return outs[0][:Vk], outs[1][:Vk], outs[2][:Vk], cut(mo), cut(vo), mask_o[:k], k
 
 
 def mse(img_rgba, target_rgba, stream=None):

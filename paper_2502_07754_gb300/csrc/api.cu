@@ -362,6 +362,7 @@ MS_API void ms_render_params_default(ms_render_params *p) {
     p->kbuf = 8;
     p->T_eps = 1e-5f;
     p->depth_bits = 0;
+    p->face_mask = nullptr;
 }
 
 static ms_status mesh_build_common(const float *means, const float *log_scales, const float *quats,
@@ -629,10 +630,11 @@ MS_API size_t ms_prune_workspace_size(int64_t n_fans) {
     return align_up(prune_scratch_bytes(n_fans), 256) + 256;
 }
 
-MS_API ms_status ms_prune_fans(const float *xyz, const float *rgb, const float *alpha, const float *m, const float *v,
-                               int64_t n_fans, int32_t K, float threshold, float *xyz_out, float *rgb_out,
-                               float *alpha_out, float *m_out, float *v_out, int64_t *n_kept, void *workspace,
-                               size_t ws_bytes, void *stream) {
+MS_API ms_status ms_prune_faces(const float *xyz, const float *rgb, const float *alpha, const float *m, const float *v,
+                                const uint32_t *face_mask_in, int64_t n_fans, int32_t K, float threshold,
+                                float *xyz_out, float *rgb_out, float *alpha_out, float *m_out, float *v_out,
+                                uint32_t *face_mask_out, int64_t *n_kept, void *workspace, size_t ws_bytes,
+                                void *stream) {
     if (n_fans < 0 || K < 3 || K > kMaxK || !n_kept) return fail(MS_ERR_INVALID, "bad n_fans, K or NULL n_kept");
     if (n_fans * (int64_t)(K + 1) >= (1ll << 32)) return fail(MS_ERR_INVALID, "too many vertices");
     if (n_fans > 0 && (!xyz || !rgb || !alpha || !xyz_out || !rgb_out || !alpha_out || !workspace))
@@ -643,11 +645,19 @@ MS_API ms_status ms_prune_fans(const float *xyz, const float *rgb, const float *
         return fail(MS_ERR_INVALID, "workspace %zu bytes < %zu needed", ws_bytes, ms_prune_workspace_size(n_fans));
     char *ws = static_cast<char *>(workspace);
     void *scratch = ws ? ws + ((256 - (reinterpret_cast<uintptr_t>(ws) & 255)) & 255) : nullptr;
-    cudaError_t e = launch_prune(xyz, rgb, alpha, m, v, n_fans, K, threshold, xyz_out, rgb_out, alpha_out, m_out,
-                                 v_out, n_kept, scratch, (cudaStream_t)stream);
+    cudaError_t e = launch_prune(xyz, rgb, alpha, m, v, face_mask_in, n_fans, K, threshold, xyz_out, rgb_out,
+                                 alpha_out, m_out, v_out, face_mask_out, n_kept, scratch, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "prune launch");
     if (n_fans > 0) count_launches(3);
     return MS_OK;
+}
+
+MS_API ms_status ms_prune_fans(const float *xyz, const float *rgb, const float *alpha, const float *m, const float *v,
+                               int64_t n_fans, int32_t K, float threshold, float *xyz_out, float *rgb_out,
+                               float *alpha_out, float *m_out, float *v_out, int64_t *n_kept, void *workspace,
+                               size_t ws_bytes, void *stream) {
+    return ms_prune_faces(xyz, rgb, alpha, m, v, nullptr, n_fans, K, threshold, xyz_out, rgb_out, alpha_out, m_out,
+                          v_out, nullptr, n_kept, workspace, ws_bytes, stream);
 }
 
 static ms_status adam_common(float *xyz, float *rgb, float *alpha, const float *d_xyz, const float *d_rgb,

@@ -26,8 +26,9 @@ struct BinArgs {
     Status *st;
     unsigned long long *keys;
     ViewTable vt;
-    float4 *dec;               // [view][vertex] decided (xs, ys, Z, 1/Z), read by the raster passes
+    float4 *dec;               // [view][vertex] decided (xr, yr, Z or -1, origin), read by the raster passes
     int64_t V;
+    const uint32_t *face_mask; // per fan, bit j = face j drawn; NULL = all
 };
 
 // Blocks take virtual ids in start order; id = view * fan_blocks + fan block, so pairs
@@ -93,8 +94,12 @@ __global__ void __launch_bounds__(kBinThreads) bin_kernel(const __grid_constant_
             mny = fminf(mny, d.ys); mxy = fmaxf(mxy, d.ys);
             zmin = fminf(zmin, d.Z);
         }
-        const uint32_t tmask = tri_valid_mask(vmask, K);
-        if (vmask != all && tmask) {   // bounds over the vertices of valid triangles only
+        uint32_t tmask = tri_valid_mask(vmask, K);
+        const uint32_t full = (1u << K) - 1u;
+        const uint32_t drawn = a.face_mask ? (__ldg(a.face_mask + f0 + tid) & full) : full;
+        const unsigned ntri_bad = K - __popc(tmask);   // culled: an invalid vertex
+        tmask &= drawn;
+        if ((vmask != all || drawn != full) && tmask) {   // bounds over the vertices of drawn triangles only
             mnx = 3.0e38f; mxx = -3.0e38f; mny = 3.0e38f; mxy = -3.0e38f; zmin = 3.0e38f;
             for (int k = 0; k < KV; ++k) {
                 if (!vertex_used(tmask, k, K)) continue;
@@ -104,7 +109,6 @@ __global__ void __launch_bounds__(kBinThreads) bin_kernel(const __grid_constant_
                 zmin = fminf(zmin, d.Z);
             }
         }
-        const unsigned ntri_bad = K - __popc(tmask);
         if (ntri_bad) atomicAdd(&s_culled, ntri_bad);
         if (tmask) {
             const FanRect r = rect_from_bounds(mnx, mxx, mny, mxy, cam.width, cam.height);
@@ -204,6 +208,7 @@ cudaError_t launch_bin(const RenderArgs &ra, cudaStream_t st) {
     a.vt = ra.vt;
     a.dec = reinterpret_cast<float4 *>(ra.ws + L.off_dec);
     a.V = L.V;
+    a.face_mask = ra.splat ? nullptr : ra.prm.face_mask;
     bin_kernel<<<(unsigned)L.bin_blocks, kBinThreads, smem, st>>>(a);
     return cudaGetLastError();
 }

@@ -116,8 +116,9 @@ cudaError_t launch_l1(const float *img, const float *tgt, int64_t n_pixels, floa
 // Pruning of fans whose vertex opacities are all below a threshold (prune.cu).
 size_t prune_scratch_bytes(int64_t n_fans);
 cudaError_t launch_prune(const float *xyz, const float *rgb, const float *alpha, const float *m, const float *v,
-                         int64_t n_fans, int K, float thr, float *xyz_o, float *rgb_o, float *alpha_o, float *m_o,
-                         float *v_o, int64_t *n_kept, void *scratch, cudaStream_t st);
+                         const uint32_t *mask_in, int64_t n_fans, int K, float thr, float *xyz_o, float *rgb_o,
+                         float *alpha_o, float *m_o, float *v_o, uint32_t *mask_o, int64_t *n_kept, void *scratch,
+                         cudaStream_t st);
 // Fine-tuning loss lambda L1 + (1 - lambda)(1 - SSIM) of one H x W RGBA image (ssim.cu).
 size_t ssim_scratch_bytes(int H, int W);
 cudaError_t launch_ssim_loss(const float *img, const float *tgt, int H, int W, float lam, float *dL, float *loss,

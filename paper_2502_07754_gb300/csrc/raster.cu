@@ -35,6 +35,7 @@ struct RastArgs {
     SplatSrc spl;              // source Gaussians (splat passes only)
     const float4 *dec;         // [view][vertex] decided vertices from binning
     int64_t V;
+    const uint32_t *face_mask; // per fan, bit j = face j drawn; NULL = all
 };
 
 constexpr int kRastWarps = 2;   // warps (work items) per block: items differ widely in cost
@@ -76,6 +77,7 @@ __global__ void __launch_bounds__(kRastWarps * 32) raster_kernel(const __grid_co
     sc.W = vw.cam.width;
     sc.H = vw.cam.height;
     sc.dec = a.dec + (size_t)view * (size_t)a.V;
+    sc.face_mask = SPLAT ? nullptr : a.face_mask;
     const int tile = (int)(it.x - vw.tile_base);
     const int tiles_x = (int)vw.tiles_x;
     const unsigned long long pix_base = vw.pix_base;
@@ -453,6 +455,7 @@ RastArgs make_args(const RenderArgs &ra) {
     a.spl = ra.spl;
     a.dec = reinterpret_cast<const float4 *>(ra.ws + L.off_dec);
     a.V = L.V;
+    a.face_mask = ra.prm.face_mask;
     return a;
 }
 

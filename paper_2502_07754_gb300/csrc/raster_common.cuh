@@ -21,6 +21,7 @@ struct SceneDev {
     const CamDev *cam;   // points into the kernel's __grid_constant__ view table
     int W, H;
     const float4 *dec;   // this view's decided vertices (xr, yr, Z or -1, origin), written by binning
+    const uint32_t *face_mask;   // per fan, bit j = face j drawn; NULL = all
 };
 
 // ------------------------------------------------------------------------------------
@@ -222,7 +223,8 @@ __device__ __forceinline__ void stage_fans(const SceneDev &a, const Stage &s, in
         }
     vmask = group_or<LPF>(vmask);
     __syncwarp();   // the group's vertex rows are complete
-    const uint32_t tmask = tri_valid_mask(vmask, K);
+    uint32_t tmask = tri_valid_mask(vmask, K);
+    if (a.face_mask && active) tmask &= __ldg(a.face_mask + fan);   // the same word in every lane of the fan
     float mnx = 3.0e38f, mxx = -3.0e38f, mny = 3.0e38f, mxy = -3.0e38f;
     uint32_t flags = 0, stie = 0, rtie = 0;
     if (active) {

@@ -69,3 +69,67 @@ def test_render_equals_render_without_the_pruned_faces():
     assert np.array_equal(full, pruned)
     gone = np.setdiff1d(np.arange(400), fans)
     assert np.all(a.reshape(400, K + 1)[gone] < oracle.PRUNE_THRESHOLD)
+
+
+# ------------------------------------------------------------------ per-face pruning
+
+def test_face_masks_hand_example():
+    """K = 4 fans (faces (c,b0,b1), (c,b1,b2), (c,b2,b3), (c,b3,b0)), threshold t:
+    a dim centre with one bright boundary vertex b2 keeps exactly the two faces holding b2;
+    a bright centre keeps every face; an all-dim fan keeps none; a face whose three
+    opacities sit exactly on the threshold stays (below means strictly below)."""
+    t = float(np.float32(math.exp(-4.0)))
+    lo, hi = 0.001, 0.5
+    alpha = np.array([
+        [lo, lo, lo, hi, lo],    # b2 bright: faces 1 and 2
+        [hi, lo, lo, lo, lo],    # centre bright: all faces
+        [lo, lo, lo, lo, lo],    # all dim: none
+        [t, t, t, t, t],         # on the threshold: all kept
+    ])
+    m = oracle.face_masks(alpha.reshape(-1), 4, threshold=t)
+    assert list(m) == [0b0110, 0b1111, 0b0000, 0b1111]
+
+
+def test_prune_faces_removes_faceless_fans_and_keeps_earlier_removals():
+    rng = np.random.Generator(np.random.PCG64(4))
+    K, n = 8, 500
+    xyz = rng.normal(size=(n * (K + 1), 3))
+    rgb = rng.random((n * (K + 1), 3))
+    a = rng.uniform(0.0, 1.0, (n, K + 1))
+    a[rng.random(n) < 0.3] *= 0.01
+    a[:, 0][rng.random(n) < 0.5] = 0.001
+    a = a.reshape(-1)
+    px, pc, pa, _, masks, fans = oracle.prune_faces(xyz, rgb, a, K)
+    # without an earlier mask the removed fans are exactly those of the fan rule
+    _, _, _, _, fans_f = oracle.prune_fans(xyz, rgb, a, K)
+    assert np.array_equal(fans, fans_f)
+    assert (masks != 0).all() and masks.max() < (1 << K)
+    # an earlier mask stays applied, and pruning again with the result changes nothing
+    early = rng.integers(0, 1 << K, n)
+    _, _, pa2, _, m2, f2 = oracle.prune_faces(xyz, rgb, a, K, face_mask=early)
+    full = oracle.face_masks(a, K)
+    assert np.array_equal(m2, (full & early)[f2])
+    _, _, _, _, m3, f3 = oracle.prune_faces(px, pc, pa, K, face_mask=masks)
+    assert np.array_equal(f3, np.arange(fans.size)) and np.array_equal(m3, masks)
+
+
+def test_masked_render_equals_render_of_the_kept_triangles():
+    """Drawing a pruned soup through its face masks is drawing the kept faces' triangles:
+    the explicit triangle list of masked_fan_tris is the reference."""
+    w = synthetic.workload(1, n=200)
+    cam = w.cameras[0]
+    K = 8
+    xyz, rgb, a = oracle.mesh_build(w.scene, K=K, cam_center=cam.C)
+    rng = np.random.Generator(np.random.PCG64(9))
+    a = a.copy().reshape(-1, K + 1)
+    a[rng.random(200) < 0.5, 0] = 0.001          # dim centres: rim faces may go
+    a[:, 1:][rng.random((200, K)) < 0.5] = 0.001
+    a = a.reshape(-1)
+    px, pc, pa, _, masks, fans = oracle.prune_faces(xyz, rgb, a, K)
+    kept = oracle.masked_fan_tris(fans.size, K, masks)
+    full_tris = oracle.fan_tris(200, K).reshape(200, K, 3)
+    bits = ((oracle.face_masks(a, K)[:, None] >> np.arange(K)) & 1).astype(bool)
+    ref, _, _ = oracle.render(xyz, rgb, a, full_tris[bits], cam)
+    img, _, _ = oracle.render(px, pc, pa, kept, cam)
+    assert np.allclose(img, ref, atol=0, rtol=0) or np.abs(img - ref).max() < 1e-12
+    assert int(bits.sum()) < 200 * K      # some faces did go
