@@ -200,6 +200,65 @@ MS_API ms_status ms_mesh_build_3d(const float *means, const float *log_scales, c
                                   const ms_fan_params *fan, const float *cam_center, float *xyz, float *rgb,
                                   float *alpha, void *stream);
 
+/*
+ * Explicit triangles (the renderer's `tris` input; Sec. 3 renders meshes whose triangles
+ * need not form fans: the three-fan conversion's shared vertices, the mesh prior's
+ * secondary triangles).  Each triangle (v1, v2, v3) is drawn as a fan of K = 3 around its
+ * centroid c, whose position, colour and opacity are the binary32 values nearest the exact
+ * means of the vertices': the three sub-triangles (c, v_i, v_i+1) tile the triangle and an
+ * attribute that is affine on the triangle interpolates to the same values on them.
+ *   ms_tris_to_fans: xyz, rgb (V x 3), alpha (V) device vertex arrays; tris: device T x 3
+ *     int32 vertex indices, or NULL for a triangle soup (triangle t = vertices 3t, 3t+1,
+ *     3t+2); writes the fan soup fan_xyz, fan_rgb (4T x 3), fan_alpha (4T): fan t is
+ *     vertices 4t (centroid), 4t+1 .. 4t+3.
+ *   ms_fans_to_tris_grads: the adjoint, ADDED to d_xyz, d_rgb, d_alpha (V arrays, caller
+ *     zeroes) with atomics: vertex k of triangle t receives fan vertex 4t+1+k's gradient and
+ *     a third of the centroid's.  The fan gradients come from three arrays (4T) or, when
+ *     grad_ws is non-NULL, from the sums a render backward left in its workspace
+ *     (ms_render_grad_offset; 16-byte aligned).
+ *   ms_mesh_render / ms_mesh_render_backward: the two steps around ms_render /
+ *     ms_render_backward (T fans of K = 3) in one workspace of ms_mesh_workspace_size bytes
+ *     (256-byte aligned; it holds the fan soup, then the render workspace).  Gradients are
+ *     added to the vertex arrays.  Errors as ms_render, MS_ERR_INVALID for T >= 2^29.
+ */
+MS_API ms_status ms_tris_to_fans(const float *xyz, const float *rgb, const float *alpha, const int32_t *tris,
+                                 int64_t T, float *fan_xyz, float *fan_rgb, float *fan_alpha, void *stream);
+MS_API ms_status ms_fans_to_tris_grads(const float *g_fan_xyz, const float *g_fan_rgb, const float *g_fan_alpha,
+                                       const void *grad_ws, const int32_t *tris, int64_t T, float *d_xyz,
+                                       float *d_rgb, float *d_alpha, void *stream);
+MS_API size_t ms_mesh_workspace_size(int64_t T, const ms_camera *cam, const ms_render_params *params);
+MS_API ms_status ms_mesh_render(const float *xyz, const float *rgb, const float *alpha, const int32_t *tris, int64_t T,
+                                const ms_camera *cam, const ms_render_params *params, float *out_rgba,
+                                void *workspace, size_t ws_bytes, void *stream);
+MS_API ms_status ms_mesh_render_backward(const float *xyz, const float *rgb, const float *alpha, const int32_t *tris,
+                                         int64_t T, const ms_camera *cam, const ms_render_params *params,
+                                         const float *out_rgba, const float *dL_drgba, float *d_xyz, float *d_rgb,
+                                         float *d_alpha, void *workspace, size_t ws_bytes, void *stream);
+
+/*
+ * Mesh-prior mode (Sec. 3, the mesh-prior paragraphs): every face (m1, m2, m3) of a
+ * geometry mesh carries S secondary triangles whose vertices are convex combinations
+ * v_i = sum_k a_ik m_k of the face's corners, with a_ik = w_ik^2 / sum_j w_ij^2 of free
+ * weights w (so a_i stays on the simplex), and per-vertex colour and opacity.
+ *   faces: device F x 3 corners x 3 floats; w: device F x S x 3 vertices x 3 corners;
+ *   rgb: device F x S x 3 x 3; alpha: device F x S x 3.
+ *   ms_mesh_prior_build writes the secondary triangles as centroid fans (as
+ *     ms_tris_to_fans: fan_xyz, fan_rgb 4FS x 3, fan_alpha 4FS), ready for ms_render with
+ *     K = 3.
+ *   ms_mesh_prior_backward ADDS to d_w (shape of w), d_rgb, d_alpha the gradients given
+ *     the fan soup's (three arrays, or grad_ws as in ms_fans_to_tris_grads): the centroid's
+ *     share goes a third to each vertex, then dL/da_ik = dL/dv_i . m_k and
+ *     dL/dw_ij = (2 w_ij / Q_i)(dL/da_ij - sum_k a_ik dL/da_ik), Q_i = sum_j w_ij^2.
+ *     (A vertex whose weights are all zero has no defined simplex point; callers keep w
+ *     away from 0.)
+ */
+MS_API ms_status ms_mesh_prior_build(const float *faces, const float *w, const float *rgb, const float *alpha,
+                                     int64_t F, int32_t S, float *fan_xyz, float *fan_rgb, float *fan_alpha,
+                                     void *stream);
+MS_API ms_status ms_mesh_prior_backward(const float *faces, const float *w, const float *g_fan_xyz,
+                                        const float *g_fan_rgb, const float *g_fan_alpha, const void *grad_ws,
+                                        int64_t F, int32_t S, float *d_w, float *d_rgb, float *d_alpha, void *stream);
+
 /* Bytes of workspace ms_render / ms_render_backward need for n_fans fans of K triangles. */
 MS_API size_t ms_render_workspace_size(int64_t n_fans, int32_t K, const ms_camera *cam,
                                        const ms_render_params *params);

@@ -215,6 +215,104 @@ class Renderer:
         return C.c_void_p(self.ws.data_ptr() + int(off))
 
 
+def tris_to_fans(xyz, rgb, alpha, tris=None, stream=None):
+    """Explicit triangles (tris: T x 3 int32 device tensor, or None for a soup of
+    consecutive vertex triples) as centroid fans of K = 3 (ms_tris_to_fans): returns the
+    fan soup (4T x 3, 4T x 3, 4T)."""
+    T = int(tris.shape[0]) if tris is not None else xyz.shape[0] // 3
+    fx = torch.empty(4 * T, 3, device=xyz.device)
+    fc = torch.empty(4 * T, 3, device=xyz.device)
+    fa = torch.empty(4 * T, device=xyz.device)
+    check(lib().ms_tris_to_fans(_ptr(xyz), _ptr(rgb), _ptr(alpha), _ptr(tris) if tris is not None else None, T,
+                                _ptr(fx), _ptr(fc), _ptr(fa), _stream(stream, fx, fc, fa)))
+    return fx, fc, fa
+
+
+class MeshRenderer:
+    """Explicit-topology render (ms_mesh_render / ms_mesh_render_backward): triangles index
+    a shared vertex array; owns the workspace and grows its capacities on MS_ERR_CAPACITY."""
+
+    def __init__(self, n_tris: int, cam, params=None, device="cuda"):
+        self.T = int(n_tris)
+        self.cam = cam if isinstance(cam, _lib.Camera) else camera_struct(cam)
+        self.params = params if params is not None else render_params()
+        self.device = torch.device(device)
+        self._alloc()
+
+    def _alloc(self):
+        n = lib().ms_mesh_workspace_size(self.T, C.byref(self.cam), C.byref(self.params))
+        if n == 0:
+            raise ValueError("invalid render configuration")
+        self.ws = None
+        self.ws = torch.empty(int(n), dtype=torch.uint8, device=self.device)
+
+    def _render_ws(self):
+        soup = (4 * self.T * 28 + 255) // 256 * 256
+        return C.c_void_p(self.ws.data_ptr() + soup)
+
+    def forward(self, xyz, rgb, alpha, tris, out=None, stream=None):
+        if out is None:
+            out = torch.empty(self.cam.height, self.cam.width, 4, device=xyz.device)
+        tp = _ptr(tris) if tris is not None else None
+        for _ in range(4):
+            check(lib().ms_mesh_render(_ptr(xyz), _ptr(rgb), _ptr(alpha), tp, self.T, C.byref(self.cam),
+                                       C.byref(self.params), _ptr(out), _ptr(self.ws), self.ws.numel(),
+                                       _stream(stream, out, self.ws)))
+            inf = _lib.RenderInfo()
+            st = lib().ms_render_get_info(self._render_ws(), C.byref(inf), _stream(stream))
+            if st == _lib.MS_ERR_CAPACITY:
+                if inf.pairs > inf.pair_capacity:
+                    self.params.pair_capacity = int(inf.pairs * 1.25) + 4096
+                if inf.frags > inf.frag_capacity:
+                    self.params.frag_capacity = int(inf.frags * 1.25) + 65536
+                self._alloc()
+                continue
+            check(st)
+            self.last_info = inf
+            return out
+        raise _lib.MSError(_lib.MS_ERR_CAPACITY, "capacity did not converge")
+
+    def backward(self, xyz, rgb, alpha, tris, out_rgba, dL, d_xyz=None, d_rgb=None, d_alpha=None, stream=None):
+        if d_xyz is None:
+            d_xyz, d_rgb, d_alpha = torch.zeros_like(xyz), torch.zeros_like(rgb), torch.zeros_like(alpha)
+        check(lib().ms_mesh_render_backward(_ptr(xyz), _ptr(rgb), _ptr(alpha), _ptr(tris) if tris is not None else None,
+                                            self.T, C.byref(self.cam), C.byref(self.params), _ptr(out_rgba),
+                                            _ptr(dL.contiguous()), _ptr(d_xyz), _ptr(d_rgb), _ptr(d_alpha),
+                                            _ptr(self.ws), self.ws.numel(),
+                                            _stream(stream, d_xyz, d_rgb, d_alpha, self.ws)))
+        return d_xyz, d_rgb, d_alpha
+
+
+def mesh_prior_build(faces, w, rgb, alpha, stream=None):
+    """Secondary triangles of the mesh prior (ms_mesh_prior_build) as centroid fans:
+    faces F x 3 x 3, w and rgb F x S x 3 x 3, alpha F x S x 3 -> fan soup (4FS x 3, 4FS x 3,
+    4FS), to render as F S fans of K = 3."""
+    F, S = int(w.shape[0]), int(w.shape[1])
+    fx = torch.empty(4 * F * S, 3, device=w.device)
+    fc = torch.empty(4 * F * S, 3, device=w.device)
+    fa = torch.empty(4 * F * S, device=w.device)
+    check(lib().ms_mesh_prior_build(_ptr(faces), _ptr(w), _ptr(rgb), _ptr(alpha), F, S, _ptr(fx), _ptr(fc), _ptr(fa),
+                                    _stream(stream, fx, fc, fa)))
+    return fx, fc, fa
+
+
+def mesh_prior_backward(faces, w, fan_grads=None, renderer=None, out=None, stream=None):
+    """Gradients of the weights and per-vertex attributes (ms_mesh_prior_backward) from the
+    fan soup's gradients: three tensors, or the sums a renderer's backward left in its
+    workspace.  Returns (d_w, d_rgb, d_alpha), added to `out` when given."""
+    F, S = int(w.shape[0]), int(w.shape[1])
+    if out is None:
+        out = (torch.zeros_like(w), torch.zeros(F, S, 3, 3, device=w.device), torch.zeros(F, S, 3, device=w.device))
+    dw, dc, da = out
+    if renderer is not None:
+        g = (None, None, None, renderer.grad_ptr())
+    else:
+        g = (_ptr(fan_grads[0]), _ptr(fan_grads[1]), _ptr(fan_grads[2]), None)
+    check(lib().ms_mesh_prior_backward(_ptr(faces), _ptr(w), *g, F, S, _ptr(dw), _ptr(dc), _ptr(da),
+                                       _stream(stream, dw, dc, da)))
+    return dw, dc, da
+
+
 class BatchRenderer:
     """Owns a workspace for rendering one fan soup into several views of any sizes with
     one pass of the pipeline (ms_batch_render).  Outputs of all views live in one flat

@@ -313,3 +313,34 @@ def workload(idx: int, n: int | None = None) -> Workload:
         cams = [make_camera(d * 3.5, 1920, 1080) for d in fibonacci_dirs(8)]
         return Workload("clustered-3M-K8-8views-1080p", sc, 8, cams)
     raise ValueError(idx)
+
+
+def sphere_mesh(n_lat: int, n_lon: int, radius: float = 1.0, centre=(0.0, 0.0, 0.0), jitter: float = 0.0,
+                seed: int = 0):
+    """A UV-tessellated sphere with shared vertices: (vertices V x 3 float32, faces T x 3
+    int32, outward winding).  `jitter` moves every vertex by N(0, jitter) so no two
+    triangles are exactly coplanar or meet a pixel centre exactly."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    verts = [(0.0, 0.0, radius)]
+    for i in range(1, n_lat):
+        th = np.pi * i / n_lat
+        for j in range(n_lon):
+            ph = 2 * np.pi * j / n_lon
+            verts.append((radius * np.sin(th) * np.cos(ph), radius * np.sin(th) * np.sin(ph), radius * np.cos(th)))
+    verts.append((0.0, 0.0, -radius))
+    V = np.asarray(verts) + np.asarray(centre)
+    if jitter:
+        V = V + rng.normal(0.0, jitter, V.shape)
+    ring = lambda i, j: 1 + (i - 1) * n_lon + (j % n_lon)
+    faces = []
+    for j in range(n_lon):
+        faces.append((0, ring(1, j), ring(1, j + 1)))
+    for i in range(1, n_lat - 1):
+        for j in range(n_lon):
+            a, b, c, d = ring(i, j), ring(i, j + 1), ring(i + 1, j), ring(i + 1, j + 1)
+            faces.append((a, c, b))
+            faces.append((b, c, d))
+    south = len(verts) - 1
+    for j in range(n_lon):
+        faces.append((south, ring(n_lat - 1, j + 1), ring(n_lat - 1, j)))
+    return V.astype(np.float32), np.asarray(faces, np.int32)
