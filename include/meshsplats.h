@@ -259,6 +259,34 @@ MS_API ms_status ms_mesh_prior_backward(const float *faces, const float *w, cons
                                         const float *g_fan_rgb, const float *g_fan_alpha, const void *grad_ws,
                                         int64_t F, int32_t S, float *d_w, float *d_rgb, float *d_alpha, void *stream);
 
+/*
+ * Ray tracing of the triangle soup with shadows (the motivation of Sec. 1: a mesh of
+ * triangles is what ray tracers take, with secondary effects such as shadows; the paper
+ * gives no shading model, so this one is stated here).  Primary rays: the pixel-centre ray
+ * C + t d of the pinhole camera with d of unit view depth; every triangle crossed at
+ * t > znear is a fragment with the ray's barycentrics (the rasteriser's perspective-correct
+ * ones), ordered by t, ties by triangle index, composited front to back as ms_render does
+ * (C += T a c, T *= 1 - a; out = (C + T bg, 1 - T)), stopping once T < T_eps (0: never).
+ * Shadows (light non-NULL and ambient < 1): a point light L; the fragment at p takes the
+ * product S of (1 - a_g) over every other triangle g crossed by the segment p -> L at a
+ * segment parameter in (1e-9, 1 - 1e-9), and its colour becomes c (ambient + (1 - ambient) S).
+ * Crossings are decided in FP64 (Moller-Trumbore, closed edges).
+ *   Triangles: tris (device T x 3 int32) or, when NULL, the implicit fan topology of K
+ *   triangles a fan (T = n_fans K); xyz, rgb (V x 3), alpha (V) device.
+ *   ms_bvh_build: a linear BVH over the triangles into `bvh` (device, >=
+ *   ms_bvh_workspace_size(T) bytes, 256-byte aligned); rebuild after the vertices move.
+ *   ms_raytrace: out_rgba device H x W x 4 (16-byte aligned); light, bg: host 3 floats
+ *   (bg NULL = black).  Traversal stacks are bounded; ms_bvh_status synchronises the
+ *   stream and returns MS_ERR_CAPACITY (with the count) if a traversal overflowed its stack.
+ */
+MS_API size_t ms_bvh_workspace_size(int64_t T);
+MS_API ms_status ms_bvh_build(const float *xyz, const int32_t *tris, int64_t T, int32_t K, void *bvh, size_t bvh_bytes,
+                              void *stream);
+MS_API ms_status ms_raytrace(const float *xyz, const float *rgb, const float *alpha, const int32_t *tris, int64_t T,
+                             int32_t K, const void *bvh, const ms_camera *cam, const float *light, float ambient,
+                             float T_eps, const float *bg, float *out_rgba, void *stream);
+MS_API ms_status ms_bvh_status(const void *bvh, int32_t *stack_overflows, void *stream);
+
 /* Bytes of workspace ms_render / ms_render_backward need for n_fans fans of K triangles. */
 MS_API size_t ms_render_workspace_size(int64_t n_fans, int32_t K, const ms_camera *cam,
                                        const ms_render_params *params);

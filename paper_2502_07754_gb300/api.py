@@ -283,6 +283,37 @@ class MeshRenderer:
         return d_xyz, d_rgb, d_alpha
 
 
+class RayTracer:
+    """Ray tracing of a triangle soup with shadows (ms_bvh_build, ms_raytrace): tris is a
+    T x 3 int32 device tensor, or None with K for the implicit fan topology."""
+
+    def __init__(self, n_tris: int, K: int = 0, device="cuda"):
+        self.T, self.K = int(n_tris), int(K)
+        self.bvh = torch.empty(max(int(lib().ms_bvh_workspace_size(self.T)), 256), dtype=torch.uint8,
+                               device=torch.device(device))
+
+    def build(self, xyz, tris=None, stream=None):
+        check(lib().ms_bvh_build(_ptr(xyz), _ptr(tris) if tris is not None else None, self.T, self.K,
+                                 _ptr(self.bvh), self.bvh.numel(), _stream(stream, self.bvh)))
+
+    def trace(self, xyz, rgb, alpha, cam, tris=None, light=None, ambient=1.0, T_eps=0.0, bg=(0.0, 0.0, 0.0),
+              out=None, stream=None):
+        cs = cam if isinstance(cam, _lib.Camera) else camera_struct(cam)
+        if out is None:
+            out = torch.empty(cs.height, cs.width, 4, device=xyz.device)
+        lt = (C.c_float * 3)(*[float(x) for x in light]) if light is not None else None
+        bgv = (C.c_float * 3)(*[float(x) for x in bg])
+        check(lib().ms_raytrace(_ptr(xyz), _ptr(rgb), _ptr(alpha), _ptr(tris) if tris is not None else None, self.T,
+                                self.K, _ptr(self.bvh), C.byref(cs), lt, float(ambient), float(T_eps), bgv, _ptr(out),
+                                _stream(stream, out)))
+        return out
+
+    def status(self, stream=None):
+        n = C.c_int32(0)
+        st = lib().ms_bvh_status(_ptr(self.bvh), C.byref(n), _stream(stream))
+        return st, n.value
+
+
 def mesh_prior_build(faces, w, rgb, alpha, stream=None):
     """Secondary triangles of the mesh prior (ms_mesh_prior_build) as centroid fans:
     faces F x 3 x 3, w and rgb F x S x 3 x 3, alpha F x S x 3 -> fan soup (4FS x 3, 4FS x 3,

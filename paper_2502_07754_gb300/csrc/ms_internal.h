@@ -89,6 +89,12 @@ cudaError_t launch_splat_polygons(const SplatSrc &s, int64_t N, float *xyz, cuda
 
 cudaError_t launch_bin(const RenderArgs &a, cudaStream_t st);
 cudaError_t launch_sort(const RenderArgs &a, cudaStream_t st);
+// Stable LSD sort of n 64-bit elements by bits [shift, shift + 8 passes): a and b are the two
+// buffers, *result receives the one holding the sorted elements; scratch (device,
+// sort_scratch_bytes, 16-byte aligned) is cleared and used for counts and look-back flags.
+size_t sort_scratch_bytes(int64_t n, int passes);
+cudaError_t sort_u64(unsigned long long *a, unsigned long long *b, int64_t n, int shift, int passes, char *scratch,
+                     cudaStream_t st, unsigned long long **result);
 constexpr int kItemFans = 64;   // fans per raster work item
 
 cudaError_t launch_raster(const RenderArgs &a, bool fill, cudaStream_t st);

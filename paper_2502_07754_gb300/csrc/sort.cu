@@ -209,7 +209,44 @@ __global__ void tile_ranges_kernel(const unsigned long long *__restrict__ keys, 
     }
 }
 
+__global__ void set_pairs_kernel(Status *st, int64_t n) { st->pairs = (unsigned long long)n; }
+
 }  // namespace
+
+size_t sort_scratch_bytes(int64_t n, int passes) {
+    const int64_t blocks = (n + kSortTile - 1) / kSortTile;
+    return 256 + 8 * 256 * 4 + (size_t)passes * (size_t)(blocks > 0 ? blocks : 1) * 256 * 4;
+}
+
+cudaError_t sort_u64(unsigned long long *a, unsigned long long *b, int64_t n, int shift, int passes, char *scratch,
+                     cudaStream_t st, unsigned long long **result) {
+    *result = a;
+    if (n <= 0 || passes <= 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(scratch, 0, sort_scratch_bytes(n, passes), st);
+    if (e != cudaSuccess) return e;
+    Status *status = reinterpret_cast<Status *>(scratch);
+    uint32_t *hist = reinterpret_cast<uint32_t *>(scratch + 256);
+    uint32_t *lookback = hist + 8 * 256;
+    const int64_t blocks = (n + kSortTile - 1) / kSortTile;
+    set_pairs_kernel<<<1, 1, 0, st>>>(status, n);
+    const int hist_grid = (int)min64((n + kHistThreads * 8 - 1) / (kHistThreads * 8), 4 * 152);
+    sort_hist_kernel<<<hist_grid, kHistThreads, 0, st>>>(a, status, n, passes, shift, hist);
+    sort_scan_kernel<<<1, 256, 0, st>>>(hist, passes);
+    const size_t smem = (size_t)kSortTile * 8 + (kSortWarps * 256 + 512) * 4;
+    cudaFuncSetAttribute(sort_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int dev = 0, n_sm = 152, per_sm = 2;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sort_pass_kernel, kSortThreads, smem);
+    const unsigned grid = (unsigned)min64(blocks, (int64_t)n_sm * (per_sm > 0 ? per_sm : 1));
+    unsigned long long *kb[2] = {a, b};
+    for (int p = 0; p < passes; ++p)
+        sort_pass_kernel<<<grid, kSortThreads, smem, st>>>(kb[p & 1], kb[(p + 1) & 1], status, n, hist,
+                                                            lookback + (size_t)p * blocks * 256, p, shift + 8 * p);
+    *result = kb[passes & 1];
+    count_launches(3 + passes);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_sort(const RenderArgs &a, cudaStream_t st) {
     const RenderLayout &L = a.L;
