@@ -416,6 +416,16 @@ MS_API ms_status ms_mlp_features(const float *log_scales, const float *quats, co
 MS_API ms_status ms_mlp_forward(const float *log_scales, const float *quats, const float *opacity, const void *sh,
                                 int32_t sh_dtype, int32_t sh_degree, int64_t N, const void *packed, int32_t n_out,
                                 float *corr, void *stream);
+/* The conversion of ms_mesh_build (flat fans) fused behind the inference: one kernel runs
+ * the perceptron on each 128-Gaussian tile and converts the tile's Gaussians with their
+ * corrections taken from on-chip registers, so the N x 2(K+1) corrections never reach device
+ * memory.  The result equals ms_mlp_forward followed by ms_mesh_build with corr bit for bit.
+ * packed: weights packed with n_out = 2(K+1) (K <= 15); other arguments as ms_mesh_build.
+ * Errors: MS_ERR_INVALID for NULL or misaligned pointers, K outside 3..15. */
+MS_API ms_status ms_mesh_build_mlp(const float *means, const float *log_scales, const float *quats,
+                                   const float *opacity, const void *sh, int32_t sh_dtype, int32_t sh_degree, int64_t N,
+                                   const ms_fan_params *fan, const float *cam_center, const void *packed, float *xyz,
+                                   float *rgb, float *alpha, void *stream);
 /* Training: mean squared error of the outputs for inputs X (n x 16) against targets T
  * (n x n_out).  ms_mlp_grads overwrites grads (device FP32, the sizes of W1, W2, W3 in that
  * order) and *loss (device).  ms_mlp_adam updates the masters W (same flat order) with

@@ -107,6 +107,8 @@ _SIGS = {
     "ms_mlp_pack": (C.c_int, [_P, _P, _P, C.c_int32, _P, _P]),
     "ms_mlp_features": (C.c_int, [_P, _P, _P, _P, C.c_int32, C.c_int32, C.c_int64, _P, _P]),
     "ms_mlp_forward": (C.c_int, [_P, _P, _P, _P, C.c_int32, C.c_int32, C.c_int64, _P, C.c_int32, _P, _P]),
+    "ms_mesh_build_mlp": (C.c_int, [_P, _P, _P, _P, _P, C.c_int32, C.c_int32, C.c_int64, _P, _P, _P, _P, _P, _P,
+                                    _P]),
     "ms_mlp_train_workspace_size": (C.c_size_t, [C.c_int64]),
     "ms_mlp_grads": (C.c_int, [_P, _P, C.c_int64, C.c_int32, _P, _P, _P, _P, C.c_size_t, _P]),
     "ms_mlp_adam": (C.c_int, [_P, _P, _P, _P, C.c_int32, _P, C.c_float, C.c_float, C.c_float, C.c_float, _P, _P]),

@@ -74,10 +74,14 @@ def render_params(tile=16, kbuf=8, T_eps=1e-5, bg=(0.0, 0.0, 0.0), pair_capacity
 
 
 def mesh_build(means, log_scales, quats, opacity, sh, sh_degree, K=8, scale_mul=SCALE_MUL, opac_mul=OPAC_MUL,
-               axis_rule=1, cam_center=None, corr=None, stream=None, out=None):
+               axis_rule=1, cam_center=None, corr=None, stream=None, out=None, mlp=None):
     """Gaussians -> fan soup (xyz, rgb, alpha) on the device.  sh is float32 or a uint16 /
     int16 / bfloat16 tensor of bfloat16 bits, shape (N, (deg+1)^2, 3).  `out` may give the
-    three output tensors (V x 3, V x 3, V) to write into."""
+    three output tensors (V x 3, V x 3, V) to write into.  corr: corrections from
+    FanMLP.forward; or mlp: a FanMLP whose inference runs fused into the conversion
+    (ms_mesh_build_mlp: the corrections stay on chip)."""
+    if corr is not None and mlp is not None:
+        raise ValueError("give corr or mlp, not both")
     N = means.shape[0]
     dev = means.device
     V = N * (K + 1)
@@ -92,6 +96,13 @@ def mesh_build(means, log_scales, quats, opacity, sh, sh_degree, K=8, scale_mul=
     fp = _lib.FanParams(int(K), float(scale_mul), float(opac_mul), int(axis_rule))
     sh_dtype = 0 if sh.dtype == torch.float32 else 1
     cc = (C.c_float * 3)(*[float(x) for x in cam_center]) if cam_center is not None else None
+    if mlp is not None:
+        if mlp.n_out != 2 * (K + 1):
+            raise ValueError("the FanMLP predicts %d outputs, K = %d needs %d" % (mlp.n_out, K, 2 * (K + 1)))
+        check(lib().ms_mesh_build_mlp(_ptr(means), _ptr(log_scales), _ptr(quats), _ptr(opacity), _ptr(sh), sh_dtype,
+                                      int(sh_degree), N, C.byref(fp), cc, _ptr(mlp.packed), _ptr(xyz), _ptr(rgb),
+                                      _ptr(alpha), _stream(stream, xyz, rgb, alpha)))
+        return xyz, rgb, alpha
     check(lib().ms_mesh_build(_ptr(means), _ptr(log_scales), _ptr(quats), _ptr(opacity), _ptr(sh), sh_dtype,
                               int(sh_degree), N, C.byref(fp), cc, _ptr(corr), _ptr(xyz), _ptr(rgb), _ptr(alpha),
                               _stream(stream, xyz, rgb, alpha)))

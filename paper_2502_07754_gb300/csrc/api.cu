@@ -368,8 +368,10 @@ MS_API void ms_render_params_default(ms_render_params *p) {
 static ms_status mesh_build_common(const float *means, const float *log_scales, const float *quats,
                                    const float *opacity, const void *sh, int32_t sh_dtype, int32_t sh_degree, int64_t N,
                                    const ms_fan_params *fan, const float *cam_center, const float *corr, float *xyz,
-                                   float *rgb, float *alpha, bool three, void *stream) {
+                                   float *rgb, float *alpha, bool three, void *stream,
+                                   const void *mlp_packed = nullptr) {
     if (!fan) return fail(MS_ERR_INVALID, "fan params NULL");
+    if (mlp_packed && fan->K > 15) return fail(MS_ERR_INVALID, "K=%d: the initializer predicts K <= 15", fan->K);
     if (N < 0) return fail(MS_ERR_INVALID, "N < 0");
     if (fan->K < 3 || fan->K > kMaxK) return fail(MS_ERR_INVALID, "K=%d outside 3..%d", fan->K, kMaxK);
     if (sh_degree < 0 || sh_degree > 3) return fail(MS_ERR_INVALID, "sh_degree %d", sh_degree);
@@ -379,6 +381,8 @@ static ms_status mesh_build_common(const float *means, const float *log_scales, 
     if (!means || !log_scales || !quats || !opacity || !sh || !xyz || !rgb || !alpha)
         return fail(MS_ERR_INVALID, "NULL pointer");
     if (reinterpret_cast<uintptr_t>(quats) & 15) return fail(MS_ERR_INVALID, "quats must be 16-byte aligned");
+    if (mlp_packed && (reinterpret_cast<uintptr_t>(mlp_packed) & 255))
+        return fail(MS_ERR_INVALID, "packed weights must be 256-byte aligned");
     if (N * (int64_t)(fan->K + 1) * (three ? 3 : 1) >= (1ll << 32)) return fail(MS_ERR_INVALID, "too many vertices");
     MeshBuildConst kc;
     memset(&kc, 0, sizeof(kc));
@@ -418,8 +422,14 @@ static ms_status mesh_build_common(const float *means, const float *log_scales, 
     cudaError_t e;
     {
         StageScope sc(MS_STAGE_MESH_BUILD, (cudaStream_t)stream);
-        e = launch_mesh_build(means, log_scales, quats, opacity, sh, sh_dtype, sh_degree, N, kc, corr, xyz, rgb, alpha,
-                              (cudaStream_t)stream);
+        if (mlp_packed) {
+            const MlpSrc src{log_scales, quats, opacity, sh, sh_dtype, sh_degree};
+            e = launch_mesh_build_mlp(means, src, N, static_cast<const char *>(mlp_packed), kc, xyz, rgb, alpha,
+                                      (cudaStream_t)stream);
+        } else {
+            e = launch_mesh_build(means, log_scales, quats, opacity, sh, sh_dtype, sh_degree, N, kc, corr, xyz, rgb,
+                                  alpha, (cudaStream_t)stream);
+        }
     }
     if (e != cudaSuccess) return cuda_fail(e, "mesh_build launch");
     count_launches(1);
@@ -432,6 +442,15 @@ MS_API ms_status ms_mesh_build(const float *means, const float *log_scales, cons
                                void *stream) {
     return mesh_build_common(means, log_scales, quats, opacity, sh, sh_dtype, sh_degree, N, fan, cam_center, corr, xyz,
                              rgb, alpha, false, stream);
+}
+
+MS_API ms_status ms_mesh_build_mlp(const float *means, const float *log_scales, const float *quats,
+                                   const float *opacity, const void *sh, int32_t sh_dtype, int32_t sh_degree, int64_t N,
+                                   const ms_fan_params *fan, const float *cam_center, const void *packed, float *xyz,
+                                   float *rgb, float *alpha, void *stream) {
+    if (!packed) return fail(MS_ERR_INVALID, "packed weights NULL");
+    return mesh_build_common(means, log_scales, quats, opacity, sh, sh_dtype, sh_degree, N, fan, cam_center, nullptr,
+                             xyz, rgb, alpha, false, stream, packed);
 }
 
 MS_API int32_t ms_three_fan_copies(int32_t K, int32_t *first_copy) {

@@ -3,9 +3,11 @@
 // accumulators in tensor memory), standing in for part of the fine-tuning of Sec. 3 by
 // predicting per-vertex radial and log-opacity corrections of each fan.
 //
-//   inference  mlp_fwd_kernel: persistent CTAs of 128 threads, one 128-row tile at a
-//              time: features -> X (smem) -> Z1 = X W1 (TMEM) -> H1 = bf16(gelu) (smem)
-//              -> Z2 -> H2 -> Z3 -> corrections (global FP32).
+//   inference  mlp_fwd_kernel: persistent CTAs of 512 threads (two per SM), one 128-row
+//              tile at a time: features -> X (smem) -> Z1 = X W1 (TMEM) -> H1 = bf16(gelu)
+//              (smem) -> Z2 -> H2 -> Z3 -> corrections (global FP32), or, fused, the
+//              conversion of each row's Gaussian with its corrections still in registers
+//              (the corrections never reach HBM).
 //   training   mlp_act_kernel: the same forward plus the activation adjoint of the mean
 //              squared error (dY, dZ2 = (dY W3^T) gelu'(Z2), dZ1 = (dZ2 W2^T) gelu'(Z1)),
 //              writing the per-tile operands of the weight gradients transposed;
@@ -16,9 +18,12 @@
 // packed to bf16 tiles in the canonical K-major layout of tc05.cuh.
 #include <cuda_bf16.h>
 #include <math.h>
+#include <string.h>
 
+#include "mesh_build.cuh"
 #include "ms_common.cuh"
 #include "ms_internal.h"
+#include "gelu_poly.h"
 #include "tc05.cuh"
 
 namespace ms {
@@ -46,11 +51,38 @@ constexpr uint32_t kTdZ2t = kTdYt + kOutPad * kRows * 2;   // dZ2^T [128][128]
 constexpr uint32_t kTdZ1t = kTdZ2t + kHid * kRows * 2;     // dZ1^T [128][128]
 constexpr uint32_t kTileBytes = kTdZ1t + kHid * kRows * 2;
 
-// Exact GELU x Phi(x), with Phi(x) = erfc(-x / sqrt 2) / 2: the complementary form keeps
-// the small negative tail (x < -5) that 1 + erf(x / sqrt 2) cancels to zero in binary32.
-__device__ __forceinline__ float gelu(float x) { return 0.5f * x * erfcf(-x * 0.70710678118654752f); }
+// GELU x Phi(x) in binary32.  With z = |x| / sqrt 2 and E = erfc(z) / 2, Phi(x) is 1 - E
+// for x >= 0 and E for x < 0; E = t exp(-z^2) 2^G(2t - 1), t = 1 / (1 + z / 2.5), with G
+// the polynomial of gelu_poly.h (a least-squares fit): one reciprocal, one ex2 and nine
+// FMAs per value, no branch.  The complementary form keeps the tail (x < -5) that
+// 1 + erf(x / sqrt 2) would cancel to zero.  Relative error: below 4e-6 for x >= -5.6,
+// below 3e-5 further out (|GELU| < 1e-8 there), both from rounding the exponent.
+__device__ __forceinline__ float ex2_approx(float a) {
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+    return r;
+}
+__device__ __forceinline__ float rcp_approx(float a) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+    return r;
+}
+__device__ __forceinline__ float half_erfc(float z) {   // z >= 0
+    const float t = rcp_approx(fmaf(z, kGeluInvC, 1.0f));
+    const float q = gelu_log2_g_m1(fmaf(t, 2.0f, -1.0f));
+    return t * ex2_approx(fmaf(-z * 1.4426950408889634f, z, q));
+}
+__device__ __forceinline__ float gelu(float x) {
+    const float E = half_erfc(fabsf(x) * 0.70710678118654752f);
+    return x >= 0.0f ? fmaf(-x, E, x) : x * E;
+}
 __device__ __forceinline__ float gelu_grad(float x) {
-    return 0.5f * erfcf(-x * 0.70710678118654752f) + x * 0.39894228040143268f * __expf(-0.5f * x * x);
+    const float E = half_erfc(fabsf(x) * 0.70710678118654752f);
+    return (x >= 0.0f ? 1.0f - E : E) + x * 0.39894228040143268f * __expf(-0.5f * x * x);
+}
+__device__ __forceinline__ void gelu16(float v[16]) {
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = gelu(v[i]);
 }
 
 __device__ __forceinline__ uint16_t bf16_bits(float x) { return __bfloat16_as_ushort(__float2bfloat16_rn(x)); }
@@ -158,37 +190,52 @@ __device__ __forceinline__ void teardown(TcState *S, uint32_t ncols) {
 
 constexpr uint32_t kFwdW = kW1f, kFwdWEnd = kW3b;        // W1f, W2f, W3f
 constexpr uint32_t kFX = kFwdWEnd - kFwdW;               // X  [128][16]
-constexpr uint32_t kFH1 = kFX + kRows * kIn * 2;         // H1 [128][128]
-constexpr uint32_t kFH2 = kFH1 + kRows * kHid * 2;       // H2
-constexpr uint32_t kFState = kFH2 + kRows * kHid * 2;
+constexpr uint32_t kFH = kFX + kRows * kIn * 2;          // H1, then H2 [128][128]
+constexpr uint32_t kFState = kFH + kRows * kHid * 2;
 constexpr uint32_t kFwdSmem = kFState + 64;
+// After the last product of a tile, X and H are free: the fused conversion stages the
+// tile's vertices there.
+constexpr uint32_t kFStageFloats = (kFState - kFX) / 4;
 
 // 16 warps: warp w reads tensor-memory lanes 32 (w % 4) .. + 31 (rows of the tile) and
 // handles accumulator columns 32 (w / 4) .. + 31, so four warps share each row's GELU
-// epilogue; warps 0-3 also compute the inputs and write the outputs.
+// epilogue; warps 0-3 also compute the inputs and the outputs.  H2 overwrites H1 once the
+// second product has read it, which keeps a CTA at 80 KB of shared memory and 256
+// tensor-memory columns: two CTAs share an SM, and one's epilogue runs while the other's
+// products are on the tensor cores.
 constexpr int kFwdThreads = 512;
+constexpr int kFwdCtasPerSm = 2;
 
 __device__ __forceinline__ void gelu_cols(uint32_t tz, char *H, int r, int c0) {
 #pragma unroll
     for (int h = 0; h < 32; h += 16) {
         float v[16];
         tc::tmem_ld16(tz + c0 + h, v);
-#pragma unroll
-        for (int i = 0; i < 16; ++i) v[i] = gelu(v[i]);
+        gelu16(v);
         put8(H, kHid, r, c0 + h, v);
         put8(H, kHid, r, c0 + h + 8, v + 8);
     }
 }
 
-__global__ void __launch_bounds__(kFwdThreads, 1) mlp_fwd_kernel(const MlpSrc s, int64_t N,
-                                                                 const char *__restrict__ packed, int n_out,
-                                                                 float *__restrict__ corr) {
+// Where the outputs go: the corrections (N x n_out FP32), or, fused, the fan soup of
+// the conversion with the row's corrections taken from registers.
+struct FwdOut {
+    float *corr;
+    mb::Gaussians G;
+    MeshBuildConst kc;
+    float *xyz, *rgb, *alpha;
+};
+
+template <bool FUSED, int DEG, bool BF16>
+__global__ void __launch_bounds__(kFwdThreads, kFwdCtasPerSm) mlp_fwd_kernel(const MlpSrc s, int64_t N,
+                                                                             const char *__restrict__ packed,
+                                                                             int n_out, const FwdOut out) {
     extern __shared__ __align__(1024) char smem[];
     TcState *S = reinterpret_cast<TcState *>(smem + kFState);
     uint32_t *timeouts = reinterpret_cast<uint32_t *>(const_cast<char *>(packed) + kStatusOff);
     setup(smem, packed, kFwdW, kFwdWEnd, smem, S, 256);
     const char *W1 = smem + (kW1f - kFwdW), *W2 = smem + (kW2f - kFwdW), *W3 = smem + (kW3f - kFwdW);
-    char *X = smem + kFX, *H1 = smem + kFH1, *H2 = smem + kFH2;
+    char *X = smem + kFX, *H = smem + kFH;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int r = 32 * (warp & 3) + lane;   // the row (tensor-memory lane) this thread reads
     const int c0 = 32 * (warp >> 2);        // its accumulator column group
@@ -214,20 +261,42 @@ __global__ void __launch_bounds__(kFwdThreads, 1) mlp_fwd_kernel(const MlpSrc s,
         sync_then(tid == 0);
         if (tid == 0) issue(tZ1, X, W1, kIn, kHid, false, &S->mbar);
         ok = wait_mma(S, phase, timeouts);
-        gelu_cols(tZ1 + lane_off, H1, r, c0);
+        gelu_cols(tZ1 + lane_off, H, r, c0);
         sync_then(tid == 0);
-        if (tid == 0) issue(tZ2, H1, W2, kHid, kHid, false, &S->mbar);
+        if (tid == 0) issue(tZ2, H, W2, kHid, kHid, false, &S->mbar);
         ok = wait_mma(S, phase, timeouts) && ok;
-        gelu_cols(tZ2 + lane_off, H2, r, c0);
+        gelu_cols(tZ2 + lane_off, H, r, c0);   // the product has read H1: H2 replaces it
         sync_then(tid == 0);
-        if (tid == 0) issue(tZ3, H2, W3, kHid, kOutPad, false, &S->mbar);
+        if (tid == 0) issue(tZ3, H, W3, kHid, kOutPad, false, &S->mbar);
         ok = wait_mma(S, phase, timeouts) && ok;
+        float y[32];
         if (row_owner) {
-            float y[32];
             tc::tmem_ld16(tZ3 + lane_off, *reinterpret_cast<float(*)[16]>(y));
             tc::tmem_ld16(tZ3 + lane_off + 16, *reinterpret_cast<float(*)[16]>(y + 16));
-            if (g < N)
-                for (int o = 0; o < n_out; ++o) corr[g * n_out + o] = y[o];
+        }
+        if (!FUSED) {
+            if (row_owner && g < N)
+                for (int o = 0; o < n_out; ++o) out.corr[g * n_out + o] = y[o];
+        } else {
+            // The tile's fans, staged in X and H (free now: every product has completed)
+            // in chunks of whole Gaussians, each chunk stored coalesced by all threads.
+            const int KV = out.kc.K + 1;
+            const int per_chunk = min((int)(kFStageFloats / (7 * KV)), kRows);
+            const int64_t g0 = t * kRows;
+            const int nloc = (int)min64(kRows, N - g0);
+            float *st = reinterpret_cast<float *>(X);
+            for (int r0 = 0; r0 < nloc; r0 += per_chunk) {
+                const int nc = min(per_chunk, nloc - r0);
+                float *s_xyz = st, *s_rgb = st + 3 * nc * KV, *s_a = st + 6 * nc * KV;
+                if (row_owner && r >= r0 && r < r0 + nc)
+                    mb::convert_gaussian<DEG, BF16>(out.G, out.kc, g, y, s_xyz, s_rgb, s_a, (r - r0) * KV);
+                __syncthreads();
+                const int64_t v0 = (g0 + r0) * KV;
+                mb::block_store(out.xyz + 3 * v0, s_xyz, 3 * nc * KV);
+                mb::block_store(out.rgb + 3 * v0, s_rgb, 3 * nc * KV);
+                mb::block_store(out.alpha + v0, s_a, nc * KV);
+                __syncthreads();
+            }
         }
         tc::fence_before_sync();
         ok = __syncthreads_and(ok);
@@ -298,7 +367,7 @@ __global__ void __launch_bounds__(128, 1) mlp_act_kernel(const float *__restrict
         for (int c0 = 0; c0 < kHid; c0 += 16) {
             float v[16];
             tc::tmem_ld16(tZ1 + lo + c0, v);
-            for (int i = 0; i < 16; ++i) v[i] = gelu(v[i]);
+            gelu16(v);
             put8(H1, kHid, r, c0, v);
             put8(H1, kHid, r, c0 + 8, v + 8);
             stage_t(T, r, c0, v, 16);
@@ -310,7 +379,7 @@ __global__ void __launch_bounds__(128, 1) mlp_act_kernel(const float *__restrict
         for (int c0 = 0; c0 < kHid; c0 += 16) {
             float v[16];
             tc::tmem_ld16(tZ2 + lo + c0, v);
-            for (int i = 0; i < 16; ++i) v[i] = gelu(v[i]);
+            gelu16(v);
             put8(H2, kHid, r, c0, v);
             put8(H2, kHid, r, c0 + 8, v + 8);
             stage_t(T, r, c0, v, 16);
@@ -523,14 +592,67 @@ cudaError_t launch_mlp_features(const MlpSrc &s, int64_t N, float *X, cudaStream
     return cudaGetLastError();
 }
 
+namespace {
+
+template <bool FUSED, int DEG, bool BF16>
+cudaError_t launch_fwd(const MlpSrc &s, int64_t N, const char *packed, int n_out, const FwdOut &out,
+                       cudaStream_t st) {
+    auto fn = mlp_fwd_kernel<FUSED, DEG, BF16>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFwdSmem);
+    if (e == cudaSuccess)   // all of the unified L1 as shared memory: room for two CTAs
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e != cudaSuccess) return e;
+    // CTAs per SM from the kernel's registers and the SM's shared memory (two when both
+    // allow; the occupancy query reported one here although both limits allow two).
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, fn);
+    if (e != cudaSuccess) return e;
+    int dev = 0, smem_sm = 0, regs_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+    const int by_smem = smem_sm / (int)(kFwdSmem + 1024);
+    const int by_regs = regs_sm / max(1, fa.numRegs * kFwdThreads);
+    const int per_sm = max(1, min(kFwdCtasPerSm, min(by_smem, by_regs)));
+    const int64_t tiles = (N + kRows - 1) / kRows;
+    const int grid = (int)min64(tiles, (int64_t)sm_count() * per_sm);
+    fn<<<grid, kFwdThreads, kFwdSmem, st>>>(s, N, packed, n_out, out);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
 cudaError_t launch_mlp_forward(const MlpSrc &s, int64_t N, const char *packed, int n_out, float *corr,
                                cudaStream_t st) {
     if (N == 0) return cudaSuccess;
-    cudaFuncSetAttribute(mlp_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFwdSmem);
-    const int64_t tiles = (N + kRows - 1) / kRows;
-    const int grid = (int)min64(tiles, sm_count());
-    mlp_fwd_kernel<<<grid, kFwdThreads, kFwdSmem, st>>>(s, N, packed, n_out, corr);
-    return cudaGetLastError();
+    FwdOut out;
+    memset(&out, 0, sizeof(out));
+    out.corr = corr;
+    return launch_fwd<false, 0, false>(s, N, packed, n_out, out, st);
+}
+
+cudaError_t launch_mesh_build_mlp(const float *means, const MlpSrc &s, int64_t N, const char *packed,
+                                  const MeshBuildConst &kc, float *xyz, float *rgb, float *alpha, cudaStream_t st) {
+    if (N == 0) return cudaSuccess;
+    FwdOut out;
+    memset(&out, 0, sizeof(out));
+    out.G = mb::Gaussians{means, s.log_scales, s.quats, s.opacity, s.sh};
+    out.kc = kc;
+    out.xyz = xyz;
+    out.rgb = rgb;
+    out.alpha = alpha;
+    const int n_out = 2 * (kc.K + 1);
+    const bool bf16 = s.sh_dtype == 1;
+    switch (s.sh_degree) {
+        case 0: return bf16 ? launch_fwd<true, 0, true>(s, N, packed, n_out, out, st)
+                            : launch_fwd<true, 0, false>(s, N, packed, n_out, out, st);
+        case 1: return bf16 ? launch_fwd<true, 1, true>(s, N, packed, n_out, out, st)
+                            : launch_fwd<true, 1, false>(s, N, packed, n_out, out, st);
+        case 2: return bf16 ? launch_fwd<true, 2, true>(s, N, packed, n_out, out, st)
+                            : launch_fwd<true, 2, false>(s, N, packed, n_out, out, st);
+        default: return bf16 ? launch_fwd<true, 3, true>(s, N, packed, n_out, out, st)
+                             : launch_fwd<true, 3, false>(s, N, packed, n_out, out, st);
+    }
 }
 
 cudaError_t launch_mlp_grads(const float *X, const float *T, int64_t n, int n_out, const char *packed, char *act,

@@ -78,6 +78,9 @@ cudaError_t launch_mlp_pack(const float *W1, const float *W2, const float *W3, i
 cudaError_t launch_mlp_features(const MlpSrc &s, int64_t N, float *X, cudaStream_t st);
 cudaError_t launch_mlp_forward(const MlpSrc &s, int64_t N, const char *packed, int n_out, float *corr,
                                cudaStream_t st);
+// The conversion fused behind the initializer's inference (flat fans, n_out = 2(K+1)).
+cudaError_t launch_mesh_build_mlp(const float *means, const MlpSrc &s, int64_t N, const char *packed,
+                                  const MeshBuildConst &kc, float *xyz, float *rgb, float *alpha, cudaStream_t st);
 cudaError_t launch_mlp_grads(const float *X, const float *T, int64_t n, int n_out, const char *packed, char *act,
                              float *grads, float *loss, cudaStream_t st);
 cudaError_t launch_mlp_adam(float *W, const float *grads, float *m, float *v, int n_out, int32_t *d_step, float lr,

@@ -202,3 +202,45 @@ def test_corrections_drive_the_conversion_like_the_oracle():
     assert np.abs(xyz.cpu().numpy() - xo).max() < 2e-6
     assert np.abs(a.cpu().numpy() - ao).max() < 2e-6
     assert np.abs(rgb.cpu().numpy() - co).max() < 2e-6
+
+
+def _scaled_weights(seed, k, scale):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    n_out = 2 * (k + 1)
+    W1 = rng.normal(0, 0.35, (16, 128))
+    W2 = rng.normal(0, 0.12, (128, 128))
+    W3 = rng.normal(0, 0.1 * scale, (128, n_out))
+    return [w.astype(np.float32) for w in (W1, W2, W3)]
+
+
+@pytest.mark.parametrize("k,n,deg,bf", [(8, 4000, 3, True), (8, 130, 3, False), (15, 1000, 2, True),
+                                        (3, 777, 1, False), (6, 300, 0, True)])
+def test_fused_inference_conversion_equals_the_two_launches(k, n, deg, bf):
+    """ms_mesh_build_mlp (inference fused into the conversion, corrections kept on chip)
+    gives the fan soup of ms_mlp_forward then ms_mesh_build bit for bit: ragged tiles,
+    K = 15 (staged in two chunks of Gaussians per tile), every SH degree; and the soup
+    matches the oracle's conversion with the same corrections."""
+    sc = synthetic.surface_scene(n, 70 + k, degree=deg, clustered=True, bf16=bf)
+    net = ms.FanMLP(K=k, weights=_scaled_weights(11 + k, k, 0.5))
+    m, s, q, o, sh = scene_tensors(sc)
+    cc = np.array([0.3, 0.2, 3.0], np.float32)
+    corr = net.forward(s, q, o, sh, sc.sh_degree)
+    want = ms.mesh_build(m, s, q, o, sh, sc.sh_degree, K=k, cam_center=cc, corr=corr)
+    got = ms.mesh_build(m, s, q, o, sh, sc.sh_degree, K=k, cam_center=cc, mlp=net)
+    for a, b in zip(got, want):
+        assert torch.equal(a, b)
+    assert net.status() == (0, 0)   # no tensor-core wait expired
+    xo, co, ao = oracle.mesh_build(sc, K=k, cam_center=cc, corr=corr.cpu().numpy().astype(np.float64))
+    assert np.abs(got[0].cpu().numpy() - xo).max() < 2e-6 * max(1.0, np.abs(xo).max())
+    assert np.abs(got[1].cpu().numpy() - co).max() < 2e-6
+    assert np.abs(got[2].cpu().numpy() - ao).max() < 2e-6
+
+
+def test_fused_conversion_rejects_bad_arguments():
+    sc = synthetic.surface_scene(50, 3, degree=0)
+    m, s, q, o, sh = scene_tensors(sc)
+    net = ms.FanMLP(K=8)
+    with pytest.raises(ValueError):
+        ms.mesh_build(m, s, q, o, sh, 0, K=6, mlp=net)          # packed for K = 8
+    with pytest.raises(ValueError):
+        ms.mesh_build(m, s, q, o, sh, 0, K=8, mlp=net, corr=torch.zeros(50, 18, device="cuda"))
