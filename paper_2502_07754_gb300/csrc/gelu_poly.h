@@ -1,19 +1,9 @@
-// Generated by gen_gelu_poly.py: erfc(z) / 2 = t exp(-z^2) 2^G(s) for z >= 0, with
-// t = 1 / (1 + z / 2.5), s = 2 t - 1 and G a polynomial of degree 8, evaluated by
-// Horner's rule in binary32.
+// Generated by gen_gelu_poly.py: erfc(z) / 2 = t exp(-z^2) 2^G(t) for z >= 0, with
+// t = 1 / (1 + z / 2) and G the polynomial of degree 7 below (coefficients of
+// t^0 .. t^7), evaluated by Horner's rule in binary32.
 #pragma once
 namespace ms {
-constexpr float kGeluInvC = 4.000000000e-01f;   // 1 / 2.5
-__device__ __forceinline__ float gelu_log2_g_m1(float s) {
-    float q = -9.028298664e-04f;
-    q = fmaf(q, s, 8.464116254e-04f);
-    q = fmaf(q, s, 6.369955838e-03f);
-    q = fmaf(q, s, -2.307655988e-03f);
-    q = fmaf(q, s, -3.418095037e-02f);
-    q = fmaf(q, s, -2.606458962e-02f);
-    q = fmaf(q, s, 2.008841634e-01f);
-    q = fmaf(q, s, 1.101366639e+00f);
-    q = fmaf(q, s, -2.246009350e+00f);
-    return q;
-}
+constexpr int kGeluDeg = 7;
+constexpr float kGeluInvC = 5.000000000e-01f;   // 1 / 2
+#define MS_GELU_POLY -2.825737238e+00f, 1.441846490e+00f, 5.572204590e-01f, -9.010969661e-03f, 3.942742646e-01f, -1.306002736e+00f, 9.950978160e-01f, -2.476870716e-01f
 }  // namespace ms

@@ -52,11 +52,13 @@ constexpr uint32_t kTdZ1t = kTdZ2t + kHid * kRows * 2;     // dZ1^T [128][128]
 constexpr uint32_t kTileBytes = kTdZ1t + kHid * kRows * 2;
 
 // GELU x Phi(x) in binary32.  With z = |x| / sqrt 2 and E = erfc(z) / 2, Phi(x) is 1 - E
-// for x >= 0 and E for x < 0; E = t exp(-z^2) 2^G(2t - 1), t = 1 / (1 + z / 2.5), with G
-// the polynomial of gelu_poly.h (a least-squares fit): one reciprocal, one ex2 and nine
-// FMAs per value, no branch.  The complementary form keeps the tail (x < -5) that
-// 1 + erf(x / sqrt 2) would cancel to zero.  Relative error: below 4e-6 for x >= -5.6,
-// below 3e-5 further out (|GELU| < 1e-8 there), both from rounding the exponent.
+// for x >= 0 and E for x < 0, written Phi = fma(1 - 2 step, E, step) with step = [x >= 0];
+// E = t 2^(G(t) - x^2 log2(e) / 2), t = 1 / (1 + z / 2), with G the degree-7 polynomial of
+// gelu_poly.h (a least-squares fit): one reciprocal, one ex2, no branch.  The complementary
+// form keeps the tail (x < -5) that 1 + erf(x / sqrt 2) would cancel to zero.  Relative
+// error: below 3e-6 for x >= -5.6 and 1e-5 beyond (where |GELU| < 1e-8).  Pairs of values
+// go through the packed f32x2 FMA and multiply of sm_100-class GPUs, which halves the
+// instruction count of everything but the reciprocal and the exponential.
 __device__ __forceinline__ float ex2_approx(float a) {
     float r;
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
@@ -67,22 +69,60 @@ __device__ __forceinline__ float rcp_approx(float a) {
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
     return r;
 }
-__device__ __forceinline__ float half_erfc(float z) {   // z >= 0
-    const float t = rcp_approx(fmaf(z, kGeluInvC, 1.0f));
-    const float q = gelu_log2_g_m1(fmaf(t, 2.0f, -1.0f));
-    return t * ex2_approx(fmaf(-z * 1.4426950408889634f, z, q));
+__device__ __forceinline__ uint64_t f2(float a, float b) {
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
 }
-__device__ __forceinline__ float gelu(float x) {
-    const float E = half_erfc(fabsf(x) * 0.70710678118654752f);
-    return x >= 0.0f ? fmaf(-x, E, x) : x * E;
+__device__ __forceinline__ void unf2(uint64_t r, float &a, float &b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+}
+__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+constexpr float kGeluT = 0.35355339059327376f;        // (1 / 2) / sqrt 2: t = 1 / (1 + |x| kGeluT)
+constexpr float kGeluX2 = -0.72134752044448170f;      // -log2(e) / 2
+__device__ __forceinline__ float gelu_step(float x) { return x >= 0.0f ? 1.0f : 0.0f; }
+
+// Phi(x), one value (the derivative's first term).
+__device__ __forceinline__ float gelu_phi(float x) {
+    constexpr float c[] = {MS_GELU_POLY};
+    const float t = rcp_approx(fmaf(fabsf(x), kGeluT, 1.0f));
+    float q = c[kGeluDeg];
+#pragma unroll
+    for (int i = kGeluDeg - 1; i >= 0; --i) q = fmaf(q, t, c[i]);
+    const float E = t * ex2_approx(fmaf(x * x, kGeluX2, q));
+    const float st = gelu_step(x);
+    return fmaf(fmaf(st, -2.0f, 1.0f), E, st);
+}
+// GELU of a pair, in place; the same roundings as x * gelu_phi(x) for each value.
+__device__ __forceinline__ void gelu2(float &a, float &b) {
+    constexpr float c[] = {MS_GELU_POLY};
+    const uint64_t t = f2(rcp_approx(fmaf(fabsf(a), kGeluT, 1.0f)), rcp_approx(fmaf(fabsf(b), kGeluT, 1.0f)));
+    const uint64_t x = f2(a, b);
+    uint64_t q = f2(c[kGeluDeg], c[kGeluDeg]);
+#pragma unroll
+    for (int i = kGeluDeg - 1; i >= 0; --i) q = fma2(q, t, f2(c[i], c[i]));
+    float ga, gb;
+    unf2(fma2(mul2(x, x), f2(kGeluX2, kGeluX2), q), ga, gb);
+    const uint64_t E = mul2(t, f2(ex2_approx(ga), ex2_approx(gb)));
+    const uint64_t st = f2(gelu_step(a), gelu_step(b));
+    const uint64_t phi = fma2(fma2(st, f2(-2.0f, -2.0f), f2(1.0f, 1.0f)), E, st);
+    unf2(mul2(x, phi), a, b);
 }
 __device__ __forceinline__ float gelu_grad(float x) {
-    const float E = half_erfc(fabsf(x) * 0.70710678118654752f);
-    return (x >= 0.0f ? 1.0f - E : E) + x * 0.39894228040143268f * __expf(-0.5f * x * x);
+    return gelu_phi(x) + x * 0.39894228040143268f * __expf(-0.5f * x * x);
 }
 __device__ __forceinline__ void gelu16(float v[16]) {
 #pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = gelu(v[i]);
+    for (int i = 0; i < 16; i += 2) gelu2(v[i], v[i + 1]);
 }
 
 __device__ __forceinline__ uint16_t bf16_bits(float x) { return __bfloat16_as_ushort(__float2bfloat16_rn(x)); }
@@ -100,13 +140,27 @@ __device__ __forceinline__ void put8(char *tile, int Kc, int r, int k0, const fl
     *reinterpret_cast<uint4 *>(tile + tc::cm_offset(r, k0, Kc)) = u;
 }
 
-// The 16 inputs of Gaussian g (see oracle/mlp.py for the list): log-scales, normalised
-// quaternion, opacity, degree-0 SH, scales sorted descending over the largest, and
-// log(s_min / s_mid), then the constant 1.
-__device__ __forceinline__ void gaussian_features(const MlpSrc &s, int64_t g, float f[kIn]) {
-    const float l0 = s.log_scales[3 * g], l1 = s.log_scales[3 * g + 1], l2 = s.log_scales[3 * g + 2];
-    const float4 q = *reinterpret_cast<const float4 *>(s.quats + 4 * g);
+// The 16 inputs of a Gaussian: log-scales, normalised quaternion, opacity, degree-0 SH,
+// scales sorted descending over the largest, and log(s_min / s_mid), then the constant 1.
+__device__ __forceinline__ void features_from(float l0, float l1, float l2, float4 q, float op, const float dc[3],
+                                              float f[kIn]) {
     const float qn = 1.0f / sqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
+    float a = l0, b = l1, c = l2, t;   // sort descending
+    if (a < b) { t = a; a = b; b = t; }
+    if (b < c) { t = b; b = c; c = t; }
+    if (a < b) { t = a; a = b; b = t; }
+    f[0] = l0; f[1] = l1; f[2] = l2;
+    f[3] = q.x * qn; f[4] = q.y * qn; f[5] = q.z * qn; f[6] = q.w * qn;
+    f[7] = op;
+    f[8] = dc[0]; f[9] = dc[1]; f[10] = dc[2];
+    f[11] = 1.0f;
+    f[12] = expf(b - a);
+    f[13] = expf(c - a);
+    f[14] = c - b;
+    f[15] = 1.0f;
+}
+
+__device__ __forceinline__ void gaussian_features(const MlpSrc &s, int64_t g, float f[kIn]) {
     const int nb = (s.sh_degree + 1) * (s.sh_degree + 1);
     float dc[3];
     for (int c = 0; c < 3; ++c) {
@@ -114,19 +168,58 @@ __device__ __forceinline__ void gaussian_features(const MlpSrc &s, int64_t g, fl
         dc[c] = s.sh_dtype == 0 ? reinterpret_cast<const float *>(s.sh)[i]
                                 : __uint_as_float((uint32_t)reinterpret_cast<const uint16_t *>(s.sh)[i] << 16);
     }
-    float a = l0, b = l1, c = l2, t;   // sort descending
-    if (a < b) { t = a; a = b; b = t; }
-    if (b < c) { t = b; b = c; c = t; }
-    if (a < b) { t = a; a = b; b = t; }
-    f[0] = l0; f[1] = l1; f[2] = l2;
-    f[3] = q.x * qn; f[4] = q.y * qn; f[5] = q.z * qn; f[6] = q.w * qn;
-    f[7] = s.opacity[g];
-    f[8] = dc[0]; f[9] = dc[1]; f[10] = dc[2];
-    f[11] = 1.0f;
-    f[12] = expf(b - a);
-    f[13] = expf(c - a);
-    f[14] = c - b;
-    f[15] = 1.0f;
+    features_from(s.log_scales[3 * g], s.log_scales[3 * g + 1], s.log_scales[3 * g + 2],
+                  *reinterpret_cast<const float4 *>(s.quats + 4 * g), s.opacity[g], dc, f);
+}
+
+// The raw inputs of a row's features, brought into shared memory by asynchronous copies
+// one tile ahead (48 bytes a row: log-scales at 0, opacity at 12, quaternion at 16, the
+// first SH coefficients at 32: three f32, or four bf16 of which three are used).  Each
+// thread copies and later reads its own row only, so the copies need no barrier.
+constexpr int kRawRow = 48;
+__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(tc::smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(tc::smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// Whether the raw inputs can be copied in 4-byte pieces: 4-byte aligned arrays, and for
+// bf16 SH an even number of coefficients per Gaussian (degree 1 or 3).
+__host__ __device__ __forceinline__ bool raw_copy_ok(const MlpSrc &s) {
+    const int nb = (s.sh_degree + 1) * (s.sh_degree + 1);
+    const uintptr_t mis = (reinterpret_cast<uintptr_t>(s.sh) | reinterpret_cast<uintptr_t>(s.log_scales) |
+                           reinterpret_cast<uintptr_t>(s.opacity)) & 3;
+    return mis == 0 && (s.sh_dtype == 0 || (nb % 2) == 0);
+}
+__device__ __forceinline__ void raw_fetch(const MlpSrc &s, int64_t g, char *row) {
+    const int nb = (s.sh_degree + 1) * (s.sh_degree + 1);
+    for (int i = 0; i < 3; ++i) cp_async4(row + 4 * i, s.log_scales + 3 * g + i);
+    cp_async4(row + 12, s.opacity + g);
+    cp_async16(row + 16, s.quats + 4 * g);
+    if (s.sh_dtype == 0) {
+        const float *p = reinterpret_cast<const float *>(s.sh) + g * nb * 3;
+        for (int i = 0; i < 3; ++i) cp_async4(row + 32 + 4 * i, p + i);
+    } else {
+        const uint16_t *p = reinterpret_cast<const uint16_t *>(s.sh) + g * nb * 3;
+        cp_async4(row + 32, p);
+        cp_async4(row + 36, p + 2);
+    }
+}
+__device__ __forceinline__ void raw_features(const MlpSrc &s, const char *row, float f[kIn]) {
+    const float *r = reinterpret_cast<const float *>(row);
+    float dc[3];
+    if (s.sh_dtype == 0) {
+        dc[0] = r[8]; dc[1] = r[9]; dc[2] = r[10];
+    } else {
+        const uint32_t w0 = reinterpret_cast<const uint32_t *>(row)[8], w1 = reinterpret_cast<const uint32_t *>(row)[9];
+        dc[0] = __uint_as_float(w0 << 16);
+        dc[1] = __uint_as_float(w0 & 0xFFFF0000u);
+        dc[2] = __uint_as_float(w1 << 16);
+    }
+    features_from(r[0], r[1], r[2], *reinterpret_cast<const float4 *>(row + 16), r[3], dc, f);
 }
 
 struct TcState {
@@ -162,6 +255,15 @@ __device__ __forceinline__ bool wait_mma(TcState *S, uint32_t &phase, uint32_t *
     return ok;
 }
 
+// Slot version: every thread of the slot waits on the slot's mbarrier.
+__device__ __forceinline__ bool wait_mma_slot(uint64_t *mbar, uint32_t &phase, uint32_t *timeouts, bool counter) {
+    const bool ok = tc::mbar_wait(mbar, phase, kTcWaitLimit);
+    phase ^= 1u;
+    if (!ok && counter) atomicAdd(timeouts, 1u);
+    tc::fence_after_sync();
+    return ok;
+}
+
 // Shared prologue: weights into shared memory, barrier, tensor memory.
 __device__ __forceinline__ void setup(char *smem, const char *packed, uint32_t wbytes_lo, uint32_t wbytes_hi,
                                       char *wdst, TcState *S, uint32_t ncols) {
@@ -188,32 +290,73 @@ __device__ __forceinline__ void teardown(TcState *S, uint32_t ncols) {
 
 // ------------------------------------------------------------------ inference
 
+// One CTA per SM holds the three forward weight tiles once and runs kSlots independent
+// 128-row tiles ("slots"), each with 8 warps, its own X / H operands, raw-input buffer,
+// mbarrier, named barrier and 128 tensor-memory columns (Z1, Z2 and Z3 of a tile reuse the
+// same columns: each product is issued after the previous accumulator has been read).  While
+// one slot waits for its product on the tensor cores, the other slots' GELU epilogues run.
+constexpr int kSlots = 4;
+constexpr int kSlotThreads = 256;
+constexpr int kFwdThreads = kSlots * kSlotThreads;
 constexpr uint32_t kFwdW = kW1f, kFwdWEnd = kW3b;        // W1f, W2f, W3f
-constexpr uint32_t kFX = kFwdWEnd - kFwdW;               // X  [128][16]
-constexpr uint32_t kFH = kFX + kRows * kIn * 2;          // H1, then H2 [128][128]
-constexpr uint32_t kFState = kFH + kRows * kHid * 2;
-constexpr uint32_t kFwdSmem = kFState + 64;
-// After the last product of a tile, X and H are free: the fused conversion stages the
-// tile's vertices there.
-constexpr uint32_t kFStageFloats = (kFState - kFX) / 4;
+constexpr uint32_t kSlotX = 0;                           // X  [128][16]
+constexpr uint32_t kSlotH = kSlotX + kRows * kIn * 2;    // H1, then H2 [128][128]
+constexpr uint32_t kSlotRaw = kSlotH + kRows * kHid * 2; // [128][kRawRow] raw inputs
+constexpr uint32_t kSlotBytes = kSlotRaw + kRows * kRawRow;
+constexpr uint32_t kFSlots = kFwdWEnd - kFwdW;
+constexpr uint32_t kFState = kFSlots + kSlots * kSlotBytes;   // kSlots mbarriers, TMEM base
+constexpr uint32_t kFwdSmem = kFState + 8 * kSlots + 16;
+// After the last product of a tile, the slot's X and H are free: the fused conversion
+// stages the tile's vertices there.
+constexpr uint32_t kStageFloats = (kSlotRaw - kSlotX) / 4;
+static_assert(kSlotBytes % 1024 == 0, "slot operands keep the 1024-byte alignment");
+static_assert(kFwdSmem <= 227 * 1024, "shared memory");
 
-// 16 warps: warp w reads tensor-memory lanes 32 (w % 4) .. + 31 (rows of the tile) and
-// handles accumulator columns 32 (w / 4) .. + 31, so four warps share each row's GELU
-// epilogue; warps 0-3 also compute the inputs and the outputs.  H2 overwrites H1 once the
-// second product has read it, which keeps a CTA at 80 KB of shared memory and 256
-// tensor-memory columns: two CTAs share an SM, and one's epilogue runs while the other's
-// products are on the tensor cores.
-constexpr int kFwdThreads = 512;
-constexpr int kFwdCtasPerSm = 2;
+// Named barrier of one slot (ids 1..kSlots; 0 is the CTA barrier), optionally AND-reducing.
+__device__ __forceinline__ void slot_sync(int slot) {
+    asm volatile("bar.sync %0, %1;" ::"r"(slot + 1), "r"(kSlotThreads) : "memory");
+}
+__device__ __forceinline__ bool slot_sync_and(int slot, bool v) {
+    uint32_t out;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 q, %1, 0;\n\t"
+        "bar.red.and.pred p, %2, %3, q;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(out) : "r"((uint32_t)v), "r"(slot + 1), "r"(kSlotThreads) : "memory");
+    return out != 0;
+}
+// The slot's operands were written: visible to the tensor cores, ordered after earlier
+// tensor-memory reads; the slot's first thread then issues.
+__device__ __forceinline__ void slot_sync_then(int slot, bool issuer) {
+    tc::fence_proxy_async();
+    tc::fence_before_sync();
+    slot_sync(slot);
+    if (issuer) tc::fence_after_sync();
+}
 
-__device__ __forceinline__ void gelu_cols(uint32_t tz, char *H, int r, int c0) {
-#pragma unroll
-    for (int h = 0; h < 32; h += 16) {
+// Warp w of a slot reads tensor-memory lanes 32 (w % 4) .. + 31 (rows of the tile) and
+// columns 64 (w / 4) .. + 63.
+__device__ __forceinline__ void gelu_cols64(uint32_t tz, char *H, int r, int c0) {
+#pragma unroll 1
+    for (int h = 0; h < 64; h += 16) {
         float v[16];
         tc::tmem_ld16(tz + c0 + h, v);
         gelu16(v);
         put8(H, kHid, r, c0 + h, v);
         put8(H, kHid, r, c0 + h + 8, v + 8);
+    }
+}
+
+// Copies n floats from shared to global with the 256 threads of a slot (16-byte stores
+// when both ends allow it).
+__device__ __forceinline__ void slot_store(float *dst, const float *src, int n, int st) {
+    if ((reinterpret_cast<uintptr_t>(dst) & 15) == 0 && (n & 3) == 0) {
+        float4 *d4 = reinterpret_cast<float4 *>(dst);
+        const float4 *s4 = reinterpret_cast<const float4 *>(src);
+        for (int i = st; i < n / 4; i += kSlotThreads) d4[i] = s4[i];
+    } else {
+        for (int i = st; i < n; i += kSlotThreads) dst[i] = src[i];
     }
 }
 
@@ -227,82 +370,126 @@ struct FwdOut {
 };
 
 template <bool FUSED, int DEG, bool BF16>
-__global__ void __launch_bounds__(kFwdThreads, kFwdCtasPerSm) mlp_fwd_kernel(const MlpSrc s, int64_t N,
-                                                                             const char *__restrict__ packed,
-                                                                             int n_out, const FwdOut out) {
+__global__ void __launch_bounds__(kFwdThreads, 1) mlp_fwd_kernel(const MlpSrc s, int64_t N,
+                                                                const char *__restrict__ packed, int n_out,
+                                                                const FwdOut out) {
     extern __shared__ __align__(1024) char smem[];
-    TcState *S = reinterpret_cast<TcState *>(smem + kFState);
+    uint64_t *mbars = reinterpret_cast<uint64_t *>(smem + kFState);
+    uint32_t *tmem_base = reinterpret_cast<uint32_t *>(smem + kFState + 8 * kSlots);
     uint32_t *timeouts = reinterpret_cast<uint32_t *>(const_cast<char *>(packed) + kStatusOff);
-    setup(smem, packed, kFwdW, kFwdWEnd, smem, S, 256);
+    {   // weights, barriers, tensor memory
+        const uint4 *src = reinterpret_cast<const uint4 *>(packed + kFwdW);
+        uint4 *dst = reinterpret_cast<uint4 *>(smem);
+        for (uint32_t i = threadIdx.x; i < (kFwdWEnd - kFwdW) / 16; i += blockDim.x) dst[i] = src[i];
+        if (threadIdx.x == 0) {
+            for (int k = 0; k < kSlots; ++k) tc::mbar_init(&mbars[k], 1);
+            tc::mbar_init_fence();
+        }
+        if (threadIdx.x < 32) tc::tmem_alloc(tmem_base, 128 * kSlots);
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+    }
     const char *W1 = smem + (kW1f - kFwdW), *W2 = smem + (kW2f - kFwdW), *W3 = smem + (kW3f - kFwdW);
-    char *X = smem + kFX, *H = smem + kFH;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int r = 32 * (warp & 3) + lane;   // the row (tensor-memory lane) this thread reads
-    const int c0 = 32 * (warp >> 2);        // its accumulator column group
-    const bool row_owner = warp < 4;
-    const uint32_t lane_off = (uint32_t)(32 * (warp & 3)) << 16;
-    const uint32_t tZ1 = S->tmem, tZ2 = S->tmem + 128, tZ3 = S->tmem;
+    const int tid = threadIdx.x, slot = tid / kSlotThreads, st = tid % kSlotThreads;
+    const int w = st >> 5, lane = tid & 31;
+    char *X = smem + kFSlots + slot * kSlotBytes + kSlotX;
+    char *H = smem + kFSlots + slot * kSlotBytes + kSlotH;
+    char *raw = smem + kFSlots + slot * kSlotBytes + kSlotRaw;
+    uint64_t *mbar = &mbars[slot];
+    const int r = 32 * (w & 3) + lane;   // the row (tensor-memory lane) this thread reads
+    const int c0 = 64 * (w >> 2);        // its accumulator columns
+    const bool row_owner = w < 4;
+    const bool issuer = st == 0;
+    const uint32_t tz = *tmem_base + 128u * slot + ((uint32_t)(32 * (w & 3)) << 16);
+    const uint32_t tz0 = *tmem_base + 128u * slot;
     const int64_t tiles = (N + kRows - 1) / kRows;
+    const int64_t stride = (int64_t)gridDim.x * kSlots;
+    const bool pre = raw_copy_ok(s);
+    int64_t t = (int64_t)blockIdx.x * kSlots + slot;
+    if (pre && row_owner) {   // this slot's first tile; later ones are fetched a tile ahead
+        const int64_t g = t * kRows + r;
+        if (t < tiles && g < N) raw_fetch(s, g, raw + r * kRawRow);
+        cp_async_commit();
+    }
     uint32_t phase = 0;
     bool ok = true;
-    for (int64_t t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
+    for (; t < tiles; t += stride) {
         const int64_t g = t * kRows + r;
         if (row_owner) {
             float f[kIn];
-            if (g < N) {
-                gaussian_features(s, g, f);
-            } else {
+            if (g >= N) {
 #pragma unroll
                 for (int i = 0; i < kIn; ++i) f[i] = 0.0f;
+            } else if (pre) {
+                cp_async_wait_all();
+                raw_features(s, raw + r * kRawRow, f);
+            } else {
+                gaussian_features(s, g, f);
             }
             put8(X, kIn, r, 0, f);
             put8(X, kIn, r, 8, f + 8);
+            if (pre) {   // the row was read: the next tile's raw inputs replace it
+                const int64_t gn = g + stride * kRows;
+                if (gn < N) raw_fetch(s, gn, raw + r * kRawRow);
+                cp_async_commit();
+            }
         }
-        sync_then(tid == 0);
-        if (tid == 0) issue(tZ1, X, W1, kIn, kHid, false, &S->mbar);
-        ok = wait_mma(S, phase, timeouts);
-        gelu_cols(tZ1 + lane_off, H, r, c0);
-        sync_then(tid == 0);
-        if (tid == 0) issue(tZ2, H, W2, kHid, kHid, false, &S->mbar);
-        ok = wait_mma(S, phase, timeouts) && ok;
-        gelu_cols(tZ2 + lane_off, H, r, c0);   // the product has read H1: H2 replaces it
-        sync_then(tid == 0);
-        if (tid == 0) issue(tZ3, H, W3, kHid, kOutPad, false, &S->mbar);
-        ok = wait_mma(S, phase, timeouts) && ok;
+        tc::fence_proxy_async();
+        tc::fence_before_sync();
+        ok = slot_sync_and(slot, ok);
+        if (!ok) break;
+        if (issuer) {
+            tc::fence_after_sync();
+            issue(tz0, X, W1, kIn, kHid, false, mbar);
+        }
+        ok = wait_mma_slot(mbar, phase, timeouts, issuer);
+        gelu_cols64(tz, H, r, c0);
+        slot_sync_then(slot, issuer);
+        if (issuer) issue(tz0, H, W2, kHid, kHid, false, mbar);
+        ok = wait_mma_slot(mbar, phase, timeouts, issuer) && ok;
+        gelu_cols64(tz, H, r, c0);   // the product has read H1: H2 replaces it
+        slot_sync_then(slot, issuer);
+        if (issuer) issue(tz0, H, W3, kHid, kOutPad, false, mbar);
+        ok = wait_mma_slot(mbar, phase, timeouts, issuer) && ok;
         float y[32];
         if (row_owner) {
-            tc::tmem_ld16(tZ3 + lane_off, *reinterpret_cast<float(*)[16]>(y));
-            tc::tmem_ld16(tZ3 + lane_off + 16, *reinterpret_cast<float(*)[16]>(y + 16));
+            tc::tmem_ld16(tz, *reinterpret_cast<float(*)[16]>(y));
+            tc::tmem_ld16(tz + 16, *reinterpret_cast<float(*)[16]>(y + 16));
         }
         if (!FUSED) {
             if (row_owner && g < N)
                 for (int o = 0; o < n_out; ++o) out.corr[g * n_out + o] = y[o];
         } else {
             // The tile's fans, staged in X and H (free now: every product has completed)
-            // in chunks of whole Gaussians, each chunk stored coalesced by all threads.
+            // in chunks of whole Gaussians, each chunk stored coalesced by the slot.
             const int KV = out.kc.K + 1;
-            const int per_chunk = min((int)(kFStageFloats / (7 * KV)), kRows);
+            const int per_chunk = min((int)(kStageFloats / (7 * KV)), kRows);
             const int64_t g0 = t * kRows;
             const int nloc = (int)min64(kRows, N - g0);
-            float *st = reinterpret_cast<float *>(X);
+            float *stg = reinterpret_cast<float *>(X);
             for (int r0 = 0; r0 < nloc; r0 += per_chunk) {
                 const int nc = min(per_chunk, nloc - r0);
-                float *s_xyz = st, *s_rgb = st + 3 * nc * KV, *s_a = st + 6 * nc * KV;
+                float *s_xyz = stg, *s_rgb = stg + 3 * nc * KV, *s_a = stg + 6 * nc * KV;
                 if (row_owner && r >= r0 && r < r0 + nc)
                     mb::convert_gaussian<DEG, BF16>(out.G, out.kc, g, y, s_xyz, s_rgb, s_a, (r - r0) * KV);
-                __syncthreads();
+                slot_sync(slot);
                 const int64_t v0 = (g0 + r0) * KV;
-                mb::block_store(out.xyz + 3 * v0, s_xyz, 3 * nc * KV);
-                mb::block_store(out.rgb + 3 * v0, s_rgb, 3 * nc * KV);
-                mb::block_store(out.alpha + v0, s_a, nc * KV);
-                __syncthreads();
+                slot_store(out.xyz + 3 * v0, s_xyz, 3 * nc * KV, st);
+                slot_store(out.rgb + 3 * v0, s_rgb, 3 * nc * KV, st);
+                slot_store(out.alpha + v0, s_a, nc * KV, st);
+                slot_sync(slot);
             }
         }
-        tc::fence_before_sync();
-        ok = __syncthreads_and(ok);
+        // the next tile's features overwrite X and its first product Z3's columns: the
+        // barrier at the top of the next iteration orders them after these reads
     }
-    if (!ok) tc::mbar_wait(&S->mbar, phase, kTcWaitLimit);   // let an unfinished product drain
-    teardown(S, 256);
+    if (!ok) tc::mbar_wait(mbar, phase, kTcWaitLimit);   // let an unfinished product drain
+    cp_async_wait_all();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (threadIdx.x < 32) tc::tmem_dealloc(*tmem_base, 128 * kSlots);
 }
 
 // ------------------------------------------------------------------ training: activations
@@ -599,23 +786,9 @@ cudaError_t launch_fwd(const MlpSrc &s, int64_t N, const char *packed, int n_out
                        cudaStream_t st) {
     auto fn = mlp_fwd_kernel<FUSED, DEG, BF16>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFwdSmem);
-    if (e == cudaSuccess)   // all of the unified L1 as shared memory: room for two CTAs
-        e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e != cudaSuccess) return e;
-    // CTAs per SM from the kernel's registers and the SM's shared memory (two when both
-    // allow; the occupancy query reported one here although both limits allow two).
-    cudaFuncAttributes fa;
-    e = cudaFuncGetAttributes(&fa, fn);
-    if (e != cudaSuccess) return e;
-    int dev = 0, smem_sm = 0, regs_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-    cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
-    const int by_smem = smem_sm / (int)(kFwdSmem + 1024);
-    const int by_regs = regs_sm / max(1, fa.numRegs * kFwdThreads);
-    const int per_sm = max(1, min(kFwdCtasPerSm, min(by_smem, by_regs)));
     const int64_t tiles = (N + kRows - 1) / kRows;
-    const int grid = (int)min64(tiles, (int64_t)sm_count() * per_sm);
+    const int grid = (int)min64((tiles + kSlots - 1) / kSlots, (int64_t)sm_count());
     fn<<<grid, kFwdThreads, kFwdSmem, st>>>(s, N, packed, n_out, out);
     return cudaGetLastError();
 }
