@@ -458,8 +458,11 @@ __global__ void __launch_bounds__(kFwdThreads, 1) mlp_fwd_kernel(const MlpSrc s,
             tc::tmem_ld16(tz + 16, *reinterpret_cast<float(*)[16]>(y + 16));
         }
         if (!FUSED) {
-            if (row_owner && g < N)
-                for (int o = 0; o < n_out; ++o) out.corr[g * n_out + o] = y[o];
+            if (row_owner && g < N) {
+#pragma unroll
+                for (int o = 0; o < kOutPad; ++o)   // unrolled: y stays in registers
+                    if (o < n_out) out.corr[g * n_out + o] = y[o];
+            }
         } else {
             // The tile's fans, staged in X and H (free now: every product has completed)
             // in chunks of whole Gaussians, each chunk stored coalesced by the slot.
