@@ -479,21 +479,15 @@ def compact_batch(idx, steps, warmup, flush):
     br = ms.BatchRenderer(sc.n, K, cams)
     target = br.forward(*ms.mesh_build(*tG, tg.sh_degree, K=K, cam_center=centre)).clone()
     del tG
-    net, corr = None, None
-    if idx == 5:
-        net = ms.FanMLP(K=K, seed=1)
-        corr = torch.empty(sc.n, 2 * (K + 1), device="cuda")
-        net.forward(G[1], G[2], G[3], G[4], sc.sh_degree, out=corr)
-    xyz, rgb, a = ms.mesh_build(*G, sc.sh_degree, K=K, cam_center=centre, corr=corr)
+    net = ms.FanMLP(K=K, seed=1) if idx == 5 else None
+    xyz, rgb, a = ms.mesh_build(*G, sc.sh_degree, K=K, cam_center=centre, mlp=net)
     br.forward(xyz, rgb, a)
     br.autotune(xyz, rgb, a, reps=1, headroom=0.05)
     flat = br.new_flat()
     adam = ms.FanAdam(xyz, rgb, a, device_step=True)
 
     def step():
-        if net is not None:
-            net.forward(G[1], G[2], G[3], G[4], sc.sh_degree, out=corr)
-        x, c, al = ms.mesh_build(*G, sc.sh_degree, K=K, cam_center=centre, corr=corr, out=(xyz, rgb, a))
+        x, c, al = ms.mesh_build(*G, sc.sh_degree, K=K, cam_center=centre, mlp=net, out=(xyz, rgb, a))
         br.forward(x, c, al, flat, check_status=False)
         _, dL = ms.l1_loss(flat, target)
         br.backward(x, c, al, flat, dL, into_workspace=True)
@@ -521,8 +515,9 @@ def compact_batch(idx, steps, warmup, flush):
          "fwd_mpix_s": npx / (ms_fwd * 1e-3) / 1e6, "fwd_ms": ms_fwd, "tile": int(br.params.tile),
          "kbuf": int(br.params.kbuf), "step": "one CUDA graph", "target": "the scene jittered by N(0, 1e-3)"}
     if net is not None:
-        r["initializer"] = ("tensor-core MLP inference of every Gaussian in the step, untrained weights "
-                            "(the same work; bench.py --workload 5 runs the trained-network experiment)")
+        r["initializer"] = ("tensor-core MLP inference of every Gaussian fused into the conversion in the step, "
+                            "untrained weights (the same work; bench.py --workload 5 runs the trained-network "
+                            "experiment)")
     return r
 
 
@@ -771,6 +766,26 @@ def initializer_experiment(args, w, K, cams, centre, G):
         f1[i].record()
     torch.cuda.synchronize()
     inf_ms = sum(a_.elapsed_time(b_) for a_, b_ in zip(f0, f1)) / 10
+    # the same inference fused into the conversion (corrections stay on chip), against the
+    # two launches it replaces
+    fo = tuple(torch.empty(Gs.n * (K + 1), 3, device="cuda") for _ in range(2)) + \
+        (torch.empty(Gs.n * (K + 1), device="cuda"),)
+    conv = lambda **kw: ms.mesh_build(Gs.means, Gs.log_scales, Gs.quats, Gs.opacity, Gs.sh, Gs.sh_degree, K=K,
+                                      cam_center=centre, out=fo, **kw)
+    for _ in range(3):
+        conv(mlp=net)
+    for i in range(10):
+        f0[i].record()
+        conv(mlp=net)
+        f1[i].record()
+    torch.cuda.synchronize()
+    fused_ms = sum(a_.elapsed_time(b_) for a_, b_ in zip(f0, f1)) / 10
+    for i in range(10):
+        f0[i].record()
+        conv(corr=corr)
+        f1[i].record()
+    torch.cuda.synchronize()
+    build_ms = sum(a_.elapsed_time(b_) for a_, b_ in zip(f0, f1)) / 10
     cmp = I.compare(Gs, cams, K, net, args.finetune_steps, centre, eval_every=10)
     target = I.source_targets(Gs, cams, centre)
     st, timeouts = net.status()
@@ -790,6 +805,9 @@ def initializer_experiment(args, w, K, cams, centre, G):
                       "tflops": train_tf, "frac_of_measured_bf16": train_tf / tc_peak},
         "mlp_inference": {"rows": Gs.n, "ms": inf_ms, "rows_per_s": Gs.n / (inf_ms * 1e-3), "tflops": inf_tf,
                           "frac_of_measured_bf16": inf_tf / tc_peak},
+        "fused_conversion": {"ms": fused_ms, "two_launch_ms": inf_ms + build_ms,
+                             "tflops": Gs.n * MLP_FLOPS_PER_ROW / (fused_ms * 1e-3) / 1e12,
+                             "corrections_hbm_bytes_saved": Gs.n * 2 * (K + 1) * 4 * 2},
         "psnr_db": {"plain": cmp["plain"], "mlp": cmp["mlp"]},
         "steps_to_plain_final": cmp["steps_to_plain_final"],
         "tensor_core_timeouts": timeouts,
@@ -823,21 +841,18 @@ def run_batch(args, ws, rank, local):
     br = ms.BatchRenderer(sc.n, K, cams)
     npx = br.n_pixels
 
-    net, init_report, corr = None, None, None
+    net, init_report = None, None
     if args.workload == 5:
         # the learned initializer: trained on pairs from fine-tunes of other scenes, judged
         # against the plain conversion on this one; its inference is part of every step
         net, init_report, target = initializer_experiment(args, w, K, cams, centre, G)
-        corr = torch.empty(sc.n, 2 * (K + 1), device="cuda")
     else:
         tg = w.target_scene
         tG = [dev(tg.means), dev(tg.log_scales), dev(tg.quats), dev(tg.opacity), G[4]]
         target = br.forward(*ms.mesh_build(*tG, tg.sh_degree, K=K, cam_center=centre)).clone()
         del tG
 
-    if net is not None:
-        net.forward(G[1], G[2], G[3], G[4], sc.sh_degree, out=corr)
-    xyz, rgb, a = ms.mesh_build(*G, sc.sh_degree, K=K, cam_center=centre, corr=corr)
+    xyz, rgb, a = ms.mesh_build(*G, sc.sh_degree, K=K, cam_center=centre, mlp=net)
     br.forward(xyz, rgb, a)
     tune = None
     if not args.no_autotune:
@@ -848,9 +863,7 @@ def run_batch(args, ws, rank, local):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     def step(gs):
-        if net is not None:
-            net.forward(gs[1], gs[2], gs[3], gs[4], sc.sh_degree, out=corr)
-        x, c, al = ms.mesh_build(*gs, sc.sh_degree, K=K, cam_center=centre, corr=corr, out=(xyz, rgb, a))
+        x, c, al = ms.mesh_build(*gs, sc.sh_degree, K=K, cam_center=centre, mlp=net, out=(xyz, rgb, a))
         br.forward(x, c, al, flat, check_status=False)
         loss, dL = ms.l1_loss(flat, target)
         br.backward(x, c, al, flat, dL, into_workspace=True)   # gradients stay in the workspace
@@ -952,8 +965,8 @@ def run_batch(args, ws, rank, local):
             "work": {"pairs": info.pairs, "rect_tests": info.rect_tests, "fragments": info.fragments,
                      "commits": info.commits, "extra_passes": info.extra_passes, "sort_bits": info.sort_bits}}
     if init_report is not None:
-        line["config"]["step"] = ("mlp_forward+mesh_build+batch_render+l1+batch_render_backward+adam "
-                                  "in one CUDA graph")
+        line["config"]["step"] = ("mesh_build_mlp (inference fused into the conversion)+batch_render+l1+"
+                                  "batch_render_backward+adam in one CUDA graph")
         line["initializer"] = init_report
     if tune is not None:
         line["autotune"] = {"cand_ms": [round(x, 3) for x in tune.cand_ms], "best": tune.best,

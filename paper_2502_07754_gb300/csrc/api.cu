@@ -421,7 +421,8 @@ static ms_status mesh_build_common(const float *means, const float *log_scales, 
     kc.sh_vec_ok = (reinterpret_cast<uintptr_t>(sh) & 15) == 0;
     cudaError_t e;
     {
-        StageScope sc(MS_STAGE_MESH_BUILD, (cudaStream_t)stream);
+        // the fused kernel is the initializer's inference with the conversion in its epilogue
+        StageScope sc(mlp_packed ? MS_STAGE_MLP : MS_STAGE_MESH_BUILD, (cudaStream_t)stream);
         if (mlp_packed) {
             const MlpSrc src{log_scales, quats, opacity, sh, sh_dtype, sh_degree};
             e = launch_mesh_build_mlp(means, src, N, static_cast<const char *>(mlp_packed), kc, xyz, rgb, alpha,

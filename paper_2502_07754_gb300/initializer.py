@@ -40,9 +40,10 @@ def psnr(m: float) -> float:
     return -10.0 * math.log10(max(m, 1e-20))
 
 
-def convert(G: Gaussians, K: int, cam_center, corr=None):
+def convert(G: Gaussians, K: int, cam_center, corr=None, mlp=None):
+    """The conversion, with corrections given, or predicted by `mlp` inside the same kernel."""
     return api.mesh_build(G.means, G.log_scales, G.quats, G.opacity, G.sh, G.sh_degree, K=K, cam_center=cam_center,
-                          corr=corr)
+                          corr=corr, mlp=mlp)
 
 
 def gaussian_colors(G: Gaussians, cam_center):
@@ -132,10 +133,7 @@ def compare(G: Gaussians, cams, K, net: FanMLP, steps, cam_center, eval_every=10
     targets = source_targets(G, cams, cam_center)
     out = {}
     for name in ("plain", "mlp"):
-        corr = None
-        if name == "mlp":
-            corr = net.forward(G.log_scales, G.quats, G.opacity, G.sh, G.sh_degree)
-        xyz, rgb, a = convert(G, K, cam_center, corr)
+        xyz, rgb, a = convert(G, K, cam_center, mlp=net if name == "mlp" else None)
         out[name] = FineTuner(G.n, K, cams, lr_color).run(xyz, rgb, a, targets, steps, eval_every)
     final_plain = out["plain"][-1][1]
     reach = next((s for s, p in out["mlp"] if p >= final_plain), None)
