@@ -14,6 +14,15 @@
  *                       (Sec. 3 "Fine-tuning", "Optimization and Pruning")
  *   ms_l1_loss, ms_fine_tune_loss, ms_adam_step   the L1 term and the full loss of Eq. 3,
  *                       and the two-learning-rate update
+ *   ms_batch_render     all of the above for up to 32 views in one index space
+ *   ms_prune_faces      the pruning of Sec. 3 "Optimization and Pruning" (per face)
+ *   ms_mesh_build_3d, ms_three_fan_sum_copies   the three-fan conversion of 3D Gaussians
+ *   ms_mesh_render      explicit triangles over a shared vertex array (centroid fans),
+ *   ms_mesh_prior_*     and the mesh-prior mode ("MeshSplats with Mesh Prior")
+ *   ms_bvh_build, ms_raytrace   ray tracing of the triangles with shadows (the secondary
+ *                       effects the mesh form is for)
+ *   ms_mlp_*, ms_mesh_build_mlp   a learned fan initializer on the tensor cores, fused into
+ *                       the conversion
  *
  * Conventions (all entry points):
  *   - Every pointer named d_* or documented as "device" is caller-owned device memory;
@@ -32,19 +41,32 @@
  *   - Camera: pinhole, OpenCV axes (x right, y down, z forward), X_cam = R_cw (p - C),
  *     pixel (fx X/Z + cx, fy Y/Z + cy); pixel (i, j) has its centre at (i+0.5, j+0.5).
  *
- * Decisions.  Coverage (top-left fill rule) and the per-pixel depth order are decided
- * in IEEE binary32 by these formulas, evaluated left to right with round-to-nearest
- * and no fused multiply-add:
- *   d = p - C;  X = (R0 d.x + R1 d.y) + R2 d.z (rows of R_cw likewise for Y, Z);
- *   xs = fx (X / Z) + cx;  ys = fy (Y / Z) + cy;  iz = 1 / Z;
- *   vertex valid iff Z > znear and |xs|, |ys| <= 2^17 (triangles with an invalid
- *   vertex are culled);
- *   area2(A,B,C) = (xB - xA)(yC - yA) - (yB - yA)(xC - xA); 0 never covers, < 0 swaps B,C;
- *   edge value of the vertex pair {a < b} (by vertex index) at pixel centre p:
- *   F = (xb - xa)(py - ya) - (yb - ya)(px - xa), negated when the oriented edge runs b->a;
- *   an edge passes if E > 0, or E == 0 and its direction (ex, ey) has ey < 0, or ey == 0
- *   and ex > 0; depth Zf = clamp(area2 / ((E0 iz0 + E1 iz1) + E2 iz2), min Z, max Z);
- *   order: ascending Zf, ties by ascending triangle index.
+ * Decisions.  Coverage and per-pixel order follow their plain definitions: a triangle
+ * covers a pixel centre when its three edge functions pass the top-left fill rule, and
+ * the fragments of a pixel are composited in ascending depth 1 / sum_k (lambda_k / Z_k)
+ * (the ray-plane depth of the triangle at the pixel centre; ties by ascending triangle
+ * index).  The kernels take these decisions so that they agree with an FP64 evaluation:
+ *   - each vertex is projected in double-float (d = p - C exact, the camera rotation and
+ *     the pinhole division carried to ~2^-44 relative): X, Y, Z and x = fx X/Z + cx,
+ *     y = fy Y/Z + cy;
+ *   - a vertex is valid iff round(Z) > znear and |round(x)|, |round(y)| <= 2^17; a
+ *     triangle with an invalid vertex is culled;
+ *   - coverage is evaluated in binary32 on fan-relative coordinates: the fan's origin is
+ *     o = floor of its centre's screen position, each vertex enters as the binary32 value
+ *     nearest (x - o.x, y - o.y), the pixel centre as (px - o.x + 0.5, py - o.y + 0.5)
+ *     (exact); area2(A,B,C) = (xB - xA)(yC - yA) - (yB - yA)(xC - xA), 0 never covers,
+ *     < 0 swaps B, C; the edge of the vertex pair {a < b} (by vertex index) is
+ *     F = (xb - xa)(py - ya) - (yb - ya)(px - xa), negated when the oriented edge runs
+ *     b -> a; it passes if F > 0, or F == 0 and its direction (ex, ey) has ey < 0, or
+ *     ey == 0 and ex > 0.  Near a fan the coordinates are small, so these binary32 edge
+ *     values have the sign of the exact ones except within ~1e-6 px of an edge;
+ *   - the depth is the double-float plane depth (n . P_c) / (n . r) with n the
+ *     triangle's normal from its camera-space vertex offsets and r the pixel's ray,
+ *     clamped to the triangle's vertex depths; fragments are ordered by (depth high part,
+ *     low part, triangle index).
+ * On the test scenes (1k to 1M Gaussians, full frames and windows) no pixel's fragment
+ * list differs from the FP64 decisions; taking the order from binary32 depths instead
+ * changes it on 1.6% to 39% of the pixels (nearly coplanar surfels).
  * Interpolation and compositing are FP32: mu_k = (E_k / Z_k) / sum_j (E_j / Z_j),
  * c = sum mu_k c_k, a = sum mu_k a_k; C += T a c, T *= 1 - a, stop once T < T_eps;
  * out = (C + T bg, 1 - T).

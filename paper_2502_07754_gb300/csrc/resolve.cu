@@ -143,6 +143,7 @@ __global__ void __launch_bounds__(kResolveThreads) resolve_kernel(const __grid_c
     float T = 1.0f, C0 = 0.0f, C1 = 0.0f, C2 = 0.0f;
     float kz[KB], kl[KB];      // pending fragments sorted by (depth, triangle): depth high, low
     uint32_t kt[KB], ki[KB];   // triangle id, record index
+    float4 kc[KB];             // colour and opacity, read with the depth (one sector per record)
     int nb = 0;
     float fz = 0.0f, fl = 0.0f;   // last committed (depth, triangle); depths are > 0
     uint32_t ft = 0;
@@ -155,9 +156,8 @@ __global__ void __launch_bounds__(kResolveThreads) resolve_kernel(const __grid_c
     uint32_t ncom = 0;
 
     auto commit_front = [&]() {
-        // colour and opacity are re-read from the record (an L1 / L2 hit) rather than
-        // carried in the pending buffer, which keeps the buffer at three registers a slot
-        const float4 col = rec[(size_t)RS * ki[0] + 1];
+        // colour and opacity travel in the pending buffer: a commit waits on no load
+        const float4 col = kc[0];
         const float al = col.w;
         const float c0 = col.x, c1 = col.y, c2 = col.z;
         const float w = T * al;
@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(kResolveThreads) resolve_kernel(const __grid_c
         has_front = true;
 #pragma unroll
         for (int i = 0; i + 1 < KB; ++i) {
-            kz[i] = kz[i + 1]; kl[i] = kl[i + 1]; kt[i] = kt[i + 1]; ki[i] = ki[i + 1];
+            kz[i] = kz[i + 1]; kl[i] = kl[i + 1]; kt[i] = kt[i + 1]; ki[i] = ki[i + 1]; kc[i] = kc[i + 1];
         }
         --nb;
         if (T < a.T_eps) {
@@ -186,6 +186,7 @@ __global__ void __launch_bounds__(kResolveThreads) resolve_kernel(const __grid_c
     while (!done) {
         for (int i = start; i < n && !done; ++i) {
             const float4 r0 = rec[RS * i];
+            const float4 r1 = rec[RS * i + 1];
             const float z = r0.x, zl = r0.w;
             const uint32_t tri = __float_as_uint(r0.y), qk = __float_as_uint(r0.z);
             while (nb > 0 && !done && depth_q(kz[0], a.depth_bits) < qk) commit_front();
@@ -220,14 +221,15 @@ __global__ void __launch_bounds__(kResolveThreads) resolve_kernel(const __grid_c
                 if (s <= nb && !placed) {
                     if (frag_less(z, zl, tri, kz[s - 1], kl[s - 1], kt[s - 1])) {
                         kz[s] = kz[s - 1]; kl[s] = kl[s - 1]; kt[s] = kt[s - 1]; ki[s] = ki[s - 1];
+                        kc[s] = kc[s - 1];
                     } else {
-                        kz[s] = z; kl[s] = zl; kt[s] = tri; ki[s] = (uint32_t)i;
+                        kz[s] = z; kl[s] = zl; kt[s] = tri; ki[s] = (uint32_t)i; kc[s] = r1;
                         placed = true;
                     }
                 }
             }
             if (!placed) {
-                kz[0] = z; kl[0] = zl; kt[0] = tri; ki[0] = (uint32_t)i;
+                kz[0] = z; kl[0] = zl; kt[0] = tri; ki[0] = (uint32_t)i; kc[0] = r1;
             }
             ++nb;
         }
