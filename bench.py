@@ -74,6 +74,8 @@ def parse():
     p.add_argument("--pairs-per-scene", type=int, default=125_000, help="training pairs kept per pair scene")
     p.add_argument("--finetune-steps", type=int, default=150)
     p.add_argument("--mlp-steps", type=int, default=400)
+    p.add_argument("--initializer-only", action="store_true",
+                   help="time the initializer's inference alone and fused into the conversion (profiling case)")
     return p.parse_args()
 
 
@@ -976,8 +978,59 @@ def run_batch(args, ws, rank, local):
     print(json.dumps(line), flush=True)
 
 
+def run_initializer_only(args):
+    """The learned initializer's inference on one Gaussian set of the workload's generator:
+    ms_mlp_forward (corrections to HBM), the conversion reading them, and the two fused
+    (ms_mesh_build_mlp); untrained weights (the same work).  One JSON line."""
+    import numpy as np
+    import torch
+    import synthetic
+    import paper_2502_07754_gb300 as ms
+    w = synthetic.workload(5, n=args.gaussians or None)
+    sc, K = w.scene, w.K
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    G = [dev(sc.means), dev(sc.log_scales), dev(sc.quats), dev(sc.opacity),
+         dev(sc.sh.view(np.int16) if sc.sh_bf16 else sc.sh)]
+    centre = w.cameras[0].C
+    net = ms.FanMLP(K=K, seed=1)
+    corr = torch.empty(sc.n, 2 * (K + 1), device="cuda")
+    out = tuple(torch.empty(sc.n * (K + 1), 3, device="cuda") for _ in range(2)) + \
+        (torch.empty(sc.n * (K + 1), device="cuda"),)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    fwd = lambda: net.forward(G[1], G[2], G[3], G[4], sc.sh_degree, out=corr)
+    conv = lambda: ms.mesh_build(*G, sc.sh_degree, K=K, cam_center=centre, corr=corr, out=out)
+    fused = lambda: ms.mesh_build(*G, sc.sh_degree, K=K, cam_center=centre, mlp=net, out=out)
+    for _ in range(args.warmup):
+        fwd(), conv(), fused()
+    t_fwd = timed(fwd, args.steps, flush, stream)
+    t_conv = timed(conv, args.steps, flush, stream)
+    t_fused = timed(fused, args.steps, flush, stream)
+    st, timeouts = net.status()
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    tc_peak = float(peaks.get("bf16_tflops", 1900.0))
+    tf = sc.n * MLP_FLOPS_PER_ROW / (t_fused * 1e-3) / 1e12
+    line = {"metric": "initializer inference fused into the conversion", "value": sc.n / (t_fused * 1e-3) / 1e6,
+            "unit": "M Gaussians/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t_fused, "higher_is_better": True, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": w.name, "gaussians": sc.n, "K": K, "l2": "flushed before every timed call"},
+            "mlp_forward_ms": t_fwd, "conversion_with_corrections_ms": t_conv, "fused_ms": t_fused,
+            "roofline": {"kernel": "mlp_fwd (fused)", "bound": "tensor", "achieved": tf, "peak": tc_peak,
+                         "unit": "TFLOP/s", "frac": tf / tc_peak},
+            "forward_only_tflops": sc.n * MLP_FLOPS_PER_ROW / (t_fwd * 1e-3) / 1e12,
+            "tensor_core_timeouts": timeouts}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
+    if args.initializer_only:
+        run_initializer_only(args)
+        return
     ws, rank, local = (1, 0, 0)
     if args.impl == "reference":
         ws = int(os.environ.get("WORLD_SIZE", "1"))

@@ -103,11 +103,11 @@ RenderLayout render_layout(int64_t n_fans, int K, const ms_camera *cams, int n_v
     L.tile_bits = bits_for(L.n_tiles);
     // A sort element is one 64-bit word: tile | quantised depth bound | fan id, the fan id in
     // the low fan_bits bits; the radix passes sort the tile and depth bits above them.
-    // Automatic depth bits: as many as fit (<= 27) without a further byte of sort key beyond
-    // tile bits + 20, and within the word.
+    // Automatic depth bits: at least 12 over the view's depth range, and as many more as fill
+    // the sort key's last byte, within the word.
     L.fan_bits = bits_for(n_fans);
     L.depth_bits = p.depth_bits ? p.depth_bits
-                                : std::min(std::min(27, 8 * ((L.tile_bits + 20 + 7) / 8) - L.tile_bits),
+                                : std::min(std::min(31, 8 * ((L.tile_bits + 12 + 7) / 8) - L.tile_bits),
                                            64 - L.fan_bits - L.tile_bits);
     L.key_bits = L.tile_bits + L.depth_bits;
     L.passes = (L.key_bits + 7) / 8;
@@ -139,6 +139,7 @@ RenderLayout render_layout(int64_t n_fans, int K, const ms_camera *cams, int n_v
     L.off_scan_state = o;        o = align_up(o + 8 * (size_t)L.scan_blocks, 256);
     L.off_tscan_state = o;       o = align_up(o + 8 * (size_t)L.tscan_blocks, 256);
     L.off_pbucket = o;           o = align_up(o + 2 * 256 * 4, 256);   // pixel-count histogram, fill cursors
+    L.off_zrange = o;            o = align_up(o + 8 * (size_t)n_views, 256);   // per view: ~bits(zlo), bits(zhi)
     L.off_keys0 = o;             o = align_up(o + 8 * (size_t)cap, 256);   // (zeroed prefix ends here)
     L.off_keys1 = o;             o = align_up(o + 8 * (size_t)cap, 256);
     L.off_tile_nitems = o;       o = align_up(o + 4 * (size_t)L.n_tiles, 256);

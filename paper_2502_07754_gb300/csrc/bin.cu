@@ -29,7 +29,59 @@ struct BinArgs {
     float4 *dec;               // [view][vertex] decided (xr, yr, Z or -1, origin), read by the raster passes
     int64_t V;
     const uint32_t *face_mask; // per fan, bit j = face j drawn; NULL = all
+    const uint32_t *zrange;    // per view: ~bits(zlo), bits(zhi) of the depth pre-pass
 };
+
+// Depth range of each view for the keys' quantisation (depth_quant): the view depths of the
+// fan centres in front of the near plane and inside a frustum twice the image's width and
+// height, widened by 1/32 on each side for the fans' extent.  Only the keys' resolution
+// depends on it (depths outside clamp, which keeps every key a lower bound); eight views
+// per sweep over the centres, one atomic per block and bound.
+constexpr int kRangeThreads = 256, kRangeViews = 8;
+__global__ void __launch_bounds__(kRangeThreads) depth_range_kernel(const float *__restrict__ xyz, int64_t n_fans,
+                                                                    int K, const __grid_constant__ ViewTable vt,
+                                                                    int v0, int nv, uint32_t *__restrict__ zr) {
+    uint32_t lo_inv[kRangeViews], hi[kRangeViews];
+#pragma unroll
+    for (int v = 0; v < kRangeViews; ++v) lo_inv[v] = hi[v] = 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n_fans; g += stride) {
+        const float *p = xyz + g * (int64_t)(K + 1) * 3;
+        const float px = __ldg(p), py = __ldg(p + 1), pz = __ldg(p + 2);
+#pragma unroll
+        for (int v = 0; v < kRangeViews; ++v) {
+            if (v >= nv) break;
+            const CamDev &c = vt.v[v0 + v].cam;
+            const float dx = px - c.C[0], dy = py - c.C[1], dz = pz - c.C[2];
+            const float z = fmaf(c.R[6], dx, fmaf(c.R[7], dy, c.R[8] * dz));
+            if (!(z > c.znear)) continue;
+            const float x = fmaf(c.R[0], dx, fmaf(c.R[1], dy, c.R[2] * dz));
+            const float y = fmaf(c.R[3], dx, fmaf(c.R[4], dy, c.R[5] * dz));
+            const float xs = fmaf(c.fx, x, c.cx * z), ys = fmaf(c.fy, y, c.cy * z);   // screen x, y times z
+            const float W = (float)c.width, H = (float)c.height;
+            if (xs < -W * z || xs > 2.0f * W * z || ys < -H * z || ys > 2.0f * H * z) continue;
+            lo_inv[v] = max(lo_inv[v], ~__float_as_uint(z * (1.0f - 1.0f / 32.0f)));
+            hi[v] = max(hi[v], __float_as_uint(z * (1.0f + 1.0f / 32.0f)));
+        }
+    }
+    // warp, then block reduction: one atomic per block and bound (a few hundred in all)
+    __shared__ uint32_t s_r[kRangeThreads / 32][2 * kRangeViews];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int v = 0; v < kRangeViews; ++v) {
+        const uint32_t l = __reduce_max_sync(0xffffffffu, lo_inv[v]), h = __reduce_max_sync(0xffffffffu, hi[v]);
+        if (lane == 0) {
+            s_r[warp][2 * v] = l;
+            s_r[warp][2 * v + 1] = h;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 2 * nv) {
+        uint32_t m = 0;
+        for (int w = 0; w < kRangeThreads / 32; ++w) m = max(m, s_r[w][threadIdx.x]);
+        if (m) atomicMax(zr + 2 * v0 + threadIdx.x, m);
+    }
+}
 
 // Blocks take virtual ids in start order; id = view * fan_blocks + fan block, so pairs
 // come out view by view and, within a view, in fan order.
@@ -59,6 +111,7 @@ __global__ void __launch_bounds__(kBinThreads) bin_kernel(const __grid_constant_
     const int nloc = (int)min64(kBinThreads, n_fans - f0);
     const CamDev &cam = a.vt.v[view].cam;
     const unsigned tiles_x = a.vt.v[view].tiles_x, tile_base = a.vt.v[view].tile_base;
+    const DepthQ dq = depth_quant(a.zrange, view, depth_bits);
 
     // Coalesced staging of the block's vertices.
     {
@@ -121,7 +174,7 @@ __global__ void __launch_bounds__(kBinThreads) bin_kernel(const __grid_constant_
                 s_rect[tid][1] = (uint32_t)w | ((uint32_t)h << 16);
                 // a lower bound of every fragment depth of the fan: the smallest rounded
                 // vertex depth, lowered by 2^-20 to cover its rounding
-                s_q[tid] = depth_q(zmin * (a.key_scale * kKeyMargin), depth_bits);
+                s_q[tid] = depth_qv(dq, zmin * (a.key_scale * kKeyMargin));
             }
         }
     }
@@ -209,6 +262,16 @@ cudaError_t launch_bin(const RenderArgs &ra, cudaStream_t st) {
     a.dec = reinterpret_cast<float4 *>(ra.ws + L.off_dec);
     a.V = L.V;
     a.face_mask = ra.splat ? nullptr : ra.prm.face_mask;
+    a.zrange = reinterpret_cast<const uint32_t *>(ra.ws + L.off_zrange);   // zeroed with the workspace prefix
+    {
+        // about one centre per thread: the sweep is latency-bound, not bandwidth-bound
+        const int grid = (int)min64((ra.n_fans + kRangeThreads - 1) / kRangeThreads, 16 * 152);
+        for (int v0 = 0; v0 < L.n_views; v0 += kRangeViews)
+            depth_range_kernel<<<grid, kRangeThreads, 0, st>>>(ra.xyz, ra.n_fans, ra.K, ra.vt, v0,
+                                                               min(kRangeViews, L.n_views - v0),
+                                                               reinterpret_cast<uint32_t *>(ra.ws + L.off_zrange));
+        count_launches((L.n_views + kRangeViews - 1) / kRangeViews);
+    }
     bin_kernel<<<(unsigned)L.bin_blocks, kBinThreads, smem, st>>>(a);
     return cudaGetLastError();
 }

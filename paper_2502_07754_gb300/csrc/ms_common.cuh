@@ -180,10 +180,35 @@ __device__ __forceinline__ bool edge_pass(float E, float ex, float ey) {
     return E > 0.0f || (E == 0.0f && (ey < 0.0f || (ey == 0.0f && ex > 0.0f)));
 }
 
-// Quantised depth used in sort keys and in the commit test: the top `bits` bits of
-// the (positive) binary32 pattern; monotone non-decreasing in z.
-__device__ __forceinline__ uint32_t depth_q(float z, int bits) {
-    return __float_as_uint(z) >> (31 - bits);
+// Quantised depth used in sort keys and in the commit test.  A view's vertex depths span
+// [zlo, zhi] (a pre-pass over the vertices); the key is the offset of the binary32 pattern
+// of z from that of zlo (lowered by a margin), shifted right so that the span fits `bits`
+// bits, clamped to [0, 2^bits - 1].  Positive binary32 patterns order like their values,
+// so the map is monotone non-decreasing in z; it spends the bits on the view's depth range
+// instead of on the whole exponent range.  zr[2 v] holds the complement of zlo's pattern
+// (maximised atomically), zr[2 v + 1] zhi's pattern.
+struct DepthQ {
+    uint32_t base, shift, qmax;
+};
+__device__ __forceinline__ DepthQ depth_quant(const uint32_t *zr, int view, int bits) {
+    const uint32_t lo = ~zr[2 * view], hi = zr[2 * view + 1];
+    DepthQ d;
+    d.qmax = (1u << bits) - 1u;
+    if (hi < lo) {   // no vertex in front of the view: any monotone map
+        d.base = 0;
+        d.shift = 31u - (uint32_t)bits;
+        return d;
+    }
+    constexpr uint32_t kMargin = 256;   // ulps below zlo / above zhi (keys sit 2^-20 below)
+    d.base = lo > kMargin ? lo - kMargin : 0u;
+    const uint32_t span = (hi + kMargin) - d.base;
+    const int need = 32 - __clz(span);   // bits of the span
+    d.shift = (uint32_t)max(0, need - bits);
+    return d;
+}
+__device__ __forceinline__ uint32_t depth_qv(const DepthQ &d, float z) {
+    const uint32_t b = __float_as_uint(z);
+    return b <= d.base ? 0u : min((b - d.base) >> d.shift, d.qmax);
 }
 
 // ---------------------------------------------------------------------------------

@@ -49,6 +49,7 @@ struct ResolveArgs {
                                // pixel's record range: (dL/dc * T a, dL/da), (triangle, pixel, 0, 0)
     uint32_t *corder;          // per pixel: record indices in commit order (same offsets as records)
     const uint32_t *perm;      // visiting order of the pixels
+    const uint32_t *zrange;    // per view depth range of the keys' quantisation (bin.cu)
     ViewTable vt;
 };
 
@@ -132,11 +133,13 @@ __global__ void __launch_bounds__(kResolveThreads) resolve_kernel(const __grid_c
     const int64_t pt = t < a.npx ? (int64_t)a.perm[t] : a.npx;
     const bool valid = pt < a.npx;
     const int64_t pix = valid ? pt : 0;
-    const ViewDev &vw = a.vt.v[view_of_pixel(a.vt, (unsigned long long)pix)];
+    const int view = view_of_pixel(a.vt, (unsigned long long)pix);
+    const ViewDev &vw = a.vt.v[view];
     const int64_t lpix = pix - (int64_t)vw.pix_base;   // index within the view's image
     int n = valid ? (int)a.counts[pix] : 0;
     const int64_t off = a.offsets[pix];
     if (off + n > a.frag_cap) n = 0;   // the buffer overflowed: reported through the status block
+    const DepthQ dq = depth_quant(a.zrange, view, a.depth_bits);
     constexpr int RS = kRecFwd;   // float4s per record
     float4 *rec = a.frags + (size_t)RS * off;
 
@@ -189,7 +192,7 @@ __global__ void __launch_bounds__(kResolveThreads) resolve_kernel(const __grid_c
             const float4 r1 = rec[RS * i + 1];
             const float z = r0.x, zl = r0.w;
             const uint32_t tri = __float_as_uint(r0.y), qk = __float_as_uint(r0.z);
-            while (nb > 0 && !done && depth_q(kz[0], a.depth_bits) < qk) commit_front();
+            while (nb > 0 && !done && depth_qv(dq, kz[0]) < qk) commit_front();
             if (done) break;
             if (has_front && !frag_less(fz, fl, ft, z, zl, tri)) continue;   // committed in an earlier pass
             if (dropped && !frag_less(z, zl, tri, dz, dl, dt)) {
@@ -337,6 +340,7 @@ cudaError_t launch_resolve(const RenderArgs &ra, bool backward, cudaStream_t st)
     a.frags = reinterpret_cast<float4 *>(ra.ws + L.off_frags);
     a.frag_cap = L.frag_cap;
     a.depth_bits = L.depth_bits;
+    a.zrange = reinterpret_cast<const uint32_t *>(ra.ws + L.off_zrange);
     a.T_eps = ra.prm.T_eps;
     a.bg0 = ra.prm.bg[0];
     a.bg1 = ra.prm.bg[1];
