@@ -140,12 +140,19 @@ RenderLayout render_layout(int64_t n_fans, int K, const ms_camera *cams, int n_v
     L.off_tscan_state = o;       o = align_up(o + 8 * (size_t)L.tscan_blocks, 256);
     L.off_pbucket = o;           o = align_up(o + 2 * 256 * 4, 256);   // pixel-count histogram, fill cursors
     L.off_zrange = o;            o = align_up(o + 8 * (size_t)n_views, 256);   // per view: ~bits(zlo), bits(zhi)
+    L.off_mask_cursor = o;       o = align_up(o + 4 * (size_t)kMaskRegions, 256);
     L.off_keys0 = o;             o = align_up(o + 8 * (size_t)cap, 256);   // (zeroed prefix ends here)
     L.off_keys1 = o;             o = align_up(o + 8 * (size_t)cap, 256);
     L.off_tile_nitems = o;       o = align_up(o + 4 * (size_t)L.n_tiles, 256);
     L.off_tile_ibase = o;        o = align_up(o + 4 * (size_t)L.n_tiles, 256);
     L.off_items = o;             o = align_up(o + 16 * (size_t)L.max_items, 256);
     L.off_icnt = o;              o = align_up(o + 4 * (size_t)L.max_items * p.tile * p.tile, 256);
+    // coverage masks of the count pass (2 bytes per (pixel, fan) test) and each pair's first
+    // mask, so that the fill pass reads its coverage instead of testing it again; tests
+    // beyond the capacity fall back to testing
+    L.mask_cap = std::min<int64_t>(16 * npx + 65536, 0xfffffffell);
+    L.off_maskoff = o;           o = align_up(o + 4 * (size_t)cap, 256);
+    L.off_masks = o;             o = align_up(o + 2 * (size_t)L.mask_cap, 256);
     L.off_counts = o;            o = align_up(o + 4 * (size_t)npx, 256);
     L.off_offsets = o;           o = align_up(o + 4 * (size_t)npx, 256);
     L.off_perm = o;              o = align_up(o + 8 * (size_t)npx, 256);   // forward, backward pixel orders

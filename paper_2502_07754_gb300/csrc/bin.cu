@@ -32,12 +32,13 @@ struct BinArgs {
     const uint32_t *zrange;    // per view: ~bits(zlo), bits(zhi) of the depth pre-pass
 };
 
-// Depth range of each view for the keys' quantisation (depth_quant): the view depths of the
-// fan centres in front of the near plane and inside a frustum twice the image's width and
-// height, widened by 1/32 on each side for the fans' extent.  Only the keys' resolution
+// Depth range of each view for the keys' quantisation (depth_quant): the view depths of
+// every kRangeStride-th fan centre in front of the near plane and inside a frustum twice the
+// image's width and height, widened by 1/32 on each side for the fans' extent (each centre
+// is a sector of its own, so a sample keeps the sweep short).  Only the keys' resolution
 // depends on it (depths outside clamp, which keeps every key a lower bound); eight views
 // per sweep over the centres, one atomic per block and bound.
-constexpr int kRangeThreads = 256, kRangeViews = 8;
+constexpr int kRangeThreads = 256, kRangeViews = 8, kRangeStride = 8;
 __global__ void __launch_bounds__(kRangeThreads) depth_range_kernel(const float *__restrict__ xyz, int64_t n_fans,
                                                                     int K, const __grid_constant__ ViewTable vt,
                                                                     int v0, int nv, uint32_t *__restrict__ zr) {
@@ -45,7 +46,8 @@ __global__ void __launch_bounds__(kRangeThreads) depth_range_kernel(const float 
 #pragma unroll
     for (int v = 0; v < kRangeViews; ++v) lo_inv[v] = hi[v] = 0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n_fans; g += stride) {
+    for (int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * kRangeStride; g < n_fans;
+         g += stride * kRangeStride) {
         const float *p = xyz + g * (int64_t)(K + 1) * 3;
         const float px = __ldg(p), py = __ldg(p + 1), pz = __ldg(p + 2);
 #pragma unroll
@@ -265,7 +267,8 @@ cudaError_t launch_bin(const RenderArgs &ra, cudaStream_t st) {
     a.zrange = reinterpret_cast<const uint32_t *>(ra.ws + L.off_zrange);   // zeroed with the workspace prefix
     {
         // about one centre per thread: the sweep is latency-bound, not bandwidth-bound
-        const int grid = (int)min64((ra.n_fans + kRangeThreads - 1) / kRangeThreads, 16 * 152);
+        const int64_t samples = (ra.n_fans + kRangeStride - 1) / kRangeStride;
+        const int grid = (int)min64((samples + kRangeThreads - 1) / kRangeThreads, 16 * 152);
         for (int v0 = 0; v0 < L.n_views; v0 += kRangeViews)
             depth_range_kernel<<<grid, kRangeThreads, 0, st>>>(ra.xyz, ra.n_fans, ra.K, ra.vt, v0,
                                                                min(kRangeViews, L.n_views - v0),

@@ -42,6 +42,8 @@ struct Status {
     unsigned int n_items;            // raster work items (<= 64 fans of one tile each)
     unsigned long long items_total;  // work items the tile scan counted
 };
+// The count pass's coverage masks live in this many equal regions, each with its own cursor.
+constexpr int kMaskRegions = 256;
 static_assert(sizeof(Status) <= 256, "status block");
 
 struct CamDev {

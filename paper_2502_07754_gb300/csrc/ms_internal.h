@@ -33,11 +33,11 @@ struct RenderLayout {
     int fan_bits;              // low bits of a sort element holding the fan id
     int tiles_x[kMaxViews], tile_base[kMaxViews];
     int64_t pix_base[kMaxViews];
-    int64_t npx, n_fans, V, cap, frag_cap;
+    int64_t npx, n_fans, V, cap, frag_cap, mask_cap;
     int64_t bin_fan_blocks, bin_blocks, sort_blocks, scan_blocks, tscan_blocks, max_items;
     size_t off_status, off_bin_state, off_keys0, off_keys1, off_hist, off_lookback,
-        off_ranges, off_scan_state, off_tscan_state, off_pbucket, off_zrange, off_perm, off_tile_nitems, off_tile_ibase, off_items, off_icnt,
-        off_counts, off_offsets, off_frags, off_adj, off_corder, off_tfinal, off_ncommit, off_grad, off_dec, total;
+        off_ranges, off_scan_state, off_tscan_state, off_pbucket, off_zrange, off_mask_cursor, off_perm, off_tile_nitems, off_tile_ibase, off_items, off_icnt,
+        off_counts, off_offsets, off_maskoff, off_masks, off_frags, off_adj, off_corder, off_tfinal, off_ncommit, off_grad, off_dec, total;
 };
 
 RenderLayout render_layout(int64_t n_fans, int K, const ms_camera *cams, int n_views, const ms_render_params &p);

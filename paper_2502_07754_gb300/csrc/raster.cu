@@ -8,10 +8,11 @@
 // of the fan's pixel rectangle inside the tile and test the fan's K triangles at each
 // with the binary32 decision formulas.  No block barriers are used.
 //
-// Count pass: per (item, pixel) fragment counts.  A per-tile prefix over the tile's
-// items turns them into each item's starting slot within the pixel and gives the
-// pixel totals; an exclusive scan over pixels gives record offsets.  Fill pass: the
-// same walk writes one 32-byte record per fragment at offset + item slot + running
+// Count pass: per (item, pixel) fragment counts, and the coverage mask of every (fan,
+// pixel) test.  A per-tile prefix over the tile's items turns the counts into each item's
+// starting slot within the pixel and gives the pixel totals; an exclusive scan over pixels
+// gives record offsets.  Fill pass: the same walk, reading the stored masks instead of
+// testing again, writes one 32-byte record per fragment at offset + item slot + running
 // index -- depth (high), triangle id, the fan's depth bound, depth (low), colour, opacity -- so a
 // pixel's records come out in tile-list order, which the resolve relies on.
 #include "raster_common.cuh"
@@ -36,6 +37,10 @@ struct RastArgs {
     const float4 *dec;         // [view][vertex] decided vertices from binning
     int64_t V;
     const uint32_t *face_mask; // per fan, bit j = face j drawn; NULL = all
+    uint32_t *maskoff;         // per pair: index of its first coverage mask, ~0 if none stored
+    uint16_t *masks;           // coverage masks (bit j: triangle j) of the count pass's tests
+    int64_t mask_cap;
+    uint32_t *mask_cursor;     // [kMaskRegions] fill levels of the mask regions (zeroed per render)
 };
 
 constexpr int kRastWarps = 2;   // warps (work items) per block: items differ widely in cost
@@ -141,6 +146,23 @@ __global__ void __launch_bounds__(kRastWarps * 32) raster_kernel(const __grid_co
         }
         const int excl = incl - my_n;
         const int total = __shfl_sync(0xffffffffu, incl, 31);
+        // The count pass stores the coverage mask of every test of the chunk (one range per
+        // chunk, reserved with one atomic) and each pair's first index; the fill pass reads
+        // them instead of testing again.  Both walk a fan's rectangle in the same order.
+        uint32_t mbase = ~0u, my_moff = ~0u;
+        if (MODE == kCount) {
+            // kMaskRegions cursors, the item picking one by its index, so that the reservations
+            // of millions of chunks do not queue on one address
+            if (lane == 0 && total > 0) {
+                const uint32_t reg = item % kMaskRegions;
+                const uint32_t rsz = (uint32_t)(a.mask_cap / kMaskRegions);
+                const uint32_t b = atomicAdd(a.mask_cursor + reg, (uint32_t)total);
+                if ((uint64_t)b + (uint64_t)total <= (uint64_t)rsz) mbase = reg * rsz + b;
+            }
+            mbase = __shfl_sync(0xffffffffu, mbase, 0);
+            if (lane < cnt) a.maskoff[cb + lane] = mbase == ~0u ? ~0u : mbase + (uint32_t)excl;
+        }
+        if (MODE == kFill && lane < cnt) my_moff = __ldg(a.maskoff + cb + lane);
         for (int base = 0; base < total; base += 32) {
             const int idx = base + lane;
             int f = 0;   // first lane (fan) whose inclusive count exceeds idx
@@ -150,6 +172,7 @@ __global__ void __launch_bounds__(kRastWarps * 32) raster_kernel(const __grid_co
                 if (v <= idx) f += step;
             }
             const int fexcl = __shfl_sync(0xffffffffu, excl, f);
+            const uint32_t fmoff = __shfl_sync(0xffffffffu, my_moff, f);
             uint32_t hits = 0, flags = 0;
             int lp = -1, px = 0, py = 0;
             float sp_t = 0.0f, sp_a = 0.0f;
@@ -166,9 +189,12 @@ __global__ void __launch_bounds__(kRastWarps * 32) raster_kernel(const __grid_co
                 if (SPLAT)
                     hits = splat_hit(s_spl[f], *sc.cam, a.spl.trunc, (double)px + 0.5, (double)py + 0.5, sp_t, sp_a)
                                ? 1u : 0u;
+                else if (MODE == kFill && fmoff != ~0u)
+                    hits = __ldg(a.masks + fmoff + (uint32_t)local);
                 else   // decisions in the fan's relative frame (the origin is an integer)
                     hits = cover_mask<KT>(S, STG, K, f, flags, (float)(px - (int)S.ox[f]) + 0.5f,
                                           (float)(py - (int)S.oy[f]) + 0.5f);
+                if (MODE == kCount && mbase != ~0u) a.masks[mbase + (uint32_t)idx] = (uint16_t)hits;
                 if (hits) lp = (py - ty0) * TILE + (px - tx0);
             }
             const int nf = __popc(hits);
@@ -456,6 +482,10 @@ RastArgs make_args(const RenderArgs &ra) {
     a.dec = reinterpret_cast<const float4 *>(ra.ws + L.off_dec);
     a.V = L.V;
     a.face_mask = ra.prm.face_mask;
+    a.maskoff = reinterpret_cast<uint32_t *>(ra.ws + L.off_maskoff);
+    a.masks = reinterpret_cast<uint16_t *>(ra.ws + L.off_masks);
+    a.mask_cap = L.mask_cap;
+    a.mask_cursor = reinterpret_cast<uint32_t *>(ra.ws + L.off_mask_cursor);
     return a;
 }
 
