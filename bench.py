@@ -67,10 +67,12 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-autotune", action="store_true")
+    p.add_argument("--no-next-rows", action="store_true",
+                   help="skip the rows beyond the hot path (full-loss fine-tune, three-fan, mesh prior, ray tracing)")
     p.add_argument("--no-other-workloads", action="store_true",
                    help="skip the compact measurements of the other configurations")
-    p.add_argument("--tile", type=int, default=16, help="screen tile edge (single-view workloads)")
-    p.add_argument("--kbuf", type=int, default=8, help="per-pixel pending buffer (single-view workloads)")
+    p.add_argument("--tile", type=int, default=16, help="screen tile edge (single-view workloads; batch workloads with --no-autotune)")
+    p.add_argument("--kbuf", type=int, default=8, help="per-pixel pending buffer (single-view workloads; batch workloads with --no-autotune)")
     p.add_argument("--pairs-per-scene", type=int, default=125_000, help="training pairs kept per pair scene")
     p.add_argument("--finetune-steps", type=int, default=150)
     p.add_argument("--mlp-steps", type=int, default=400)
@@ -539,6 +541,203 @@ def other_workloads(flush, steps=10, warmup=3):
     return out
 
 
+def _scene_tensors(sc):
+    import torch
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    return [dev(sc.means), dev(sc.log_scales), dev(sc.quats), dev(sc.opacity),
+            dev(sc.sh.view(np.int16) if sc.sh_bf16 else sc.sh)]
+
+
+def row_full_fine_tune(flush, steps, warmup):
+    """Next-row f1: the fine-tuning of Sec. 3 with the full loss of Eq. 3 (0.6 L1 +
+    0.4 (1 - SSIM)) on the 1M-fan 1080p scene (FanFineTune: render, loss, adjoint, Adam),
+    and one per-face pruning step (ms_prune_faces) of that soup with its moments."""
+    import torch
+    import synthetic
+    import paper_2502_07754_gb300 as ms
+    from paper_2502_07754_gb300.finetune import FanFineTune
+    w = synthetic.workload(3)
+    sc, K, cam = w.scene, w.K, w.cameras[0]
+    G, tG = _scene_tensors(sc), _scene_tensors(w.target_scene)
+    target = ms.Renderer(sc.n, K, cam).forward(*ms.mesh_build(*tG, sc.sh_degree, K=K, cam_center=cam.C)).clone()
+    del tG
+    xyz, rgb, a = ms.mesh_build(*G, sc.sh_degree, K=K, cam_center=cam.C)
+    ft = FanFineTune(xyz, rgb, a, K, [cam], target.view(-1, 4), prune_every=0)
+    for _ in range(warmup):
+        ft.step()
+    stream = torch.cuda.current_stream()
+    t_step = timed(ft.step, steps, flush, stream)
+    opt = ft.adam
+    for _ in range(2):
+        ms.prune_faces(ft.xyz, ft.rgb, ft.alpha, K, m=opt.m, v=opt.v)
+    t_prune = timed(lambda: ms.prune_faces(ft.xyz, ft.rgb, ft.alpha, K, m=opt.m, v=opt.v), 3, flush, stream)
+    kept = ms.prune_faces(ft.xyz, ft.rgb, ft.alpha, K, m=opt.m, v=opt.v)[6]
+    W, H = cam.width, cam.height
+    return {"workload": w.name, "step": "render+(0.6 L1 + 0.4 (1 - SSIM))+adjoint+adam (FanFineTune)",
+            "value": mpix(W, H, t_step), "unit": "Mpix/s", "ms_per_step": t_step,
+            "prune_faces_ms": t_prune, "fans": sc.n, "fans_kept": int(kept),
+            "parity": "tests/test_gpu_finetune.py (the loop against the FP64 oracle loop)"}
+
+
+def row_three_fan(flush, steps, warmup):
+    """Next-row f2: the three-fan conversion of 3D Gaussians (ms_mesh_build_3d) and the
+    fine-tune step of the three-fan mesh (render 3N fans, L1, adjoint, copies' gradients
+    summed, Adam), on the 200k-Gaussian surface scene with the normal axis thickened to a
+    third of the in-plane scale, 800x800; image error of the render against the oracle."""
+    import torch
+    import synthetic
+    import paper_2502_07754_gb300 as ms
+    w = synthetic.workload(2)
+    sc, K, cam = w.scene, w.K, w.cameras[0]
+    ls = sc.log_scales.copy()
+    ls[:, 0] = ls[:, 1] - np.log(3.0)
+    sc = synthetic.Scene(sc.means, ls, sc.quats, sc.opacity, sc.sh, sc.sh_degree, sc.sh_bf16)
+    tg = synthetic.jittered(sc, 1e-3, 1302)
+    G, tG = _scene_tensors(sc), _scene_tensors(tg)
+    N = sc.n
+    rend = ms.Renderer(3 * N, K, cam)
+    target = rend.forward(*ms.mesh_build_3d(*tG, tg.sh_degree, K=K, cam_center=cam.C)).clone()
+    del tG
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        ms.mesh_build_3d(*G, sc.sh_degree, K=K, cam_center=cam.C)
+    t_conv = timed(lambda: ms.mesh_build_3d(*G, sc.sh_degree, K=K, cam_center=cam.C), steps, flush, stream)
+    xyz, rgb, a = ms.mesh_build_3d(*G, sc.sh_degree, K=K, cam_center=cam.C)
+    out = rend.forward(xyz, rgb, a).clone()
+    err = image_error(out.cpu().numpy(), (xyz.cpu().numpy(), rgb.cpu().numpy(), a.cpu().numpy()), K, cam,
+                      error_windows(cam.width, cam.height))
+    adam = ms.FanAdam(xyz, rgb, a)
+
+    def step():
+        rend.forward(xyz, rgb, a, out=out, check_status=False)
+        _, dL = ms.l1_loss(out, target)
+        rend.backward(xyz, rgb, a, out, dL, into_workspace=True)
+        ms.three_fan_sum_copies(N, K, renderer=rend)
+        adam.step_ws(xyz, rgb, a, rend)
+
+    for _ in range(warmup):
+        step()
+    t_step = timed(step, steps, flush, stream)
+    st, _ = rend.info()
+    from paper_2502_07754_gb300 import _lib
+    _lib.check(st)
+    nb = (sc.sh_degree + 1) ** 2 * 3 * 4
+    conv_bytes = N * (44 + nb) + 3 * N * (K + 1) * 28
+    W, H = cam.width, cam.height
+    return {"workload": "surfaces-200k-3D-three-fan-K8-800px", "gaussians": N, "fans": 3 * N, "K": K,
+            "conversion_ms": t_conv, "conversion_gbs": conv_bytes / (t_conv * 1e-3) / 1e9,
+            "conversion_bytes": conv_bytes, "value": mpix(W, H, t_step), "unit": "Mpix/s", "ms_per_step": t_step,
+            "step": "render+l1+adjoint+copies summed+adam", "image_error": err}
+
+
+def row_mesh_prior(flush, steps, warmup):
+    """Next-row f3: the mesh-prior mode on two tessellated spheres (S = 4 secondary
+    triangles per face, midpoint subdivision), 1920x1080: secondary triangles built as
+    centroid fans from the simplex weights, render, L1 against the same mesh with
+    perturbed colours, adjoint, fold of the fan gradients to the weights and attributes;
+    image error of the render against the oracle."""
+    import torch
+    import synthetic
+    import paper_2502_07754_gb300 as ms
+    V1, F1 = synthetic.sphere_mesh(160, 320, 0.8, (0.1, 0.0, 0.0), jitter=2e-4, seed=31)
+    V2, F2 = synthetic.sphere_mesh(100, 200, 0.4, (-0.4, 0.3, 0.6), jitter=2e-4, seed=32)
+    Vm = np.concatenate([V1, V2]).astype(np.float64)
+    Fm = np.concatenate([F1, F2 + len(V1)])
+    faces = Vm[Fm]                                    # F x 3 corners x 3
+    S = 4
+    wts = synthetic.mesh_prior_weights(faces.shape[0], S)   # midpoint subdivision of every face
+    rng = np.random.Generator(np.random.PCG64(33))
+    Fn = faces.shape[0]
+    rgb = rng.uniform(0.1, 0.9, (Fn, S, 3, 3))
+    alpha = rng.uniform(0.3, 0.9, (Fn, S, 3))
+    dev = lambda a_: torch.from_numpy(np.ascontiguousarray(a_, dtype=np.float32)).cuda()
+    Fd, Wd, Cd, Ad = dev(faces), dev(wts), dev(rgb), dev(alpha)
+    cam = synthetic.make_camera(np.array([0.9, 0.7, 2.6]), 1920, 1080)
+    rend = ms.Renderer(Fn * S, 3, cam)
+    tgt = rend.forward(*ms.mesh_prior_build(Fd, Wd, dev(np.clip(rgb + rng.normal(0, 0.05, rgb.shape), 0, 1)),
+                                            Ad)).clone()
+    fx, fc, fa = ms.mesh_prior_build(Fd, Wd, Cd, Ad)
+    out = rend.forward(fx, fc, fa).clone()
+    err = image_error(out.cpu().numpy(), (fx.cpu().numpy(), fc.cpu().numpy(), fa.cpu().numpy()), 3, cam,
+                      error_windows(cam.width, cam.height))
+    grads = (torch.zeros_like(Wd), torch.zeros_like(Cd), torch.zeros_like(Ad))
+
+    def step():
+        x, c, a_ = ms.mesh_prior_build(Fd, Wd, Cd, Ad)
+        rend.forward(x, c, a_, out=out, check_status=False)
+        _, dL = ms.l1_loss(out, tgt)
+        rend.backward(x, c, a_, out, dL, into_workspace=True)
+        for g_ in grads:
+            g_.zero_()
+        ms.mesh_prior_backward(Fd, Wd, renderer=rend, out=grads)
+
+    for _ in range(warmup):
+        step()
+    t_step = timed(step, steps, flush, torch.cuda.current_stream())
+    st, _ = rend.info()
+    from paper_2502_07754_gb300 import _lib
+    _lib.check(st)
+    return {"workload": "two-spheres-mesh-prior-S4-1080p", "faces": int(Fn), "secondary_triangles": int(Fn * S),
+            "value": mpix(1920, 1080, t_step), "unit": "Mpix/s", "ms_per_step": t_step,
+            "step": "prior build+render+l1+adjoint+fold to weights", "image_error": err}
+
+
+def row_ray_tracing(flush, steps, warmup):
+    """Next-row f4: ray tracing of the 200k-fan surface soup (1.6M triangles, 800x800):
+    linear BVH build, primary rays alone and with a point light's shadows; the primary image
+    against the FP64 oracle's rasterised composite (they differ only at pixel centres within
+    rounding of an edge)."""
+    import torch
+    import synthetic
+    import paper_2502_07754_gb300 as ms
+    w = synthetic.workload(2)
+    sc, K, cam = w.scene, w.K, w.cameras[0]
+    G = _scene_tensors(sc)
+    xyz, rgb, a = ms.mesh_build(*G, sc.sh_degree, K=K, cam_center=cam.C)
+    T = sc.n * K
+    rt = ms.RayTracer(T, K)
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        rt.build(xyz)
+    t_build = timed(lambda: rt.build(xyz), steps, flush, stream)
+    light = (2.5, 3.0, 3.5)
+    out = torch.empty(cam.height, cam.width, 4, device="cuda")
+    for _ in range(warmup):
+        rt.trace(xyz, rgb, a, cam, out=out, T_eps=1e-5)
+    t_prim = timed(lambda: rt.trace(xyz, rgb, a, cam, out=out, T_eps=1e-5), steps, flush, stream)
+    prim = out.clone()
+    t_shadow = timed(lambda: rt.trace(xyz, rgb, a, cam, light=light, ambient=0.3, out=out, T_eps=1e-5),
+                     max(steps // 2, 1), flush, stream)
+    st, ov = rt.status()
+    from paper_2502_07754_gb300 import _lib
+    _lib.check(st)
+    err = image_error(prim.cpu().numpy(), (xyz.cpu().numpy(), rgb.cpu().numpy(), a.cpu().numpy()), K, cam,
+                      error_windows(cam.width, cam.height, size=48))
+    W, H = cam.width, cam.height
+    return {"workload": w.name + "-raytraced", "triangles": T, "bvh_build_ms": t_build,
+            "primary_ms": t_prim, "primary_mpix_s": mpix(W, H, t_prim), "shadow_ms": t_shadow,
+            "value": mpix(W, H, t_shadow), "unit": "Mpix/s (primary + shadow rays)", "stack_overflows": ov,
+            "image_error_primary_vs_raster_oracle": err}
+
+
+def next_rows(flush, steps=10, warmup=3):
+    """The rows built beyond the hot path (full-loss fine-tune with pruning, three-fan
+    meshes, mesh prior, ray tracing), each timed on its own synthetic case."""
+    import torch
+    out = {}
+    for name, fn in (("f1_full_loss_fine_tune", row_full_fine_tune), ("f2_three_fan", row_three_fan),
+                     ("f3_mesh_prior", row_mesh_prior), ("f4_ray_tracing", row_ray_tracing)):
+        t0 = time.perf_counter()
+        try:
+            r = fn(flush, steps, warmup)
+        except Exception as e:   # reported, not hidden: the headline line stays valid
+            r = {"error": f"{type(e).__name__}: {e}"}
+        r["wall_s"] = round(time.perf_counter() - t0, 1)
+        out[name] = r
+        torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args, ws, rank, local):
     import torch
 
@@ -699,11 +898,14 @@ def run_ours(args, ws, rank, local):
         err = image_error(out.cpu().numpy(), (x.cpu().numpy(), c.cpu().numpy(), al.cpu().numpy()), K, cam,
                           [(912, 492, 1008, 588), (1500, 560, 1596, 656)] + error_windows(W, H)[2:]
                           if (W, H) == (1920, 1080) else error_windows(W, H, size=min(96, W, H)))
-    others = None
+    others = rows = None
     if not args.no_other_workloads and args.workload == 3 and not args.gaussians:
         del x, c, al
         torch.cuda.empty_cache()
         others = other_workloads(flush)
+    if not args.no_next_rows and args.workload == 3 and not args.gaussians:
+        torch.cuda.empty_cache()
+        rows = next_rows(flush)
 
     if rank != 0:
         return
@@ -724,6 +926,8 @@ def run_ours(args, ws, rank, local):
             "image_error": err}
     if others is not None:
         line["other_workloads"] = others
+    if rows is not None:
+        line["next_rows"] = rows
     if not args.no_cpu_baseline and ws == 1:
         line["cpu_baseline"] = cpu_baseline(w, K)
     print(json.dumps(line), flush=True)
@@ -840,7 +1044,9 @@ def run_batch(args, ws, rank, local):
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
     sh_host = sc.sh.view(np.int16) if sc.sh_bf16 else sc.sh
     G = [dev(sc.means), dev(sc.log_scales), dev(sc.quats), dev(sc.opacity), dev(sh_host)]
-    br = ms.BatchRenderer(sc.n, K, cams)
+    # without the autotuner the tile and pending buffer come from the command line
+    br = ms.BatchRenderer(sc.n, K, cams, ms.render_params(tile=args.tile, kbuf=args.kbuf)
+                          if args.no_autotune else None)
     npx = br.n_pixels
 
     net, init_report = None, None

@@ -344,3 +344,18 @@ def sphere_mesh(n_lat: int, n_lon: int, radius: float = 1.0, centre=(0.0, 0.0, 0
     for j in range(n_lon):
         faces.append((south, ring(n_lat - 1, j + 1), ring(n_lat - 1, j)))
     return V.astype(np.float32), np.asarray(faces, np.int32)
+
+
+def mesh_prior_weights(n_faces: int, n_sub: int, jitter: float = 0.0, seed: int = 0) -> np.ndarray:
+    """Weights w (F, n_sub, 3 vertices, 3 corners) of secondary triangles laid out on each
+    face: one triangle per face covering it (n_sub = 1), or its midpoint subdivision (four:
+    the three corner triangles, then the middle one).  Each entry is the square root of the
+    layout's barycentric coordinate, plus N(0, jitter) noise when jitter > 0."""
+    h = 0.5 ** 0.5
+    layouts = {1: [[[1, 0, 0], [0, 1, 0], [0, 0, 1]]],
+               4: [[[1, 0, 0], [h, h, 0], [h, 0, h]], [[h, h, 0], [0, 1, 0], [0, h, h]],
+                   [[h, 0, h], [0, h, h], [0, 0, 1]], [[h, h, 0], [0, h, h], [h, 0, h]]]}
+    w = np.broadcast_to(np.asarray(layouts[n_sub], np.float64), (n_faces, n_sub, 3, 3)).copy()
+    if jitter > 0:
+        w += np.random.Generator(np.random.PCG64(seed)).normal(0.0, jitter, w.shape)
+    return w
