@@ -151,7 +151,7 @@ RenderLayout render_layout(int64_t n_fans, int K, const ms_camera *cams, int n_v
     // mask, so that the fill pass reads its coverage instead of testing it again; tests
     // beyond the capacity fall back to testing
     L.mask_cap = std::min<int64_t>(16 * npx + 65536, 0xfffffffell);
-    L.off_maskoff = o;           o = align_up(o + 4 * (size_t)cap, 256);
+    L.off_maskoff = o;           o = align_up(o + 8 * (size_t)cap, 256);   // per pair: mask index, rectangle
     L.off_masks = o;             o = align_up(o + 2 * (size_t)L.mask_cap, 256);
     L.off_counts = o;            o = align_up(o + 4 * (size_t)npx, 256);
     L.off_offsets = o;           o = align_up(o + 4 * (size_t)npx, 256);

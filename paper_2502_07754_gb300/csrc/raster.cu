@@ -8,11 +8,12 @@
 // of the fan's pixel rectangle inside the tile and test the fan's K triangles at each
 // with the binary32 decision formulas.  No block barriers are used.
 //
-// Count pass: per (item, pixel) fragment counts, and the coverage mask of every (fan,
-// pixel) test.  A per-tile prefix over the tile's items turns the counts into each item's
-// starting slot within the pixel and gives the pixel totals; an exclusive scan over pixels
-// gives record offsets.  Fill pass: the same walk, reading the stored masks instead of
-// testing again, writes one 32-byte record per fragment at offset + item slot + running
+// Count pass: per (item, pixel) fragment counts, the coverage mask of every (fan, pixel)
+// test, and per pair its first mask index and its pixel rectangle within the tile.  A
+// per-tile prefix over the tile's items turns the counts into each item's starting slot
+// within the pixel and gives the pixel totals; an exclusive scan over pixels gives record
+// offsets.  Fill pass: the same walk, reading the stored masks and rectangles instead of
+// staging the decisions and testing again, writes one 32-byte record per fragment at offset + item slot + running
 // index -- depth (high), triangle id, the fan's depth bound, depth (low), colour, opacity -- so a
 // pixel's records come out in tile-list order, which the resolve relies on.
 #include "raster_common.cuh"
@@ -37,13 +38,20 @@ struct RastArgs {
     const float4 *dec;         // [view][vertex] decided vertices from binning
     int64_t V;
     const uint32_t *face_mask; // per fan, bit j = face j drawn; NULL = all
-    uint32_t *maskoff;         // per pair: index of its first coverage mask, ~0 if none stored
+    uint2 *pinfo;              // per pair: index of its first coverage mask (~0 if none stored), and its
+                               // pixel rectangle clipped to the tile (pair_geo; 0 if empty)
     uint16_t *masks;           // coverage masks (bit j: triangle j) of the count pass's tests
     int64_t mask_cap;
     uint32_t *mask_cursor;     // [kMaskRegions] fill levels of the mask regions (zeroed per render)
 };
 
 constexpr int kRastWarps = 2;   // warps (work items) per block: items differ widely in cost
+
+// A pair's pixel rectangle clipped to its tile, relative to the tile's corner: x0 | y0 << 6 |
+// (w - 1) << 12 | (h - 1) << 18, bit 31 set; 0 for a pair with no pixel to test.
+__device__ __forceinline__ uint32_t pair_geo(int rx0, int ry0, int w, int h) {
+    return 0x80000000u | (uint32_t)rx0 | (uint32_t)ry0 << 6 | (uint32_t)(w - 1) << 12 | (uint32_t)(h - 1) << 18;
+}
 
 // Pass kinds: count fragments; fill their 32-byte forward records.  The splat passes draw
 // the source Gaussians themselves (count, then 32-byte records) over the tile lists of
@@ -114,6 +122,11 @@ __global__ void __launch_bounds__(kRastWarps * 32) raster_kernel(const __grid_co
     __syncwarp();
     for (uint32_t cb = it.y; cb < it.z; cb += STG) {
         const int cnt = (int)min((uint32_t)STG, it.z - cb);
+        // The fill pass takes a chunk whose pairs all have their masks stored without the
+        // decision stage: the count pass left each pair's rectangle beside its mask index.
+        uint2 pinf = make_uint2(~0u, 0u);
+        if (MODE == kFill && lane < cnt) pinf = __ldg(a.pinfo + cb + lane);
+        const bool stored = MODE == kFill && __all_sync(0xffffffffu, lane >= cnt || pinf.x != ~0u);
         {
             constexpr int LPF = 32 / STG;   // lanes staging one fan
             const int slot = lane / LPF;
@@ -124,7 +137,7 @@ __global__ void __launch_bounds__(kRastWarps * 32) raster_kernel(const __grid_co
                 q = (uint32_t)((e >> a.fan_bits) & ((1ull << a.depth_bits) - 1ull));
                 fan = (uint32_t)(e & ((1ull << a.fan_bits) - 1ull));
             }
-            stage_fans<LPF>(sc, S, K, lane, slot < cnt, fan, q, LEVEL);
+            stage_fans<LPF>(sc, S, K, lane, slot < cnt, fan, q, LEVEL, !stored);
             if (SPLAT && lane < cnt)
                 s_spl[lane] = splat_setup(a.spl, *sc.cam,
                                           (uint32_t)(__ldg(a.keys + cb + lane) & ((1ull << a.fan_bits) - 1ull)));
@@ -133,11 +146,16 @@ __global__ void __launch_bounds__(kRastWarps * 32) raster_kernel(const __grid_co
         // The staged fans' rectangles (clipped to the tile) form one packed (fan, pixel)
         // index space, fan-major, so every lane tests a pixel even when fans are tiny.
         int my_n = 0;
-        if (lane < cnt) {
+        uint32_t my_geo = 0;
+        if (stored) {
+            my_geo = pinf.y;
+        } else if (lane < cnt) {
             const int4 r = S.rect[lane];
             const int rx0 = max(r.x, tx0), rx1 = min(r.y, tx1), ry0 = max(r.z, ty0), ry1 = min(r.w, ty1);
-            if (S.flags[lane] != 0 && rx0 <= rx1 && ry0 <= ry1) my_n = (rx1 - rx0 + 1) * (ry1 - ry0 + 1);
+            if (S.flags[lane] != 0 && rx0 <= rx1 && ry0 <= ry1)
+                my_geo = pair_geo(rx0 - tx0, ry0 - ty0, rx1 - rx0 + 1, ry1 - ry0 + 1);
         }
+        if (my_geo) my_n = (int)((((my_geo >> 12) & 63u) + 1u) * (((my_geo >> 18) & 63u) + 1u));
         int incl = my_n;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -160,9 +178,9 @@ __global__ void __launch_bounds__(kRastWarps * 32) raster_kernel(const __grid_co
                 if ((uint64_t)b + (uint64_t)total <= (uint64_t)rsz) mbase = reg * rsz + b;
             }
             mbase = __shfl_sync(0xffffffffu, mbase, 0);
-            if (lane < cnt) a.maskoff[cb + lane] = mbase == ~0u ? ~0u : mbase + (uint32_t)excl;
+            if (lane < cnt) a.pinfo[cb + lane] = make_uint2(mbase == ~0u ? ~0u : mbase + (uint32_t)excl, my_geo);
         }
-        if (MODE == kFill && lane < cnt) my_moff = __ldg(a.maskoff + cb + lane);
+        if (MODE == kFill) my_moff = pinf.x;
         for (int base = 0; base < total; base += 32) {
             const int idx = base + lane;
             int f = 0;   // first lane (fan) whose inclusive count exceeds idx
@@ -173,15 +191,14 @@ __global__ void __launch_bounds__(kRastWarps * 32) raster_kernel(const __grid_co
             }
             const int fexcl = __shfl_sync(0xffffffffu, excl, f);
             const uint32_t fmoff = __shfl_sync(0xffffffffu, my_moff, f);
+            const uint32_t fgeo = __shfl_sync(0xffffffffu, my_geo, f);
             uint32_t hits = 0, flags = 0;
             int lp = -1, px = 0, py = 0;
             float sp_t = 0.0f, sp_a = 0.0f;
             if (idx < total) {
                 ++c_rect;
-                flags = S.flags[f];
-                const int4 r = S.rect[f];
-                const int rx0 = max(r.x, tx0), rx1 = min(r.y, tx1), ry0 = max(r.z, ty0);
-                const int w = rx1 - rx0 + 1, local = idx - fexcl;
+                const int rx0 = tx0 + (int)(fgeo & 63u), ry0 = ty0 + (int)((fgeo >> 6) & 63u);
+                const int w = (int)((fgeo >> 12) & 63u) + 1, local = idx - fexcl;
                 // (local + 0.5) / w is at least 1/(2w) away from an integer: exact row
                 const int yy = (int)(((float)local + 0.5f) * (1.0f / (float)w));
                 px = rx0 + (local - yy * w);
@@ -191,9 +208,11 @@ __global__ void __launch_bounds__(kRastWarps * 32) raster_kernel(const __grid_co
                                ? 1u : 0u;
                 else if (MODE == kFill && fmoff != ~0u)
                     hits = __ldg(a.masks + fmoff + (uint32_t)local);
-                else   // decisions in the fan's relative frame (the origin is an integer)
+                else {   // decisions in the fan's relative frame (the origin is an integer)
+                    flags = S.flags[f];
                     hits = cover_mask<KT>(S, STG, K, f, flags, (float)(px - (int)S.ox[f]) + 0.5f,
                                           (float)(py - (int)S.oy[f]) + 0.5f);
+                }
                 if (MODE == kCount && mbase != ~0u) a.masks[mbase + (uint32_t)idx] = (uint16_t)hits;
                 if (hits) lp = (py - ty0) * TILE + (px - tx0);
             }
@@ -482,7 +501,7 @@ RastArgs make_args(const RenderArgs &ra) {
     a.dec = reinterpret_cast<const float4 *>(ra.ws + L.off_dec);
     a.V = L.V;
     a.face_mask = ra.prm.face_mask;
-    a.maskoff = reinterpret_cast<uint32_t *>(ra.ws + L.off_maskoff);
+    a.pinfo = reinterpret_cast<uint2 *>(ra.ws + L.off_maskoff);
     a.masks = reinterpret_cast<uint16_t *>(ra.ws + L.off_masks);
     a.mask_cap = L.mask_cap;
     a.mask_cursor = reinterpret_cast<uint32_t *>(ra.ws + L.off_mask_cursor);

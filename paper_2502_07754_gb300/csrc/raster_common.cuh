@@ -199,18 +199,15 @@ __device__ __forceinline__ float group_max(float x) {
     return x;
 }
 
-// Stages CH = 32 / LPF fans into slots 0..CH-1 with the whole warp: the LPF lanes of slot
-// lane / LPF share the fan's vertices, triangles and colours (every lane of the warp
-// calls this; a lane whose slot is not active does no loads or stores but takes part in
-// the shuffles).  The staged words are the same as one lane per fan would write.
+// The decision part of stage_fans: decided vertices, spoke and rim directions, areas,
+// tie bits, valid-triangle flags and the pixel rectangle of every slot.
 template <int LPF>
-__device__ __forceinline__ void stage_fans(const SceneDev &a, const Stage &s, int K, int lane, bool active,
-                                           uint32_t fan, uint32_t q, int level) {
+__device__ __forceinline__ void stage_decisions(const SceneDev &a, const Stage &s, int K, int slot, int sub,
+                                                bool active, uint32_t fan, uint32_t q) {
     constexpr int CH = 32 / LPF;
     const int KV = K + 1;
-    const int slot = lane / LPF, sub = lane % LPF;
-    const float *p = a.xyz + (size_t)fan * KV * 3;
     const float4 *dv = a.dec + (size_t)fan * KV;
+
     uint32_t vmask = 0;
     if (active)
         for (int k = sub; k < KV; k += LPF) {
@@ -279,7 +276,14 @@ __device__ __forceinline__ void stage_fans(const SceneDev &a, const Stage &s, in
         s.fan[slot] = fan;
         s.rect[slot] = make_int4(r.i0, r.i1, r.j0, r.j1);
     }
-    if (level < kStageValues || !active) return;
+}
+// The value part of stage_fans (fill passes): the double-float centre projection, the
+// boundary vertices' screen offsets and view offsets, 1 / depth, colours and opacities.
+template <int LPF>
+__device__ __forceinline__ void stage_values(const SceneDev &a, const Stage &s, int K, int slot, int sub, uint32_t fan,
+                                             const float *p) {
+    constexpr int CH = 32 / LPF;
+    const int KV = K + 1;
     const float m[3] = {__ldg(p), __ldg(p + 1), __ldg(p + 2)};
     const CentreProj cp = project_centre(*a.cam, m);
     const dfl zc = df_fast_two_sum(cp.Zh, cp.Zl);
@@ -326,6 +330,26 @@ __device__ __forceinline__ void stage_fans(const SceneDev &a, const Stage &s, in
     }
 }
 
+// Stages CH = 32 / LPF fans into slots 0..CH-1 with the whole warp: the LPF lanes of slot
+// lane / LPF share the fan's vertices, triangles and colours (every lane of the warp
+// calls this; a lane whose slot is not active does no loads or stores but takes part in
+// the shuffles).  The staged words are the same as one lane per fan would write.  With
+// `decide` false (warp-uniform) only the fan id, depth bound and the values are staged:
+// the caller already holds the fans' coverage masks and pixel rectangles.
+template <int LPF>
+__device__ __forceinline__ void stage_fans(const SceneDev &a, const Stage &s, int K, int lane, bool active,
+                                           uint32_t fan, uint32_t q, int level, bool decide = true) {
+    const int slot = lane / LPF, sub = lane % LPF;
+    const float *p = a.xyz + (size_t)fan * (K + 1) * 3;
+    if (decide)
+        stage_decisions<LPF>(a, s, K, slot, sub, active, fan, q);
+    else if (active && sub == 0) {
+        s.q[slot] = q;
+        s.fan[slot] = fan;
+    }
+    if (level < kStageValues || !active) return;
+    stage_values<LPF>(a, s, K, slot, sub, fan, p);
+}
 // Coverage of the pixel centre (pxc, pyc) by staged fan f: bit j is set when triangle j
 // covers it.  Each spoke value is computed once and turned into two pass bits (as the
 // edge c -> b_i and as its reverse; the top-left tie bit of each direction was staged),
