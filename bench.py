@@ -39,11 +39,10 @@ STAGES = ["mesh_build", "bin", "sort", "raster", "raster_bwd", "loss", "adam", "
 NSTAGE = len(STAGES)
 # ncu DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of a stage's
 # kernels on the 1M-fan 1080p workload, with the digest of the kernel sources it was taken
-# on; reported only while the digest still matches.  Taken on the 200k-Gaussian case of
-# the same generator (10.86M fragments: count 34 MB, tile prefix 9, pixel scan 8, pixel
-# order 8, fill 545, resolve 984) and scaled by fragments to 10.12M (the stage's traffic is
-# per fragment: records written and re-read).
-TRAFFIC = {"raster": {"bytes": 1.48e9, "digest": "1b710aacb3a4ab02"}}
+# on; reported only while the digest still matches.  Measured on that workload itself (one
+# pass per launch): work items 0.2 MB, count 254, tile prefix 24, pixel scan 8, pixel order
+# 8, fill 974, resolve 481.
+TRAFFIC = {"raster": {"bytes": 1.75e9, "digest": "7748d47ebf83aa9a"}}
 
 
 def kernel_digest():
@@ -59,7 +58,7 @@ def kernel_digest():
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--steps", type=int, default=300)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", type=int, default=3)
