@@ -291,7 +291,8 @@ MS_API ms_status ms_mesh_prior_backward(const float *faces, const float *w, cons
  * (C += T a c, T *= 1 - a; out = (C + T bg, 1 - T)), stopping once T < T_eps (0: never).
  * Shadows (light non-NULL and ambient < 1): a point light L; the fragment at p takes the
  * product S of (1 - a_g) over every other triangle g crossed by the segment p -> L at a
- * segment parameter in (1e-9, 1 - 1e-9), and its colour becomes c (ambient + (1 - ambient) S).
+ * segment parameter in (1e-9, 1 - 1e-9), and its colour becomes c (ambient + (1 - ambient) S);
+ * a shadow ray stops once S < T_eps (so the factor moves by at most (1 - ambient) T_eps).
  * Crossings are decided in FP64 (Moller-Trumbore, closed edges).
  *   Triangles: tris (device T x 3 int32) or, when NULL, the implicit fan topology of K
  *   triangles a fan (T = n_fans K); xyz, rgb (V x 3), alpha (V) device.

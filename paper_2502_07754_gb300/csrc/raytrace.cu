@@ -10,7 +10,7 @@
 //   * shadows: a point light L; a fragment at p gets the transmittance S, the product of
 //     (1 - a_g) over every other triangle g the segment p -> L crosses (parameter strictly
 //     inside (1e-9, 1 - 1e-9)), and its colour becomes c (k + (1 - k) S), k the ambient
-//     share.
+//     share; a shadow ray stops once S < T_eps, the primary composite's own bound.
 // Intersections are decided in FP64 (Moller-Trumbore, edges closed), values in FP64.
 //
 // Acceleration: a linear BVH (Karras 2012, "Maximizing parallelism in the construction of
@@ -25,7 +25,9 @@
 // Tracing gathers a ray's crossings in passes: each pass walks the BVH keeping the KB
 // nearest crossings beyond the last composited one (by (t, triangle)), composites them in
 // order, and repeats while some crossing was left out and the transmittance is above
-// T_eps.
+// T_eps.  A pass skips boxes that end before the last composited crossing and, once its
+// buffer is full, boxes that start beyond the farthest kept one; a binary32 filter
+// (mt_may_hit) keeps the FP64 test for triangles the ray may cross.
 #include "ms_common.cuh"
 #include "ms_internal.h"
 
@@ -279,6 +281,76 @@ __device__ __forceinline__ bool mt(const double o[3], const double d[3], const d
     return u >= 0.0 && v >= 0.0 && u + v <= 1.0;
 }
 
+// Binary32 filter of mt for a crossing parameter in [tmin, tmax]: false only when the
+// crossing certainly fails in exact arithmetic by a margin far above the FP64 test's own
+// rounding, so mt, run on what passes, decides exactly as without the filter.  Every
+// binary32 quantity q below carries an error of at most a few units of 2^-24 times S_q, the
+// same expression over the absolute values of its operands (with |a - b| bounded by
+// |a| + |b|, which also covers the rounding of o and d to binary32); the margins are 64
+// such units.  An undetermined sign of the determinant passes the triangle on to FP64.
+// FP64 arithmetic runs at a small fraction of the binary32 rate on this GPU, and most
+// boxes the traversal reaches hold triangles the ray misses.
+struct RayF {
+    float o[3], d[3], ao[3], ad[3];
+};
+__device__ __forceinline__ RayF ray_f(const double o[3], const double d[3]) {
+    RayF r;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        r.o[k] = (float)o[k];
+        r.d[k] = (float)d[k];
+        r.ao[k] = fabsf(r.o[k]);
+        r.ad[k] = fabsf(r.d[k]);
+    }
+    return r;
+}
+__device__ __forceinline__ bool mt_may_hit(const RayF &r, const float P0[3], const float P1[3], const float P2[3],
+                                           float tmin, float tmax) {
+    constexpr float kU = 64.0f * 0x1p-24f;
+    float e1[3], e2[3], tv[3], E1[3], E2[3], TV[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        e1[k] = P1[k] - P0[k];
+        e2[k] = P2[k] - P0[k];
+        tv[k] = r.o[k] - P0[k];
+        const float a0 = fabsf(P0[k]);
+        E1[k] = fabsf(P1[k]) + a0;
+        E2[k] = fabsf(P2[k]) + a0;
+        TV[k] = r.ao[k] + a0;
+    }
+    const float pv[3] = {r.d[1] * e2[2] - r.d[2] * e2[1], r.d[2] * e2[0] - r.d[0] * e2[2],
+                         r.d[0] * e2[1] - r.d[1] * e2[0]};
+    const float PV[3] = {r.ad[1] * E2[2] + r.ad[2] * E2[1], r.ad[2] * E2[0] + r.ad[0] * E2[2],
+                         r.ad[0] * E2[1] + r.ad[1] * E2[0]};
+    const float det = e1[0] * pv[0] + e1[1] * pv[1] + e1[2] * pv[2];
+    const float eDet = kU * (E1[0] * PV[0] + E1[1] * PV[1] + E1[2] * PV[2]);
+    if (!(fabsf(det) > eDet)) return true;
+    const float sg = det > 0.0f ? 1.0f : -1.0f;
+    const float U = tv[0] * pv[0] + tv[1] * pv[1] + tv[2] * pv[2];
+    const float eU = kU * (TV[0] * PV[0] + TV[1] * PV[1] + TV[2] * PV[2]);
+    if (sg * U < -eU) return false;
+    const float qv[3] = {tv[1] * e1[2] - tv[2] * e1[1], tv[2] * e1[0] - tv[0] * e1[2], tv[0] * e1[1] - tv[1] * e1[0]};
+    const float QV[3] = {TV[1] * E1[2] + TV[2] * E1[1], TV[2] * E1[0] + TV[0] * E1[2], TV[0] * E1[1] + TV[1] * E1[0]};
+    const float V = qv[0] * r.d[0] + qv[1] * r.d[1] + qv[2] * r.d[2];
+    const float eV = kU * (QV[0] * r.ad[0] + QV[1] * r.ad[1] + QV[2] * r.ad[2]);
+    if (sg * V < -eV) return false;
+    if (sg * (U + V - det) > eU + eV + eDet) return false;
+    const float Tn = e2[0] * qv[0] + e2[1] * qv[1] + e2[2] * qv[2];
+    const float eT = kU * (E2[0] * QV[0] + E2[1] * QV[1] + E2[2] * QV[2]);
+    const float t = Tn / det;
+    const float dt = (eT + fabsf(t) * eDet) / (fabsf(det) - eDet) + kU * fabsf(t);
+    return t + dt >= tmin && t - dt <= tmax;
+}
+
+__device__ __forceinline__ void tri_f(const TraceArgs &a, int tri, float P[3][3]) {
+    int64_t v[3];
+    tri_verts(a.tris, a.K, tri, v);
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int r = 0; r < 3; ++r) P[k][r] = __ldg(a.xyz + 3 * v[k] + r);
+}
+
 __device__ __forceinline__ void load_tri(const TraceArgs &a, int tri, int64_t v[3], double P[3][3]) {
     tri_verts(a.tris, a.K, tri, v);
 #pragma unroll
@@ -301,12 +373,30 @@ __device__ __forceinline__ bool box_hit(const BvhNode &nd, const float o[3], con
     return t0 <= t1;
 }
 
+// The same slab test returning the parameter interval [tn, tf] of the box (within t0, t1).
+__device__ __forceinline__ bool box_span(const BvhNode &nd, const float o[3], const float id[3], float t0, float t1,
+                                         float &tn, float &tf) {
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        float a = (nd.lo[r] - o[r]) * id[r], b = (nd.hi[r] - o[r]) * id[r];
+        if (a > b) { const float tmp = a; a = b; b = tmp; }
+        if (!(a == a)) a = -3.0e38f;   // 0 * inf
+        if (!(b == b)) b = 3.0e38f;
+        t0 = fmaxf(t0, a);
+        t1 = fminf(t1, b);
+    }
+    tn = t0;
+    tf = t1;
+    return t0 <= t1;
+}
+
 __device__ __forceinline__ bool hit_less(double ta, int ia, double tb, int ib) { return ta < tb || (ta == tb && ia < ib); }
 
 // Transmittance of the segment p -> L through every triangle but `own`.
 __device__ double shadow(const TraceArgs &a, const double p[3], int own) {
     const double d[3] = {a.L[0] - p[0], a.L[1] - p[1], a.L[2] - p[2]};
     const float of[3] = {(float)p[0], (float)p[1], (float)p[2]};
+    const RayF rf = ray_f(p, d);
     float id[3];
 #pragma unroll
     for (int r = 0; r < 3; ++r) id[r] = 1.0f / (float)d[r];
@@ -322,6 +412,11 @@ __device__ double shadow(const TraceArgs &a, const double p[3], int own) {
         if (node >= n - 1) {
             const int tri = a.leaf_tri[node - (n - 1)];
             if (tri == own) continue;
+            {
+                float Pf[3][3];
+                tri_f(a, tri, Pf);
+                if (!mt_may_hit(rf, Pf[0], Pf[1], Pf[2], (float)kSegEps, (float)(1.0 - kSegEps))) continue;
+            }
             int64_t v[3];
             double P[3][3], t, u, w;
             load_tri(a, tri, v, P);
@@ -329,6 +424,9 @@ __device__ double shadow(const TraceArgs &a, const double p[3], int own) {
                 const double al = (1.0 - u - w) * __ldg(a.alpha + v[0]) + u * __ldg(a.alpha + v[1]) +
                                   w * __ldg(a.alpha + v[2]);
                 S *= 1.0 - al;
+                // the light is blocked to within T_eps: the colour's shadow factor moves by at
+                // most (1 - ambient) T_eps, the primary composite's own termination bound
+                if (S < a.T_eps) return S;
             }
             continue;
         }
@@ -361,6 +459,7 @@ __global__ void __launch_bounds__(kTraceThreads) trace_kernel(const __grid_const
     float id[3];
 #pragma unroll
     for (int r = 0; r < 3; ++r) id[r] = 1.0f / (float)d[r];
+    const RayF rf = ray_f(o, d);
     const int64_t n = a.T;
     double T = 1.0, C0 = 0.0, C1 = 0.0, C2 = 0.0;
     double after_t = -1.0e300;
@@ -372,12 +471,28 @@ __global__ void __launch_bounds__(kTraceThreads) trace_kernel(const __grid_const
         int stack[kStack];
         int sp = 0;
         stack[sp++] = 0;
+        // Boxes wholly before the last composited crossing hold nothing for this pass, and
+        // boxes wholly beyond the farthest kept crossing of a full buffer only mean another
+        // pass; both bounds are widened by 1e-5 relative, far above the slab test's rounding.
+        const float t_after = after_t > 0.0 ? (float)after_t * (1.0f - 1e-5f) : 0.0f;
         while (sp > 0) {
             const int node = stack[--sp];
             const BvhNode &nd = a.nodes[node];
-            if (!box_hit(nd, of, id, (float)c.znear * 0.999f, 3.0e38f)) continue;
+            float tn, tf;
+            if (!box_span(nd, of, id, (float)c.znear * 0.999f, 3.0e38f, tn, tf)) continue;
+            if (tf < t_after) continue;
+            if (nb == kTraceKB && tn > (float)buf[kTraceKB - 1].t * (1.0f + 1e-5f)) {
+                more = true;
+                continue;
+            }
             if (node >= n - 1) {
                 const int tri = a.leaf_tri[node - (n - 1)];
+                {
+                    // crossings before the last composited one were taken in an earlier pass
+                    float Pf[3][3];
+                    tri_f(a, tri, Pf);
+                    if (!mt_may_hit(rf, Pf[0], Pf[1], Pf[2], fmaxf(c.znear, (float)after_t), 3.0e38f)) continue;
+                }
                 int64_t v[3];
                 double P[3][3], t, u, w;
                 load_tri(a, tri, v, P);
