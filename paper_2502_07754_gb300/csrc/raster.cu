@@ -295,14 +295,34 @@ __global__ void __launch_bounds__(kRastWarps * 32) raster_kernel(const __grid_co
 
 // Exclusive scan of u32 counts into u32 offsets (decoupled look-back over virtual block
 // ids, bounded waits); the grand total goes to *total_out.
+//
+// With SLOTS the scan runs over the pixels in tile order (slot s = tile * TILE^2 + row *
+// TILE + column within the tile; slots outside the image count 0 and get no offset), so the
+// fragment records of one screen tile are contiguous: the passes that walk the records in
+// order (the adjoint chain) then find the same fans again within a few hundred records,
+// and the fill's writes for a tile stay in one region of the buffer.
 constexpr int kScanThreads = 256, kScanItems = 8, kScanTile = kScanThreads * kScanItems;
 constexpr unsigned long long kFlagAgg = 1ull << 62, kFlagPre = 2ull << 62, kValMask = (1ull << 62) - 1;
 
+// Pixel index of slot s (tile-ordered pixels), or -1 for a slot outside its view's image.
+__device__ __forceinline__ int64_t slot_pixel(const ViewTable &vt, int tile_shift, int64_t s) {
+    const uint32_t t = (uint32_t)(s >> (2 * tile_shift));
+    const int local = (int)(s & ((1 << (2 * tile_shift)) - 1));
+    const ViewDev &vw = vt.v[view_of_tile(vt, t)];
+    const int lt = (int)(t - vw.tile_base), tiles_x = (int)vw.tiles_x;
+    const int x = ((lt % tiles_x) << tile_shift) + (local & ((1 << tile_shift) - 1));
+    const int y = ((lt / tiles_x) << tile_shift) + (local >> tile_shift);
+    if (x >= vw.cam.width || y >= vw.cam.height) return -1;
+    return (int64_t)vw.pix_base + (int64_t)y * vw.cam.width + x;
+}
+
+template <bool SLOTS>
 __global__ void __launch_bounds__(kScanThreads) scan_u32_kernel(const uint32_t *__restrict__ counts,
                                                                 uint32_t *__restrict__ offsets, int64_t n,
                                                                 int64_t nblocks, unsigned long long *state,
                                                                 unsigned *ticket, unsigned long long *total_out,
-                                                                Status *st) {
+                                                                Status *st, const __grid_constant__ ViewTable vt,
+                                                                int tile_shift) {
     __shared__ int s_vid;
     __shared__ uint32_t s_warp[kScanThreads / 32];
     __shared__ unsigned long long s_excl;
@@ -312,10 +332,12 @@ __global__ void __launch_bounds__(kScanThreads) scan_u32_kernel(const uint32_t *
     const int64_t vid = s_vid;
     const int64_t base = vid * kScanTile + (int64_t)tid * kScanItems;
     uint32_t v[kScanItems];
+    int64_t pi[kScanItems];
     uint32_t sum = 0;
 #pragma unroll
     for (int i = 0; i < kScanItems; ++i) {
-        v[i] = base + i < n ? counts[base + i] : 0u;
+        pi[i] = base + i < n ? (SLOTS ? slot_pixel(vt, tile_shift, base + i) : base + i) : -1;
+        v[i] = pi[i] >= 0 ? counts[pi[i]] : 0u;
         sum += v[i];
     }
     uint32_t x = sum;
@@ -370,7 +392,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_u32_kernel(const uint32_t *
 #pragma unroll
     for (int i = 0; i < kScanItems; ++i) {
         // offsets beyond 2^32 are clamped; such a buffer overflows its capacity anyway
-        if (base + i < n) offsets[base + i] = (uint32_t)(run < 0xffffffffull ? run : 0xffffffffull);
+        if (pi[i] >= 0) offsets[pi[i]] = (uint32_t)(run < 0xffffffffull ? run : 0xffffffffull);
         run += v[i];
     }
 }
@@ -520,9 +542,9 @@ cudaError_t launch_raster_count(const RenderArgs &ra, cudaStream_t st) {
     uint32_t *ibase = reinterpret_cast<uint32_t *>(ws + L.off_tile_ibase);
     const int tg = (L.n_tiles + 255) / 256;
     tile_item_count_kernel<<<tg, 256, 0, st>>>(ranges, L.n_tiles, nitems);
-    scan_u32_kernel<<<(unsigned)L.tscan_blocks, kScanThreads, 0, st>>>(
+    scan_u32_kernel<false><<<(unsigned)L.tscan_blocks, kScanThreads, 0, st>>>(
         nitems, ibase, L.n_tiles, L.tscan_blocks, reinterpret_cast<unsigned long long *>(ws + L.off_tscan_state),
-        &status->tscan_ticket, &status->items_total, status);
+        &status->tscan_ticket, &status->items_total, status, ra.vt, 0);
     tile_item_emit_kernel<<<tg, 256, 0, st>>>(ranges, L.n_tiles, nitems, ibase,
                                               reinterpret_cast<uint4 *>(ws + L.off_items), L.max_items, status,
                                               (unsigned long long)L.frag_cap);
@@ -536,11 +558,13 @@ cudaError_t launch_raster_count(const RenderArgs &ra, cudaStream_t st) {
         item_prefix_kernel<32><<<L.n_tiles, 1024, 0, st>>>(nitems, ibase, ra.vt, a.icnt, cnts, hist);
     else
         item_prefix_kernel<16><<<L.n_tiles, 256, 0, st>>>(nitems, ibase, ra.vt, a.icnt, cnts, hist);
-    const int64_t n = L.npx;
-    scan_u32_kernel<<<(unsigned)L.scan_blocks, kScanThreads, 0, st>>>(
+    int tile_shift = 0;
+    while ((1 << tile_shift) < L.tile) ++tile_shift;
+    const int64_t n = (int64_t)L.n_tiles << (2 * tile_shift);   // pixel slots in tile order
+    scan_u32_kernel<true><<<(unsigned)L.scan_blocks, kScanThreads, 0, st>>>(
         reinterpret_cast<const uint32_t *>(ws + L.off_counts), reinterpret_cast<uint32_t *>(ws + L.off_offsets), n,
         L.scan_blocks, reinterpret_cast<unsigned long long *>(ws + L.off_scan_state), &status->scan_ticket,
-        &status->frags, status);
+        &status->frags, status, ra.vt, tile_shift);
     e = cudaGetLastError();
     if (e == cudaSuccess) count_launches(6);
     if (e == cudaSuccess) e = launch_pixel_order(ra, st);
