@@ -108,10 +108,12 @@ __device__ __forceinline__ void chain_record(const ChainArgs &a, const float4 gr
     }
 }
 
-// Each warp walks chunks of kChainChunk consecutive records (neighbouring pixels, so the
-// next pass over the chunk finds the same fans in L1), loading the next record's words
-// while it works on the current one.
-constexpr int kChainChunk = 32 * 8;
+// Each warp walks chunks of kChainChunk consecutive records, loading the next record's
+// words while it works on the current one.  The warps of a block take consecutive chunks,
+// so with the records in tile order a block works through one screen tile at a time and
+// its warps find the same fans in the SM's L1 (measured on the 1M-fan 1080p step: chunks
+// of 32, 64, 128, 256 and 512 records gave 1.17, 0.94, 0.91, 0.97 and 1.02 ms).
+constexpr int kChainChunk = 32 * 4;
 
 __global__ void __launch_bounds__(kChainThreads) record_chain_kernel(const __grid_constant__ ChainArgs a) {
     const unsigned long long nrec_all = a.st->frags;
