@@ -126,7 +126,7 @@ RenderLayout render_layout(int64_t n_fans, int K, const ms_camera *cams, int n_v
     L.frag_cap = fcap;
     L.bin_fan_blocks = (n_fans + 255) / 256;
     L.bin_blocks = L.bin_fan_blocks * n_views;
-    L.sort_blocks = (cap + 8191) / 8192;   // sort tiles of 8192 elements
+    L.sort_blocks = (cap + sort_tile_elems() - 1) / sort_tile_elems();
     L.scan_blocks = ((int64_t)L.n_tiles * L.tile * L.tile + 2047) / 2048;   // pixel slots in tile order
     L.max_items = L.n_tiles + (cap + kItemFans - 1) / kItemFans;
     L.tscan_blocks = ((int64_t)L.n_tiles + 2047) / 2048;

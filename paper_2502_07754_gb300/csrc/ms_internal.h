@@ -96,6 +96,8 @@ cudaError_t launch_sort(const RenderArgs &a, cudaStream_t st);
 // buffers, *result receives the one holding the sorted elements; scratch (device,
 // sort_scratch_bytes, 16-byte aligned) is cleared and used for counts and look-back flags.
 size_t sort_scratch_bytes(int64_t n, int passes);
+// Elements of one sort tile (one look-back slot per tile and digit).
+int64_t sort_tile_elems();
 cudaError_t sort_u64(unsigned long long *a, unsigned long long *b, int64_t n, int shift, int passes, char *scratch,
                      cudaStream_t st, unsigned long long **result);
 constexpr int kItemFans = 64;   // fans per raster work item

@@ -9,7 +9,8 @@
 // with the binary32 decision formulas.  No block barriers are used.
 //
 // Count pass: per (item, pixel) fragment counts, the coverage mask of every (fan, pixel)
-// test, and per pair its first mask index and its pixel rectangle within the tile.  A
+// test, and per pair its first mask index and its pixel rectangle within the tile (zero
+// when the pair covers no pixel centre, so the fill skips it).  A
 // per-tile prefix over the tile's items turns the counts into each item's starting slot
 // within the pixel and gives the pixel totals; an exclusive scan over pixels gives record
 // offsets.  Fill pass: the same walk, reading the stored masks and rectangles instead of
@@ -137,7 +138,10 @@ __global__ void __launch_bounds__(kRastWarps * 32) raster_kernel(const __grid_co
                 q = (uint32_t)((e >> a.fan_bits) & ((1ull << a.depth_bits) - 1ull));
                 fan = (uint32_t)(e & ((1ull << a.fan_bits) - 1ull));
             }
-            stage_fans<LPF>(sc, S, K, lane, slot < cnt, fan, q, LEVEL, !stored);
+            // a stored chunk skips the values of pairs that the count pass found without any
+            // covered pixel centre (their rectangle word is 0)
+            const uint32_t sgeo = __shfl_sync(0xffffffffu, pinf.y, slot);
+            stage_fans<LPF>(sc, S, K, lane, slot < cnt && (!stored || sgeo != 0u), fan, q, LEVEL, !stored);
             if (SPLAT && lane < cnt)
                 s_spl[lane] = splat_setup(a.spl, *sc.cam,
                                           (uint32_t)(__ldg(a.keys + cb + lane) & ((1ull << a.fan_bits) - 1ull)));
@@ -178,9 +182,9 @@ __global__ void __launch_bounds__(kRastWarps * 32) raster_kernel(const __grid_co
                 if ((uint64_t)b + (uint64_t)total <= (uint64_t)rsz) mbase = reg * rsz + b;
             }
             mbase = __shfl_sync(0xffffffffu, mbase, 0);
-            if (lane < cnt) a.pinfo[cb + lane] = make_uint2(mbase == ~0u ? ~0u : mbase + (uint32_t)excl, my_geo);
         }
         if (MODE == kFill) my_moff = pinf.x;
+        uint32_t fan_hit = 0;   // count pass: bit f set when staged fan f covers some pixel centre
         for (int base = 0; base < total; base += 32) {
             const int idx = base + lane;
             int f = 0;   // first lane (fan) whose inclusive count exceeds idx
@@ -216,6 +220,7 @@ __global__ void __launch_bounds__(kRastWarps * 32) raster_kernel(const __grid_co
                 if (MODE == kCount && mbase != ~0u) a.masks[mbase + (uint32_t)idx] = (uint16_t)hits;
                 if (hits) lp = (py - ty0) * TILE + (px - tx0);
             }
+            if (MODE == kCount) fan_hit |= __reduce_or_sync(0xffffffffu, hits ? 1u << f : 0u);
             const int nf = __popc(hits);
             c_frag += nf;
             if (!FILL) {   // counting: the order of a pixel's slots does not matter yet
@@ -280,6 +285,10 @@ __global__ void __launch_bounds__(kRastWarps * 32) raster_kernel(const __grid_co
             }
             __syncwarp();   // the next batch may append to the same pixels
         }
+        // each pair's first mask index, and its rectangle if it covers any pixel centre
+        if (MODE == kCount && lane < cnt)
+            a.pinfo[cb + lane] = make_uint2(mbase == ~0u ? ~0u : mbase + (uint32_t)excl,
+                                            ((fan_hit >> lane) & 1u) ? my_geo : 0u);
         __syncwarp();
     }
     if (!FILL) {

@@ -213,6 +213,8 @@ __global__ void set_pairs_kernel(Status *st, int64_t n) { st->pairs = (unsigned 
 
 }  // namespace
 
+int64_t sort_tile_elems() { return kSortTile; }
+
 size_t sort_scratch_bytes(int64_t n, int passes) {
     const int64_t blocks = (n + kSortTile - 1) / kSortTile;
     return 256 + 8 * 256 * 4 + (size_t)passes * (size_t)(blocks > 0 ? blocks : 1) * 256 * 4;
