@@ -66,6 +66,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-autotune", action="store_true")
+    p.add_argument("--input-order", action="store_true",
+                   help="keep the Gaussians in the generator's order (no spatial storage order)")
     p.add_argument("--no-next-rows", action="store_true",
                    help="skip the rows beyond the hot path (full-loss fine-tune, three-fan, mesh prior, ray tracing)")
     p.add_argument("--no-other-workloads", action="store_true",
@@ -405,6 +407,31 @@ def error_windows(W, H, size=96, seed=7):
     return wins
 
 
+# Gaussians are stored in the order ms_spatial_order gives (Morton order of the means), the
+# way a scene is loaded for training: set by --input-order to keep the generator's order.
+SPATIAL_ORDER = True
+
+
+def stored_in_spatial_order(w):
+    """The workload with its Gaussians (and the jittered target scene, by the same
+    permutation) stored in the order the library's ms_spatial_order computes on the GPU;
+    done once, before anything is timed.  The method does not depend on the order of its
+    inputs (exact depth ties aside); the render's gathers and the adjoint's gradient sums
+    do."""
+    if not SPATIAL_ORDER:
+        return w
+    import torch
+    import synthetic
+    import paper_2502_07754_gb300 as ms
+    p = ms.spatial_order(torch.from_numpy(np.ascontiguousarray(w.scene.means)).cuda()).cpu().numpy()
+    reorder = lambda s_: synthetic.Scene(s_.means[p], s_.log_scales[p], s_.quats[p], s_.opacity[p], s_.sh[p],
+                                         s_.sh_degree, s_.sh_bf16)
+    w.scene = reorder(w.scene)
+    if w.target_scene is not None:
+        w.target_scene = reorder(w.target_scene)
+    return w
+
+
 def timed(fn, steps, flush, stream):
     """Mean CUDA-event milliseconds of fn() over `steps` calls, L2 flushed before each."""
     import torch
@@ -427,7 +454,7 @@ def compact_single(idx, steps, warmup, flush):
 
     import synthetic
     import paper_2502_07754_gb300 as ms
-    w = synthetic.workload(idx)
+    w = stored_in_spatial_order(synthetic.workload(idx))
     sc, K, cam = w.scene, w.K, w.cameras[0]
     tg = w.target_scene or synthetic.jittered(sc, 1e-3, 1100 + idx)
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
@@ -471,7 +498,7 @@ def compact_batch(idx, steps, warmup, flush):
 
     import synthetic
     import paper_2502_07754_gb300 as ms
-    w = synthetic.workload(idx)
+    w = stored_in_spatial_order(synthetic.workload(idx))
     sc, K, cams = w.scene, w.K, w.cameras
     centre = cams[0].C
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
@@ -555,7 +582,7 @@ def row_full_fine_tune(flush, steps, warmup):
     import synthetic
     import paper_2502_07754_gb300 as ms
     from paper_2502_07754_gb300.finetune import FanFineTune
-    w = synthetic.workload(3)
+    w = stored_in_spatial_order(synthetic.workload(3))
     sc, K, cam = w.scene, w.K, w.cameras[0]
     G, tG = _scene_tensors(sc), _scene_tensors(w.target_scene)
     target = ms.Renderer(sc.n, K, cam).forward(*ms.mesh_build(*tG, sc.sh_degree, K=K, cam_center=cam.C)).clone()
@@ -586,7 +613,7 @@ def row_three_fan(flush, steps, warmup):
     import torch
     import synthetic
     import paper_2502_07754_gb300 as ms
-    w = synthetic.workload(2)
+    w = stored_in_spatial_order(synthetic.workload(2))
     sc, K, cam = w.scene, w.K, w.cameras[0]
     ls = sc.log_scales.copy()
     ls[:, 0] = ls[:, 1] - np.log(3.0)
@@ -689,7 +716,7 @@ def row_ray_tracing(flush, steps, warmup):
     import torch
     import synthetic
     import paper_2502_07754_gb300 as ms
-    w = synthetic.workload(2)
+    w = stored_in_spatial_order(synthetic.workload(2))
     sc, K, cam = w.scene, w.K, w.cameras[0]
     G = _scene_tensors(sc)
     xyz, rgb, a = ms.mesh_build(*G, sc.sh_degree, K=K, cam_center=cam.C)
@@ -749,7 +776,7 @@ def run_ours(args, ws, rank, local):
         _lib.lib()
     barrier(ws)
     L = _lib.lib(build_if_missing=False)
-    w = synthetic.workload(args.workload, n=args.gaussians or None)
+    w = stored_in_spatial_order(synthetic.workload(args.workload, n=args.gaussians or None))
     sc, K, cam = w.scene, w.K, w.cameras[0]
     W, H = cam.width, cam.height
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
@@ -915,7 +942,9 @@ def run_ours(args, ws, rank, local):
             "config": {"workload": w.name, "gaussians": sc.n, "K": K, "resolution": f"{W}x{H}",
                        "sh": f"degree {sc.sh_degree} {'bf16' if sc.sh_bf16 else 'f32'}",
                        "step": "mesh_build+render+l1+render_backward+adam", "tile": args.tile, "kbuf": args.kbuf,
-                       "l2": "flushed before every timed step (256 MB write)", "parallelism": "replicas"},
+                       "l2": "flushed before every timed step (256 MB write)", "parallelism": "replicas",
+                       "storage": ("Gaussians in Morton order of their means (ms_spatial_order, at load)"
+                                   if SPATIAL_ORDER else "generator order")},
             "fwd_mpix_s": ws * mpix(W, H, fwd_ms), "fwd_ms": fwd_ms,
             "e2e": e2e, "gpu_launches": int(launches), "clocks": clk.summary(), "roofline": roof, "stages": stages,
             "work": {"pairs": info.pairs, "rect_tests": info.rect_tests, "fragments": info.fragments,
@@ -1037,7 +1066,7 @@ def run_batch(args, ws, rank, local):
         _lib.lib()
     barrier(ws)
     L = _lib.lib(build_if_missing=False)
-    w = synthetic.workload(args.workload, n=args.gaussians or None)
+    w = stored_in_spatial_order(synthetic.workload(args.workload, n=args.gaussians or None))
     sc, K, cams = w.scene, w.K, w.cameras
     centre = cams[0].C          # SH colours are evaluated once per step for the shared soup
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
@@ -1166,7 +1195,9 @@ def run_batch(args, ws, rank, local):
                        "sh": f"degree {sc.sh_degree} {'bf16' if sc.sh_bf16 else 'f32'}",
                        "step": "mesh_build+batch_render+l1+batch_render_backward+adam in one CUDA graph",
                        "tile": int(br.params.tile), "kbuf": int(br.params.kbuf),
-                       "l2": "flushed before every timed step (256 MB write)", "parallelism": "replicas"},
+                       "l2": "flushed before every timed step (256 MB write)", "parallelism": "replicas",
+                       "storage": ("Gaussians in Morton order of their means (ms_spatial_order, at load)"
+                                   if SPATIAL_ORDER else "generator order")},
             "fwd_mpix_s": ws * npx / (fwd_ms * 1e-3) / 1e6, "fwd_ms": fwd_ms,
             "e2e": e2e, "gpu_launches": int(launches), "clocks": clk.summary(), "roofline": roof, "stages": stages,
             "work": {"pairs": info.pairs, "rect_tests": info.rect_tests, "fragments": info.fragments,
@@ -1191,7 +1222,7 @@ def run_initializer_only(args):
     import torch
     import synthetic
     import paper_2502_07754_gb300 as ms
-    w = synthetic.workload(5, n=args.gaussians or None)
+    w = stored_in_spatial_order(synthetic.workload(5, n=args.gaussians or None))
     sc, K = w.scene, w.K
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
     G = [dev(sc.means), dev(sc.log_scales), dev(sc.quats), dev(sc.opacity),
@@ -1232,7 +1263,9 @@ def run_initializer_only(args):
 
 
 def main():
+    global SPATIAL_ORDER
     args = parse()
+    SPATIAL_ORDER = not args.input_order
     if args.initializer_only:
         run_initializer_only(args)
         return

@@ -23,6 +23,8 @@
  *                       effects the mesh form is for)
  *   ms_mlp_*, ms_mesh_build_mlp   a learned fan initializer on the tensor cores, fused into
  *                       the conversion
+ *   ms_spatial_order, ms_gather_rows   the Gaussians' storage order (Morton order of the
+ *                       means), applied once when a scene is loaded
  *
  * Conventions (all entry points):
  *   - Every pointer named d_* or documented as "device" is caller-owned device memory;
@@ -309,6 +311,31 @@ MS_API ms_status ms_raytrace(const float *xyz, const float *rgb, const float *al
                              int32_t K, const void *bvh, const ms_camera *cam, const float *light, float ambient,
                              float T_eps, const float *bg, float *out_rgba, void *stream);
 MS_API ms_status ms_bvh_status(const void *bvh, int32_t *stack_overflows, void *stream);
+
+/*
+ * Storage order of the Gaussians (no counterpart in the paper, whose render does not
+ * depend on the order of its inputs except for exact depth ties, which go to the lower
+ * triangle index).  ms_spatial_order writes the permutation perm (device int32, N entries)
+ * that sorts the Gaussians by the Morton code of their means: each coordinate quantised to
+ * 10 bits over the means' bounding box, q = min(max(floor((m - lo) / (hi - lo) * 1024), 0),
+ * 1023) in binary32 (an axis of zero extent counts as 1), bits interleaved x, y, z from the
+ * top; equal codes keep the input order.  Gaussians stored in that order (ms_gather_rows
+ * on each attribute array, once, when a scene is loaded) put the fans that meet in one
+ * screen tile near each other in memory, which the render's gathers and the adjoint's
+ * gradient sums profit from.
+ *   means: device N x 3; N < 2^31.  workspace: device, 256-byte aligned, at least
+ *   ms_spatial_order_workspace_size(N) bytes (0 for an invalid N).  Kernel launches on `stream`
+ *   only (the library's radix sort among them), no host synchronisation.
+ * ms_gather_rows: dst row i = src row perm[i] for n_rows rows of row_bytes bytes (a multiple
+ *   of 4; src and dst device, 4-byte aligned, not overlapping; perm device, every entry in
+ *   0..n_rows-1, which the caller guarantees).  One kernel launch.
+ * Errors: MS_ERR_INVALID for bad sizes, NULL or misaligned pointers.
+ */
+MS_API size_t ms_spatial_order_workspace_size(int64_t N);
+MS_API ms_status ms_spatial_order(const float *means, int64_t N, int32_t *perm, void *workspace, size_t ws_bytes,
+                                  void *stream);
+MS_API ms_status ms_gather_rows(const void *src, int64_t n_rows, int64_t row_bytes, const int32_t *perm, void *dst,
+                                void *stream);
 
 /* Bytes of workspace ms_render / ms_render_backward need for n_fans fans of K triangles. */
 MS_API size_t ms_render_workspace_size(int64_t n_fans, int32_t K, const ms_camera *cam,

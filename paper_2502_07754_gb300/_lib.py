@@ -69,6 +69,9 @@ _SIGS = {
     "ms_bvh_build": (C.c_int, [_P, _P, C.c_int64, C.c_int32, _P, C.c_size_t, _P]),
     "ms_raytrace": (C.c_int, [_P, _P, _P, _P, C.c_int64, C.c_int32, _P, _P, _P, C.c_float, C.c_float, _P, _P, _P]),
     "ms_bvh_status": (C.c_int, [_P, _P, _P]),
+    "ms_spatial_order_workspace_size": (C.c_size_t, [C.c_int64]),
+    "ms_spatial_order": (C.c_int, [_P, C.c_int64, _P, _P, C.c_size_t, _P]),
+    "ms_gather_rows": (C.c_int, [_P, C.c_int64, C.c_int64, _P, _P, _P]),
     "ms_fans_to_tris_grads": (C.c_int, [_P, _P, _P, _P, _P, C.c_int64, _P, _P, _P, _P]),
     "ms_mesh_workspace_size": (C.c_size_t, [C.c_int64, _P, _P]),
     "ms_mesh_render": (C.c_int, [_P, _P, _P, _P, C.c_int64, _P, _P, _P, _P, C.c_size_t, _P]),

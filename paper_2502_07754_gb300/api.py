@@ -128,6 +128,34 @@ def mesh_build_3d(means, log_scales, quats, opacity, sh, sh_degree, K=8, scale_m
     return xyz, rgb, alpha
 
 
+def spatial_order(means, stream=None):
+    """Permutation (int32 device tensor of N) that puts the Gaussians in Morton order of
+    their means (ms_spatial_order)."""
+    N = int(means.shape[0])
+    perm = torch.empty(N, dtype=torch.int32, device=means.device)
+    ws = torch.empty(max(int(lib().ms_spatial_order_workspace_size(N)), 256), dtype=torch.uint8, device=means.device)
+    check(lib().ms_spatial_order(_ptr(means.contiguous()), N, _ptr(perm), _ptr(ws), ws.numel(),
+                                 _stream(stream, perm, ws)))
+    return perm
+
+
+def gather_rows(t, perm, stream=None):
+    """Rows of t (first dimension) in the order perm (ms_gather_rows): out[i] = t[perm[i]]."""
+    t = t.contiguous()
+    out = torch.empty_like(t)
+    n = int(t.shape[0])
+    row = t.element_size() * (t.numel() // max(n, 1))
+    check(lib().ms_gather_rows(_ptr(t), n, row, _ptr(perm), _ptr(out), _stream(stream, out)))
+    return out
+
+
+def spatially_ordered(means, *attrs, stream=None):
+    """The Gaussians' arrays (means first, then any per-Gaussian arrays) in Morton order of
+    the means, and the permutation: (perm, means', *attrs')."""
+    perm = spatial_order(means, stream=stream)
+    return (perm, gather_rows(means, perm, stream=stream)) + tuple(gather_rows(a, perm, stream=stream) for a in attrs)
+
+
 def three_fan_copies(K):
     """Copy map of one Gaussian's 3 (K+1) three-fan vertex slots (ms_three_fan_copies):
     (first-copy slot of every slot as a list, number of distinct vertices)."""

@@ -102,3 +102,16 @@ def test_host_side_validation_of_the_fine_tune_entry_points():
     st = L.ms_batch_render(None, None, None, 0, 8, cams, 5, C.byref(p), outs, dummy, 1 << 40, None)
     assert st == _lib.MS_ERR_INVALID
     assert b"pixels" in L.ms_last_error()
+
+
+def test_spatial_order_argument_checks_without_gpu():
+    from paper_2502_07754_gb300 import _lib
+    L = _lib.lib()
+    assert L.ms_spatial_order_workspace_size(-1) == 0
+    assert L.ms_spatial_order_workspace_size(1 << 31) == 0
+    assert L.ms_spatial_order_workspace_size(1000) > 8 * 1000 * 2
+    assert L.ms_spatial_order(None, 10, None, None, 0, None) == _lib.MS_ERR_INVALID
+    assert L.ms_spatial_order(None, 0, None, None, 0, None) == _lib.MS_OK       # nothing to order
+    assert L.ms_gather_rows(None, 10, 6, None, None, None) == _lib.MS_ERR_INVALID   # row not whole words
+    assert b"row" in L.ms_last_error()
+    assert L.ms_gather_rows(None, 10, 8, None, None, None) == _lib.MS_ERR_INVALID
