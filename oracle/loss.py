@@ -4,7 +4,7 @@ Only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline leg may import 
 module; it shares no code with the CUDA library.
 
 Sec. 3 "Loss Function" (Eq. 3): a weighted combination of the L1 loss and SSIM with
-lambda = 0.6, taken as in 3DGS.  Readings, each also listed in the design notes:
+lambda = 0.6, taken as in 3DGS.  Readings:
 
 * The SSIM term enters as (1 - lambda)(1 - SSIM): the equation as printed adds SSIM
   itself, which a minimiser would drive down, while the text says the loss follows 3DGS,

@@ -7,7 +7,7 @@ Sec. 3, the mesh-prior paragraphs (the convex-combination equation for the secon
 triangles): on top of a geometry mesh, every face (m_1, m_2, m_3) carries a fixed number
 of disjoint secondary triangles whose vertices are convex combinations
 v_i = a_i1 m_1 + a_i2 m_2 + a_i3 m_3 (a_i on the simplex) with trainable weights, and
-trainable per-vertex colour and opacity.  Readings, each also listed in the design notes:
+trainable per-vertex colour and opacity.  Readings:
 
 * The simplex constraint is kept by the parameterisation a_ik = w_ik^2 / sum_j w_ij^2 of
   free weights w (non-negative, summing to 1, reaching exact zeros, smooth where any w is

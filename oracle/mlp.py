@@ -6,7 +6,7 @@ module; it shares no code with the CUDA library.
 The initializer is a small multilayer perceptron that maps a Gaussian's parameters to
 per-vertex corrections of its fan, standing in for part of the fine-tuning of Sec. 3
 ("Fine-tuning", "Optimization and Pruning": vertex positions and opacities are
-optimised after the conversion).  Readings, each also listed in the design notes:
+optimised after the conversion).  Readings:
 
 * Input (15 features + a constant 1 = 16): log-scales (3), the normalised quaternion
   (w, x, y, z) (4), opacity (1), the degree-0 SH coefficients (3), the scales sorted in

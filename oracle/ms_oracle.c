@@ -15,7 +15,7 @@
  *     peeling with an unbounded number of layers composites every fragment of a
  *     pixel in depth order; this file does exactly that with a full sort.
  *
- * Readings where the paper is silent (each one is listed in the design notes):
+ * Readings where the paper is silent:
  *   angles theta_i = -pi + 2 pi i / K (K distinct angles in [-pi, pi));
  *   quaternion (w,x,y,z) normalised before use; s are log-scales;
  *   colour = max(0, 0.5 + sum_lm Y_lm(dir) f_lm), dir = normalize(m - camera centre);

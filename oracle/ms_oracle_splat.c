@@ -4,7 +4,7 @@
  * The image the fans stand in for: every flat Gaussian (m, R, S, sigma, colour) of the
  * scene drawn as itself (Sec. 3: the Gaussian component with mean m, rotation R, scale
  * S and opacity sigma, in the GaMeS flat form whose thin axis is dropped), composited in
- * depth order exactly like the fans.  Readings (also listed in the design notes):
+ * depth order exactly like the fans.  Readings:
  *   - the pixel ray x = C + t d, d = R_cw^T ((px - cx)/fx, (py - cy)/fy, 1), meets the
  *     plane through m spanned by the two kept unit axes u_a, u_b (same axis rule as the
  *     fan conversion) at local coordinates u = (x - m).u_a, v = (x - m).u_b;

@@ -6,7 +6,7 @@ module; it shares no code with the CUDA library.
 
 The paper's motivation (Sec. 1 and the discussion of ray-tracing renderers) is that a
 triangle soup can be ray traced with secondary effects such as shadows; it gives no
-shading model.  Readings, each also listed in the design notes:
+shading model.  Readings:
 
 * Primary rays: the pixel-centre ray of the pinhole camera; every triangle it crosses in
   front of the near plane is a fragment with the ray's barycentrics (which equal the

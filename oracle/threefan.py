@@ -11,8 +11,7 @@ quaternion); one fan per pair of axes (1, 2), (1, 3), (2, 3), each with K bounda
 v_i = m + cos(t_i) sr_a + sin(t_i) sr_b at the angles t_i = -pi + 2 pi i / K (the reading
 of the flat case), and K triangles (m, v_i, v_{i+1 mod K}); 3K triangles per Gaussian.
 Colour and opacity as in the flat case: every vertex carries the Gaussian's colour, the
-centre its opacity sigma and the boundary vertices opac_mul sigma.  Readings, each also
-listed in the design notes:
+centre its opacity sigma and the boundary vertices opac_mul sigma.  Readings:
 
 * "Shared points at surface intersections": the fans meet where a boundary vertex is an
   axis tip m +- sr_k, which two fans reach when both contain the angle giving that tip;
