@@ -58,9 +58,9 @@ struct ResolveArgs {
 // the 32 lanes of a warp walk lists of about the same length and the deepest pixels
 // start first instead of trailing at the end of the grid.  Backward: the same sort within
 // spans of kOrderSpan consecutive pixels only: that pass does little arithmetic per
-// record and is bound by memory latency, and pixels of one span have their records in
-// one small region of the buffer.  The order within one count varies from run to run;
-// no pixel's result depends on it.
+// record and is bound by memory latency, and the pixels of one span (part of a row) have
+// their records in the regions of the row's tiles (records are laid out tile by tile).
+// The order within one count varies from run to run; no pixel's result depends on it.
 constexpr int kOrderThreads = 256, kOrderItems = 4, kOrderSpan = kOrderThreads * kOrderItems;
 
 // Exclusive prefix of v over the buckets in descending order (thread t holds bucket 255 - t).
