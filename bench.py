@@ -43,7 +43,7 @@ NSTAGE = len(STAGES)
 # sources it was taken on; reported only while the digest still matches.  Measured on that
 # workload itself (one pass per launch): work items 0.2 MB, count 193, tile prefix 24, pixel
 # scan 8, pixel order 8, fill 648, resolve 491.
-TRAFFIC = {"raster": {"bytes": 1.37e9, "digest": "c8b16ba63f1a3039"}}
+TRAFFIC = {"raster": {"bytes": 1.37e9, "digest": "94721382e11f362b"}}
 
 
 def kernel_digest():
