@@ -29,7 +29,10 @@ struct ChainArgs {
     ViewTable vt;
 };
 
-constexpr int kChainThreads = 256;
+// 7 warps a block and at most 73 registers (no spills), so four blocks (28 warps) share an
+// SM: the chain waits on scattered loads and wants warps in flight; 8 warps at 76 registers
+// fit three blocks (24 warps) and measured 5% slower on the 1M-fan step.
+constexpr int kChainThreads = 224;
 
 // One record's chain: adds its contributions to the three vertices' gradient sums.
 __device__ __forceinline__ void chain_record(const ChainArgs &a, const float4 gr, const float4 id) {
@@ -115,7 +118,7 @@ __device__ __forceinline__ void chain_record(const ChainArgs &a, const float4 gr
 // of 32, 64, 128, 256 and 512 records gave 1.17, 0.94, 0.91, 0.97 and 1.02 ms).
 constexpr int kChainChunk = 32 * 4;
 
-__global__ void __launch_bounds__(kChainThreads) record_chain_kernel(const __grid_constant__ ChainArgs a) {
+__global__ void __launch_bounds__(kChainThreads, 4) record_chain_kernel(const __grid_constant__ ChainArgs a) {
     const unsigned long long nrec_all = a.st->frags;
     const int64_t nrec = (int64_t)(nrec_all < (unsigned long long)a.frag_cap ? nrec_all : (unsigned long long)a.frag_cap);
     const int lane = threadIdx.x & 31;
