@@ -836,50 +836,72 @@ def run_ours(args, ws, rank, local):
     xyz, rgb, a = convert(G)
     rend.forward(xyz, rgb, a)           # sizes the pair capacity (host check, untimed)
     V = xyz.shape[0]
-    adam = ms.FanAdam(xyz, rgb, a)
+    adam = ms.FanAdam(xyz, rgb, a, device_step=True)
     out = torch.empty(H, W, 4, device="cuda")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
     def step(gs):
-        x, c, al = convert(gs)
+        x, c, al = ms.mesh_build(*gs, sc.sh_degree, K=K, cam_center=cam.C, out=(xyz, rgb, a))
         rend.forward(x, c, al, out=out, check_status=False)
         loss, dL = ms.l1_loss(out, target)
         rend.backward(x, c, al, out, dL, into_workspace=True)   # gradients stay in the workspace
         adam.step_ws(x, c, al, rend)
         return loss
 
+    def capture(gs):
+        # one step captured in a CUDA graph (after an eager run on a side stream)
+        s_ = torch.cuda.Stream()
+        s_.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s_):
+            step(gs)
+        torch.cuda.current_stream().wait_stream(s_)
+        g_ = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g_):
+            loss_ = step(gs)
+        return g_, loss_
+
     for _ in range(args.warmup):
         step(G)
     torch.cuda.synchronize()
     st, info = rend.info()
     _lib.check(st)
+    launches0 = L.ms_kernel_launches()
+    graph, _ = capture(G)
+    launches = (L.ms_kernel_launches() - launches0) // 2   # the eager run and the capture
+    for _ in range(args.warmup):
+        graph.replay()
+    torch.cuda.synchronize()
 
-    # ---- timed region: K full steps, L2 flushed before each, per-step CUDA events
+    # ---- timed region: K full steps (graph replays), L2 flushed before each, per-step CUDA events
     ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    L.ms_profile_read(None, None, 0)
-    launches0 = L.ms_kernel_launches()
-    L.ms_profile_enable(1)
     barrier(ws)
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
         for i in range(args.steps):
             flush.zero_()
             ev0[i].record(stream)
-            step(G)
+            graph.replay()
             ev1[i].record(stream)
         torch.cuda.synchronize()
     barrier(ws)
-    L.ms_profile_enable(0)
-    launches = (L.ms_kernel_launches() - launches0) // args.steps
-    stage_ms = (C.c_double * NSTAGE)()
-    stage_n = (C.c_int64 * NSTAGE)()
-    _lib.check(L.ms_profile_read(stage_ms, stage_n, NSTAGE))
     step_ms = sum(a_.elapsed_time(b_) for a_, b_ in zip(ev0, ev1)) / args.steps
     step_ms = max_over_ranks(step_ms, ws)
     st, info = rend.info()
     _lib.check(st)
+
+    # per-stage times from eager steps with the stage profiler on (not the headline number)
+    L.ms_profile_read(None, None, 0)
+    L.ms_profile_enable(1)
+    for _ in range(5):
+        flush.zero_()
+        step(G)
+    torch.cuda.synchronize()
+    L.ms_profile_enable(0)
+    stage_ms = (C.c_double * NSTAGE)()
+    stage_n = (C.c_int64 * NSTAGE)()
+    _lib.check(L.ms_profile_read(stage_ms, stage_n, NSTAGE))
 
     # ---- forward-only throughput (render call alone)
     f0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -941,19 +963,27 @@ def run_ours(args, ws, rank, local):
         # serial: copy, step and read-back one after the other (L2 flushed before each)
         e0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
         e1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ge = [capture(devGs[0]), capture(devGs[1])]   # one captured step per input set
+        for k in (0, 1):
+            ge[k][0].replay()
+        torch.cuda.synchronize()
         devG = devGs[0]
         for i in range(args.steps):
             flush.zero_()
             e0[i].record(stream)
             for d_, h_ in zip(devG, hostG):
                 d_.copy_(h_, non_blocking=True)
-            loss = step(devG)
-            loss_host.copy_(loss, non_blocking=True)
+            ge[0][0].replay()
+            loss_host.copy_(ge[0][1], non_blocking=True)
             e1[i].record(stream)
         torch.cuda.synchronize()
         serial_ms = max_over_ranks(sum(a_.elapsed_time(b_) for a_, b_ in zip(e0, e1)) / args.steps, ws)
         # pipelined: the next step's inputs copied while this one computes
-        e2e_ms = max_over_ranks(pipelined_e2e(lambda k: step(devGs[k]), hostG, devGs, args.steps, stream), ws)
+        def run_step(k):
+            ge[k][0].replay()
+            return ge[k][1]
+
+        e2e_ms = max_over_ranks(pipelined_e2e(run_step, hostG, devGs, args.steps, stream), ws)
         e2e = {"value": ws * mpix(W, H, e2e_ms), "unit": "Mpix/s", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": 4, "ms_per_step": e2e_ms,
                "pipeline": "step i + 1's inputs copied on a second stream during step i (two input sets)",
@@ -986,7 +1016,7 @@ def run_ours(args, ws, rank, local):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": w.name, "gaussians": sc.n, "K": K, "resolution": f"{W}x{H}",
                        "sh": f"degree {sc.sh_degree} {'bf16' if sc.sh_bf16 else 'f32'}",
-                       "step": "mesh_build+render+l1+render_backward+adam", "tile": args.tile, "kbuf": args.kbuf,
+                       "step": "mesh_build+render+l1+render_backward+adam in one CUDA graph", "tile": args.tile, "kbuf": args.kbuf,
                        "l2": "flushed before every timed step (256 MB write)", "parallelism": "replicas",
                        "storage": ("Gaussians in Morton order of their means (ms_spatial_order, at load)"
                                    if SPATIAL_ORDER else "generator order")},
